@@ -1,0 +1,90 @@
+"""Local effective-field terms, total H_eff and the micromagnetic energy (FP64).
+
+Paper: Sec. 2.1 lists five contributions to H_eff (magnetostatic, exchange,
+applied, anisotropy, thermal).
+
+* exchange (Sec. 2.1.2, Eq. 3): H_ex = 2A/(mu0 Ms) lap(m), discretised with the
+  6-neighbour scheme that drops to 4 neighbours when nz = 1.  A missing
+  neighbour at an open boundary contributes nothing (free/Neumann boundary);
+  periodic axes wrap.
+* uniaxial anisotropy (Sec. 2.1.3, Eq. 4, phi = Ku sin^2 theta):
+  H_an = 2 Ku/(mu0 Ms) (m . u) u, Ku > 0 an easy axis u (unit vector).
+* Zeeman: H_z = B / mu0 for an applied flux density B in tesla.
+* thermal (Sec. 2.1.3, Eq. 6): H_th = eta sqrt(2 alpha kB T / (gamma0 mu0 Ms V dt)),
+  eta ~ N(0,1) per cell, component and step (drawn by ``philox``).
+
+Energy (not printed in the paper; the standard micromagnetic energy whose
+variational derivative is the field above):
+    E = - mu0 Ms V sum_i [ 1/2 m.(H_d + H_ex + H_an) + m.H_z ].
+
+m: (3, nz, ny, nx) float64, unit vectors.  Fields in A/m, energy in J.
+Pins: tests/test_oracle_fields.py (uniform state, spin-wave eigenvalue,
+closed-form anisotropy, energy = sum of bond energies, Langevin statistics).
+"""
+
+import numpy as np
+
+MU0 = 4.0e-7 * np.pi          # H/m
+KB = 1.380649e-23             # J/K
+GAMMA0 = 2.211e5              # m/(A s): gamma acting on H in A/m (a reading)
+
+
+def exchange_field(m, Ms, Aex, cell, pbc=(False, False, False)):
+    """H_ex = 2A/(mu0 Ms) sum_axes sum_{existing nbr j} (m_j - m_i) / d_axis^2."""
+    m = np.asarray(m, float)
+    H = np.zeros_like(m)
+    pref = 2.0 * Aex / (MU0 * Ms)
+    # array axes: 3 -> x, 2 -> y, 1 -> z
+    for axis, d, per in ((3, cell[0], pbc[0]), (2, cell[1], pbc[1]), (1, cell[2], pbc[2])):
+        n = m.shape[axis]
+        if n == 1 and not per:
+            continue
+        for shift in (1, -1):
+            nb = np.roll(m, shift, axis=axis)           # value of the neighbour
+            diff = nb - m
+            if not per:
+                # the neighbour of the first/last cell is missing: no contribution
+                sl = [slice(None)] * 4
+                sl[axis] = 0 if shift == 1 else n - 1
+                diff[tuple(sl)] = 0.0
+            H += diff / (d * d)
+    return pref * H
+
+
+def anisotropy_field(m, Ms, Ku, u):
+    """H_an = 2 Ku/(mu0 Ms) (m.u) u; u shape (3,) or (3, nz, ny, nx), unit length."""
+    m = np.asarray(m, float)
+    u = np.asarray(u, float)
+    if u.ndim == 1:
+        u = u.reshape(3, 1, 1, 1)
+    mu = (m * u).sum(axis=0, keepdims=True)
+    return (2.0 * Ku / (MU0 * Ms)) * mu * u
+
+
+def zeeman_field(m, B):
+    """H_z = B/mu0 (uniform applied flux density B in T)."""
+    B = np.asarray(B, float).reshape(3, 1, 1, 1)
+    return np.broadcast_to(B / MU0, m.shape).copy()
+
+
+def thermal_sigma(alpha, T, Ms, V, dt, gamma0=GAMMA0):
+    """Standard deviation of each thermal-field component (A/m), Eq. 6."""
+    return np.sqrt(2.0 * alpha * KB * T / (gamma0 * MU0 * Ms * V * dt))
+
+
+def thermal_field(eta, alpha, T, Ms, V, dt, gamma0=GAMMA0):
+    """H_th = eta * sigma, eta standard normal with shape of m."""
+    return np.asarray(eta, float) * thermal_sigma(alpha, T, Ms, V, dt, gamma0)
+
+
+def energy(m, Ms, V, Hd, Hex, Han, Hz):
+    """E = -mu0 Ms V sum [ 1/2 m.(Hd+Hex+Han) + m.Hz ] (J)."""
+    m = np.asarray(m, float)
+    e = 0.5 * (m * (Hd + Hex + Han)).sum() + (m * Hz).sum()
+    return -MU0 * Ms * V * e
+
+
+def torque_max(m, H, Ms):
+    """max_i |m_i x H_i| / Ms (dimensionless)."""
+    c = np.cross(m, H, axis=0)
+    return float(np.sqrt((c * c).sum(axis=0)).max() / Ms)

@@ -1,0 +1,157 @@
+"""Pins for oracle.fields and oracle.philox.
+
+* exchange: uniform state gives zero; a periodic spin wave m = (cos kx, sin kx, 0)
+  is an exact eigenvector of the discrete Laplacian with eigenvalue
+  -(2 - 2 cos k d)/d^2; at a free boundary a missing neighbour adds nothing
+  (checked on a three-cell chain worked by hand);
+* exchange energy equals the bond sum A V sum_bonds |m_i - m_j|^2 / d^2;
+* anisotropy: |H_an| = 2Ku/(mu0 Ms) cos(theta) along u; energy -Ku V cos^2;
+* Zeeman energy -Ms V m.B;
+* demag energy of a uniformly magnetised body: mu0 Ms^2 Vtot N_prism / 2;
+* Philox-4x32-10 known-answer vectors (Salmon et al., SC'11, Random123);
+* the Gaussian draw has zero mean, unit variance, no cross-correlation.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import fields as F
+from oracle import demag, newell, philox
+
+MS, AEX = 8e5, 1.3e-11
+
+
+def test_uniform_state_has_no_exchange_field():
+    m = np.zeros((3, 3, 4, 5))
+    m[1] = 1.0
+    for pbc in [(False,) * 3, (True, True, True)]:
+        H = F.exchange_field(m, MS, AEX, (4e-9, 3e-9, 2e-9), pbc)
+        assert np.max(np.abs(H)) == 0.0
+
+
+@pytest.mark.parametrize("q", [1, 3, 7])
+def test_spin_wave_eigenvalue(q):
+    nx, d = 16, 3e-9
+    k = 2 * np.pi * q / (nx * d)
+    x = np.arange(nx) * d
+    m = np.zeros((3, 1, 1, nx))
+    m[0, 0, 0] = np.cos(k * x)
+    m[1, 0, 0] = np.sin(k * x)
+    H = F.exchange_field(m, MS, AEX, (d, 5e-9, 5e-9), (True, False, False))
+    lam = -(2 - 2 * np.cos(k * d)) / d ** 2
+    expect = 2 * AEX / (F.MU0 * MS) * lam * m
+    assert np.max(np.abs(H - expect)) <= 1e-12 * np.max(np.abs(expect))
+
+
+def test_free_boundary_three_cell_chain():
+    d = 2e-9
+    m = np.zeros((3, 1, 1, 3))
+    m[:, 0, 0, 0] = (1, 0, 0)
+    m[:, 0, 0, 1] = (0, 1, 0)
+    m[:, 0, 0, 2] = (0, 0, 1)
+    H = F.exchange_field(m, MS, AEX, (d, 1e-9, 1e-9))
+    c = 2 * AEX / (F.MU0 * MS) / d ** 2
+    np.testing.assert_allclose(H[:, 0, 0, 0], c * np.array([-1, 1, 0]), rtol=1e-14)     # only right nbr
+    np.testing.assert_allclose(H[:, 0, 0, 1], c * np.array([1, -2, 1]), rtol=1e-14)
+    np.testing.assert_allclose(H[:, 0, 0, 2], c * np.array([0, 1, -1]), rtol=1e-14)     # only left nbr
+
+
+def test_exchange_energy_equals_bond_sum():
+    rng = np.random.default_rng(5)
+    nx, ny, nz = 6, 5, 3
+    cell = (4e-9, 3e-9, 2e-9)
+    m = rng.standard_normal((3, nz, ny, nx))
+    m /= np.linalg.norm(m, axis=0)
+    V = cell[0] * cell[1] * cell[2]
+    H = F.exchange_field(m, MS, AEX, cell)
+    z = np.zeros_like(m)
+    E = F.energy(m, MS, V, z, H, z, z)
+    bonds = 0.0
+    for axis, d in ((3, cell[0]), (2, cell[1]), (1, cell[2])):
+        diff = np.diff(m, axis=axis)
+        bonds += (diff ** 2).sum() / d ** 2
+    assert E == pytest.approx(AEX * V * bonds, rel=1e-12)
+
+
+def test_anisotropy_closed_form():
+    Ku = 5e3
+    u = np.array([1.0, 2.0, 2.0]) / 3.0
+    th = np.linspace(0, np.pi, 7)
+    perp = np.array([2.0, -1.0, 0.0]) / np.sqrt(5)
+    m = (np.cos(th)[:, None] * u + np.sin(th)[:, None] * perp).T.reshape(3, 1, 1, 7)
+    H = F.anisotropy_field(m, MS, Ku, u)
+    expect = (2 * Ku / (F.MU0 * MS)) * np.cos(th)[None, :] * u[:, None]
+    np.testing.assert_allclose(H.reshape(3, 7), expect, rtol=1e-13, atol=1e-9)
+    V = 1e-25
+    z = np.zeros_like(m)
+    for i in range(7):
+        mi = m[:, :, :, i:i + 1]
+        Ei = F.energy(mi, MS, V, z[:, :, :, :1], z[:, :, :, :1], H[:, :, :, i:i + 1], z[:, :, :, :1])
+        assert Ei == pytest.approx(-Ku * V * np.cos(th[i]) ** 2, rel=1e-12, abs=1e-40)
+
+
+def test_zeeman_energy():
+    m = np.zeros((3, 1, 1, 2))
+    m[:, 0, 0, 0] = (0.6, 0.8, 0.0)
+    m[:, 0, 0, 1] = (0.0, 0.0, -1.0)
+    B = np.array([0.01, -0.02, 0.03])
+    V = 2e-26
+    Hz = F.zeeman_field(m, B)
+    z = np.zeros_like(m)
+    E = F.energy(m, MS, V, z, z, z, Hz)
+    assert E == pytest.approx(-MS * V * ((0.6 * 0.01 - 0.8 * 0.02) + (-0.03)), rel=1e-12)
+
+
+def test_uniform_body_demag_energy():
+    shape, cell = (12, 6, 2), (4e-9, 4e-9, 2e-9)
+    nx, ny, nz = shape
+    m = np.zeros((3, nz, ny, nx))
+    m[0] = 1.0
+    V = cell[0] * cell[1] * cell[2]
+    Hd = demag.Demag(shape, cell).field(m, MS)
+    z = np.zeros_like(m)
+    E = F.energy(m, MS, V, Hd, z, z, z)
+    Nxx = float(newell.newell_tensor(0, 0, 0, nx * cell[0], ny * cell[1], nz * cell[2])["xx"])
+    assert E == pytest.approx(0.5 * F.MU0 * MS ** 2 * V * nx * ny * nz * Nxx, rel=1e-10)
+
+
+KAT = [
+    ((0x00000000, 0x00000000, 0x00000000, 0x00000000), (0x00000000, 0x00000000),
+     (0x6627e8d5, 0xe169c58d, 0xbc57ac4c, 0x9b00dbd8)),
+    ((0xffffffff, 0xffffffff, 0xffffffff, 0xffffffff), (0xffffffff, 0xffffffff),
+     (0x408f276d, 0x41c83b0e, 0xa20bc7c6, 0x6d5451fd)),
+    ((0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344), (0xa4093822, 0x299f31d0),
+     (0xd16cfe09, 0x94fdcceb, 0x5001e420, 0x24126ea1)),
+]
+
+
+@pytest.mark.parametrize("ctr,key,expect", KAT)
+def test_philox_known_answers(ctr, key, expect):
+    got = philox.philox4x32_10(*ctr, *key)
+    assert tuple(int(v) for v in got) == expect
+
+
+def test_gaussian_moments():
+    eta = philox.thermal_eta((3, 1, 256, 256), seed=1234, step=7)
+    x = eta.reshape(3, -1)
+    n = x.shape[1]
+    assert np.all(np.abs(x.mean(axis=1)) < 5 / np.sqrt(n))
+    assert np.all(np.abs(x.var(axis=1) - 1.0) < 5 * np.sqrt(2.0 / n))
+    c = np.corrcoef(x)
+    assert np.all(np.abs(c[np.triu_indices(3, 1)]) < 5 / np.sqrt(n))
+    # different step or seed -> different numbers
+    assert not np.allclose(eta, philox.thermal_eta((3, 1, 256, 256), seed=1234, step=8))
+    assert not np.allclose(eta, philox.thermal_eta((3, 1, 256, 256), seed=1235, step=7))
+
+
+def test_uniform_open_interval_exact_in_binary32():
+    w = np.array([0, 1, 511, 512, 0xFFFFFFFF], dtype=np.uint64)
+    u = philox.uniform_open(w)
+    assert np.all(u > 0) and np.all(u < 1)
+    assert np.all(u.astype(np.float32).astype(np.float64) == u)
+
+
+def test_thermal_sigma_units():
+    # sigma^2 * gamma0 mu0 Ms V dt = 2 alpha kB T  (Eq. 6)
+    s = F.thermal_sigma(0.05, 300.0, 1.1e6, 27e-27, 50e-15)
+    assert s * s * F.GAMMA0 * F.MU0 * 1.1e6 * 27e-27 * 50e-15 == pytest.approx(2 * 0.05 * F.KB * 300.0, rel=1e-12)

@@ -1,0 +1,197 @@
+"""Pins for oracle.llg: Landau-Lifshitz right-hand side and the integrators.
+
+Macrospin closed forms (one cubic cell: its own demag field is parallel to m
+and exerts no torque; no exchange partner) with H = B/mu0 along z and
+gamma' = gamma0/(1+alpha^2):
+    phi(t) = phi0 + gamma' H t,   cos theta(t) = tanh(alpha gamma' H t + atanh cos theta0).
+* Larmor: alpha = 0 precession at gamma0 H;
+* uniaxial easy axis along the field (alpha = 0): precession at
+  gamma0 (H + 2Ku/(mu0 Ms) cos theta0), which is Kittel's small-angle FMR
+  frequency gamma0 (H + H_K) as theta0 -> 0;
+* convergence orders 1 (Euler), 2 (Heun), 5 (Dormand-Prince) and order 5 of
+  the embedded error estimate;
+* energy does not increase under damping; relaxation reaches the torque bound;
+* Langevin: an ensemble of uncoupled thermal macrospins in a field has
+  <cos theta> = coth x - 1/x, x = mu0 Ms V H / (kB T), which fixes the variance
+  of Eq. 6 and the noise interpretation of the Heun scheme.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import fields as F
+from oracle import llg
+
+MS = 8e5
+CELL = (4e-9, 4e-9, 4e-9)
+
+
+def _macrospin(alpha, B=0.05, Ku=0.0):
+    return llg.Problem((1, 1, 1), CELL, MS, 1.3e-11, alpha, Ku=Ku, u=(0, 0, 1), B=(0, 0, B))
+
+
+def _m0(theta, phi):
+    return np.array([np.sin(theta) * np.cos(phi), np.sin(theta) * np.sin(phi), np.cos(theta)]).reshape(3, 1, 1, 1)
+
+
+def _exact(alpha, B, theta0, phi0, t):
+    H = B / F.MU0
+    gp = F.GAMMA0 / (1 + alpha ** 2)
+    phi = phi0 + gp * H * t
+    ct = np.tanh(alpha * gp * H * t + np.arctanh(np.cos(theta0)))
+    st = np.sqrt(1 - ct * ct)
+    return np.array([st * np.cos(phi), st * np.sin(phi), ct]).reshape(3, 1, 1, 1)
+
+
+def test_rhs_direction_and_magnitude():
+    # m along x, H along z: precession pushes m towards +y, damping towards +z
+    m = _m0(np.pi / 2, 0.0)
+    H = np.array([0, 0, 1e5]).reshape(3, 1, 1, 1)
+    d = llg.ll_rhs(m, H, 0.1)
+    gp = F.GAMMA0 / 1.01
+    np.testing.assert_allclose(d.ravel(), [0.0, gp * 1e5, 0.1 * gp * 1e5], rtol=1e-14, atol=1e-6)
+
+
+@pytest.mark.parametrize("alpha", [0.0, 0.02, 0.5])
+def test_macrospin_closed_form_rkdp(alpha):
+    B, th0, ph0 = 0.05, 1.0, 0.3
+    p = _macrospin(alpha, B)
+    h, n = 2e-13, 500
+    m = llg.rkdp_fixed(p, _m0(th0, ph0), h, n)
+    np.testing.assert_allclose(m, _exact(alpha, B, th0, ph0, h * n), atol=1e-10)
+
+
+def test_larmor_frequency():
+    B = 0.1
+    p = _macrospin(0.0, B)
+    T = 2 * np.pi / (F.GAMMA0 * B / F.MU0)           # one Larmor period
+    n = 400
+    m = llg.rkdp_fixed(p, _m0(0.7, 0.0), T / n, n)
+    np.testing.assert_allclose(m, _m0(0.7, 0.0), atol=1e-9)
+
+
+def test_uniaxial_precession_frequency():
+    B, Ku, th0 = 0.02, 5e4, 0.4
+    p = _macrospin(0.0, B, Ku)
+    HK = 2 * Ku / (F.MU0 * MS)
+    w = F.GAMMA0 * (B / F.MU0 + HK * np.cos(th0))
+    t = 3.0 * 2 * np.pi / w
+    n = 600
+    m = llg.rkdp_fixed(p, _m0(th0, 0.0), t / n, n)
+    np.testing.assert_allclose(m, _m0(th0, 0.0), atol=1e-9)
+
+
+def _order(stepper, hs, T, alpha=0.1, B=0.05):
+    p = _macrospin(alpha, B)
+    errs = []
+    for h in hs:
+        n = int(round(T / h))
+        m = _m0(1.0, 0.0)
+        for k in range(n):
+            m = stepper(p, m, h, k)
+        errs.append(np.max(np.abs(m - _exact(alpha, B, 1.0, 0.0, n * h))))
+    return np.log2(errs[0] / errs[1])
+
+
+def test_convergence_orders():
+    T = 1e-10
+    assert _order(llg.euler_step, [1e-12, 5e-13], T) == pytest.approx(1.0, abs=0.15)
+    assert _order(llg.heun_step, [2e-12, 1e-12], T) == pytest.approx(2.0, abs=0.15)
+
+    def dp(p, m, h, k):
+        return llg.rkdp_stages(p, m, h)[0]
+
+    assert _order(dp, [1e-11, 5e-12], T) == pytest.approx(5.0, abs=0.3)
+
+
+def test_embedded_error_estimate_is_order_five():
+    p = _macrospin(0.1, 0.05)
+    m = _m0(1.0, 0.0)
+    e1 = llg.rkdp_stages(p, m, 4e-12)[2]
+    e2 = llg.rkdp_stages(p, m, 2e-12)[2]
+    assert np.log2(e1 / e2) == pytest.approx(5.0, abs=0.3)
+
+
+def test_adaptive_run_hits_closed_form():
+    alpha, B, th0, ph0 = 0.05, 0.05, 1.2, 0.0
+    p = _macrospin(alpha, B)
+    st = llg.Stepper(p, _m0(th0, ph0), h0=1e-13, tol=1e-9)
+    st.run_until(2e-10)
+    assert st.t == pytest.approx(2e-10, rel=1e-12)
+    np.testing.assert_allclose(st.m, _exact(alpha, B, th0, ph0, st.t), atol=100 * 1e-9)
+    assert st.accepted > 10
+
+
+def _random_film(alpha, seed=0, shape=(16, 8, 1), B=(0, 0, 0.01)):
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = shape
+    m = rng.standard_normal((3, nz, ny, nx))
+    m /= np.linalg.norm(m, axis=0)
+    p = llg.Problem(shape, (4e-9, 4e-9, 4e-9), 8.6e5, 1.3e-11, alpha, B=B)
+    return p, m
+
+
+def test_energy_never_increases_under_damping():
+    p, m = _random_film(0.5)
+    st = llg.Stepper(p, m, h0=1e-14, tol=1e-6)
+    E = [p.energy(st.m)]
+    for _ in range(40):
+        if st.step():
+            E.append(p.energy(st.m))
+    E = np.array(E)
+    scale = abs(E[0])
+    assert np.all(np.diff(E) <= 1e-6 * scale)
+    assert E[-1] < E[0]
+
+
+def test_candidate_norm_error_is_of_order_tol():
+    p, m = _random_film(0.02, seed=3)
+    h = 2e-14
+    k1 = p.rhs(m)
+    mn = m.copy()
+    ks = [k1]
+    for s in range(1, 7):
+        ms = m.copy()
+        for j, a in enumerate(llg.DP_A[s]):
+            ms = ms + h * a * ks[j]
+        ks.append(p.rhs(ms))
+    for j in range(6):
+        mn = mn + h * llg.DP_B[j] * ks[j]
+    err = llg.rkdp_stages(p, m, h)[2]
+    assert np.max(np.abs(np.linalg.norm(mn, axis=0) - 1.0)) < 10 * err + 1e-12
+
+
+def test_relax_reaches_torque_bound():
+    p, m = _random_film(1.0, seed=1, shape=(8, 4, 1))
+    E0 = p.energy(m)
+    mr, steps, tq = llg.relax(p, m, torque_tol=1e-4, tol=1e-5)
+    assert tq < 1e-4
+    assert p.torque(mr) < 1e-4
+    assert p.energy(mr) < E0
+    assert steps > 0
+
+
+def test_rkdp_refuses_thermal_noise():
+    p = llg.Problem((2, 1, 1), CELL, MS, 1e-11, 0.1, T=300.0)
+    with pytest.raises(ValueError):
+        llg.rkdp_stages(p, _m0(0.5, 0.5).repeat(2, axis=3), 1e-13)
+
+
+def test_langevin_statistics_of_thermal_macrospins():
+    # uncoupled macrospins: no exchange partner effect (A = 0), no demag
+    n = 4096
+    T, x = 300.0, 2.0
+    V = CELL[0] * CELL[1] * CELL[2]
+    B = x * F.KB * T / (MS * V)
+    dt = 0.02 / (F.GAMMA0 * B / F.MU0)
+    p = llg.Problem((n, 1, 1), CELL, MS, 0.0, 1.0, B=(0, 0, B), T=T, seed=42, demag=False)
+    m = np.zeros((3, 1, 1, n))
+    m[2] = 1.0
+    acc, cnt = 0.0, 0
+    for k in range(3000):
+        m = llg.heun_step(p, m, dt, k)
+        if k >= 500 and k % 10 == 0:
+            acc += m[2].mean()
+            cnt += 1
+    expect = 1.0 / np.tanh(x) - 1.0 / x
+    assert acc / cnt == pytest.approx(expect, abs=0.01)
