@@ -1,0 +1,351 @@
+"""Benchmark: Dormand-Prince time steps of the 1024 x 1024 x 1 film (4 x 4 x 2 nm
+cells, Ms 8e5 A/m, A 1.3e-11 J/m, Ku 5e3 J/m^3 along x, alpha 0.01, open
+boundaries -> 2048 x 2048 padded FFT, vortex-plus-noise start, applied field
+0-50 mT in a random direction).  One bench step = one adaptive RKDP step =
+6 effective-field evaluations (FFT demag + exchange + anisotropy + Zeeman + LL
+torque + stage combination) and the device-side step controller.
+
+Metric: effective-field cell-evaluations per second (all evaluations counted,
+rejected steps included), with the dominant pass compared with the HBM
+roofline.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle on this host instead (bounded sample
+of the same workload).  Under torchrun (N > 1) each rank runs an independent
+replica of the workload (the path has no data exchange between GPUs).
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "film_1024x1024"
+METRIC = "Heff cell-evals/s"
+UNIT = "cell-evals/s"
+EVALS_PER_STEP = 6
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = max(mx, float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+def _source_hash():
+    h = hashlib.sha256()
+    cdir = os.path.join(ROOT, "paper_1102_3069_gb300", "csrc")
+    for fn in sorted(os.listdir(cdir)):
+        with open(os.path.join(cdir, fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_for(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on these sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("source_hash") != _source_hash():
+            return None
+        return d["kernels"][kernel]["dram_bytes_per_launch_full_size"]
+    except Exception:
+        return None
+
+
+def algorithmic_bytes(nx, ny):
+    """Bytes each pass must move per launch (2-D open film, FP32, Sec. 3.2 pass layout)."""
+    N = nx * ny
+    px, py = 2 * nx, 2 * ny
+    hx = px // 2 + 1
+    spec = 3 * hx * ny * 8                 # half spectrum of the valid rows, complex64
+    kern = 4 * hx * (py // 2 + 1) * 4      # real kernel octant, 4 components
+    m = 12 * N
+    # local pass: spectrum + m_s + per-stage reads of m_n and earlier k's + writes of k_s, m_{s+1}
+    # stage s = 2..6: reads m_n, k_1..k_{s-1} (k2 unused from stage 6 on); stage 7: k1, k3..k6
+    reads = {2: 2, 3: 3, 4: 4, 5: 5, 6: 5, 7: 5}
+    writes = {2: 2, 3: 2, 4: 2, 5: 2, 6: 2, 7: 1}
+    loc = [spec + m + 12 * N * (reads[s] + writes[s]) for s in range(2, 8)]
+    xf = [spec + m] * 6
+    xf[0] = spec + 3 * m                   # stage 2 combines m_n + h a21 k1 and writes m_2
+    return {
+        "k_xfwd": sum(xf) / 6.0,
+        "k_yconv": float(2 * spec + kern),
+        "k_xinv_local": sum(loc) / 6.0,
+        "step": float(sum(xf) + 6 * (2 * spec + kern) + sum(loc)),
+    }
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_1102_3069_gb300 import binding as B
+    from paper_1102_3069_gb300 import inputs
+
+    ws, rank = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.cuda.current_device()
+    w = inputs.workload(WORKLOAD, seed=rank)
+    nx, ny, nz = w["shape"]
+    N = nx * ny * nz
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = B.Solver(w["shape"], w["cell"], pbc=w["pbc"], stream=stream.cuda_stream, **w["material"])
+        m = torch.from_numpy(w["m"]).cuda()
+        ctx = s.ctx
+        B.mm_load(ctx, m)
+        # warm-up (also settles the step size)
+        B.mm_advance(ctx, B.MM_RKDP, args.warmup, dt_s=1e-13, tol=1e-6)
+        st0 = B.mm_get_stats(ctx)
+        flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")    # > 129 MB L2
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(dev) as clk:
+            t_wall0 = time.perf_counter()
+            for k in range(args.steps):
+                flush.fill_(k & 0xFF)                     # evict the previous step from L2
+                ev[k][0].record(stream)
+                B.mm_advance(ctx, B.MM_RKDP, 1, dt_s=0.0, tol=1e-6)
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
+            t_wall = time.perf_counter() - t_wall0
+        st1 = B.mm_get_stats(ctx)
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+        gpu_ms = sum(step_ms)
+        evals = st1["evals"] - st0["evals"]
+        sim_t = st1["t"] - st0["t"]
+        assert st1["status"] == 0, st1
+
+        # per-pass durations over a second timed region of the same steps
+        passes = B.pass_times(ctx, lambda: B.mm_advance(ctx, B.MM_RKDP, args.steps, dt_s=0.0, tol=1e-6))
+
+        # end to end through the host-buffer entry point: H2D + step + D2H per step
+        mh = torch.from_numpy(w["m"]).pin_memory()
+        mh_np = mh.numpy()
+        B.mm_run_host(ctx, mh_np, B.MM_RKDP, 1, dt_s=1e-13, tol=1e-6)
+        torch.cuda.synchronize()
+        e0 = B.mm_get_stats(ctx)["evals"]
+        ke = max(3, args.steps // 2)
+        te = time.perf_counter()
+        ev_total = 0
+        for _ in range(ke):
+            B.mm_run_host(ctx, mh_np, B.MM_RKDP, 1, dt_s=0.0, tol=1e-6)
+            ev_total += B.mm_get_stats(ctx)["evals"]
+        te = time.perf_counter() - te
+        del e0
+
+    value_local = evals * N / (gpu_ms * 1e-3)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([gpu_ms, float(evals * N)], device="cuda", dtype=torch.float64)
+        mx = t.clone()
+        dist.all_reduce(mx[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        gpu_ms_max, total_cells = float(mx[0]), float(t[1])
+        value = total_cells / (gpu_ms_max * 1e-3)
+    else:
+        gpu_ms_max, value = gpu_ms, value_local
+    if rank != 0:
+        return None
+
+    hbm, peak_kind = _peaks()
+    ab = algorithmic_bytes(nx, ny)
+    dom = max(("k_xfwd", "k_yconv", "k_xinv_local"), key=lambda k: passes.get(k, {}).get("ms_per_launch", 0.0))
+    dms = passes[dom]["ms_per_launch"]
+    achieved = ab[dom] / (dms * 1e-3) / 1e9
+    step_bytes = ab["step"]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": gpu_ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded vortex-plus-noise state, random applied field)",
+        "config": {"workload": WORKLOAD, "grid": [nx, ny, nz], "cell_nm": [4, 4, 2], "fft": [2 * nx, 2 * ny],
+                   "method": "RKDP adaptive, tol 1e-6", "evals_per_step": EVALS_PER_STEP,
+                   "l2": "flushed between timed steps (256 MB write, outside the events)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": _traffic_for(dom), "kernel": dom, "peak_source": peak_kind,
+                     "bytes_per_launch": ab[dom], "ms_per_launch": dms},
+        "step_roofline": {"bytes_per_step": step_bytes, "achieved_gbs": step_bytes / (gpu_ms / args.steps * 1e-3) / 1e9,
+                          "frac": step_bytes / (gpu_ms / args.steps * 1e-3) / 1e9 / hbm},
+        "passes": passes,
+        "ns_simulated_per_hour": sim_t * 1e9 / (t_wall / 3600.0) if t_wall > 0 else None,
+        "clocks": clk.summary(),
+        "gpu_launches": int(args.steps * (3 * EVALS_PER_STEP)),
+        "e2e": {"value": ev_total * N / te if te > 0 else None, "unit": UNIT,
+                "h2d_bytes_per_step": 12 * N, "d2h_bytes_per_step": 12 * N,
+                "note": "mm_run_host: pinned host m in, one RKDP step (7 evaluations: fresh k1 + 6), m out"},
+    }
+    return line
+
+
+def run_reference(args):
+    """Time the FP64 oracle (as it stands) on this host on a bounded sample."""
+    import numpy as np
+
+    from oracle import llg
+    from paper_1102_3069_gb300 import inputs
+
+    ws, rank = _dist()
+    if rank != 0:
+        return None
+    w = inputs.workload(WORKLOAD, seed=0)
+    mat = w["material"]
+    t0 = time.perf_counter()
+    p = llg.Problem(w["shape"], w["cell"], mat["Ms"], mat["Aex"], mat["alpha"], Ku=mat["Ku"], u=mat["easy_axis"],
+                    B=mat["B"])
+    setup_s = time.perf_counter() - t0
+    m = w["m"].astype(np.float64)
+    N = int(np.prod(w["shape"]))
+    # one sample = one Heff evaluation of the full grid with its LL right-hand side
+    for _ in range(args.warmup):
+        p.rhs(m)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        p.rhs(m)
+    dt = time.perf_counter() - t
+    value = args.steps * N / dt
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "grid": list(w["shape"]), "sample": "one full-grid H_eff + LL rhs per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} full-grid H_eff evaluations of {WORKLOAD} (kernel setup "
+                                       f"{setup_s:.0f} s untimed)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def cpu_baseline_sample(seconds=20.0):
+    """Oracle on a bounded sample of the same workload (rank 0, N = 1 only)."""
+    import numpy as np
+
+    from oracle import llg
+    from paper_1102_3069_gb300 import inputs
+
+    w = inputs.workload(WORKLOAD, seed=0)
+    mat = w["material"]
+    p = llg.Problem(w["shape"], w["cell"], mat["Ms"], mat["Aex"], mat["alpha"], Ku=mat["Ku"], u=mat["easy_axis"],
+                    B=mat["B"])
+    m = w["m"].astype(np.float64)
+    N = int(np.prod(w["shape"]))
+    n = 0
+    t = time.perf_counter()
+    while time.perf_counter() - t < seconds or n < 2:
+        p.rhs(m)
+        n += 1
+    dt = time.perf_counter() - t
+    return {"value": n * N / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} full-grid H_eff evaluations (FP64 numpy, one thread) of {WORKLOAD}"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        if args.steps > 5:
+            args.steps = 5
+        if args.warmup > 1:
+            args.warmup = 1
+        line = run_reference(args)
+        if line:
+            print(json.dumps(line))
+        return
+    import __graft_entry__
+    from paper_1102_3069_gb300 import binding
+    if not os.path.exists(binding.LIB_PATH):
+        __graft_entry__.build()
+    line = run_gpu(args)
+    if line is None:
+        return
+    ws, _ = _dist()
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample()
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

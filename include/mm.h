@@ -1,0 +1,220 @@
+/*
+ * mm.h - C ABI of libmm: effective-field evaluation and Landau-Lifshitz time
+ * stepping of a finite-difference micromagnetic grid on one GB300 GPU.
+ *
+ * Method: A. Vansteenkiste and B. Van de Wiele, "MuMax: a new high-performance
+ * micromagnetic simulation tool", arXiv:1102.3069 (2011).
+ *
+ * General conventions (apply to every call below)
+ *  - Magnetisation arrays are reduced m = M/Ms, float32, structure-of-arrays
+ *    [3][nz][ny][nx] (component, z, y, x; x fastest), contiguous, 3*nx*ny*nz
+ *    floats, in DEVICE memory owned by the caller.  Only mm_*_host calls take
+ *    host pointers.
+ *  - All device work is issued on the stream given to mm_init_geometry and is
+ *    asynchronous, except calls that return host scalars (they synchronise that
+ *    stream before returning).
+ *  - The library never allocates device memory.  The caller allocates one
+ *    workspace of mm_workspace_bytes() bytes and hands it over with
+ *    mm_set_workspace(); it must stay valid until mm_destroy().
+ *  - SI units at the boundary (m, s, A/m, J/m, J/m^3, T, K).  Internally the
+ *    library works in units with field unit Ms and time unit 1/(gamma0 Ms)
+ *    (the paper's Sec. 3.3 keeps mu0 = gamma0 = Ms = 1 for single precision).
+ *  - Return value: MM_OK (0) or a negative mm_status; a message describing the
+ *    last failure is available from mm_last_error().  Nothing is thrown across
+ *    the ABI.  A failed call leaves the context usable unless it returns
+ *    MM_ECUDA.
+ */
+#ifndef MM_H
+#define MM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mm_ctx mm_ctx;   /* opaque; created by mm_init_geometry, freed by mm_destroy */
+
+typedef enum {
+    MM_OK = 0,
+    MM_EINVAL = -1,          /* bad argument or call order                          */
+    MM_ENOMEM = -2,          /* workspace too small / not set                       */
+    MM_ECUDA = -3,           /* a CUDA runtime call failed                          */
+    MM_ENOTCONVERGED = -4,   /* step size underflow or step budget exhausted        */
+    MM_ENONFINITE = -5,      /* NaN/Inf met in m, H or the step error               */
+    MM_ETIMEOUT = -6,        /* a bounded wait ran out                              */
+    MM_ESTATE = -7           /* operation needs state that is not there yet         */
+} mm_status;
+
+/* Time integrators of Sec. 2.2 (values are the Runge-Kutta order names). */
+enum { MM_EULER = 1, MM_HEUN = 2, MM_RKDP = 5 };
+
+typedef struct mm_stats {
+    long long evals;        /* H_eff evaluations issued since the last mm_load      */
+    long long accepted;     /* accepted steps                                       */
+    long long rejected;     /* rejected (adaptive) steps                            */
+    long long step_index;   /* thermal-noise step counter                           */
+    double t;               /* simulated time, s                                    */
+    double dt;              /* next proposed step (RKDP) or last fixed step, s      */
+    double last_err;        /* last step-error estimate (dimensionless, |dm|)       */
+    double max_torque;      /* max_i |m_i x H_i|/Ms at the last accepted state      */
+    double energy;          /* last energy computed by mm_eval_heff, J              */
+    int status;             /* device-side status: 0 or a negative mm_status        */
+    int done;               /* 1 when t_end / torque target reached or on failure   */
+} mm_stats;
+
+/*
+ * Create a context for an nx x ny x nz grid of dx x dy x dz cuboid cells
+ * (Sec. 2.1.1: regular finite-difference grid of identical cuboids).
+ * pbc_x/y/z != 0 makes that axis periodic (Sec. 2.1.1, periodic boundary
+ * conditions: periodic images added to the kernel, no zero padding);
+ * pbc_images = number of images on each side of a periodic axis (>= 0).
+ * Open axes are zero padded to the next power of two >= 2n-1; a periodic axis
+ * needs n to be a power of two.  nx, ny, nz in [1, 2048] for open axes
+ * (padded length <= 4096) and [1, 4096] for periodic ones.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * On success *out owns host memory only; free it with mm_destroy.
+ */
+int mm_init_geometry(mm_ctx** out, int nx, int ny, int nz, double dx, double dy, double dz,
+                     int pbc_x, int pbc_y, int pbc_z, int pbc_images, void* cuda_stream);
+
+/* Device workspace size in bytes for this geometry (kernel, spectra, RK stages). */
+size_t mm_workspace_bytes(const mm_ctx* ctx);
+
+/* Hand over the caller-owned device workspace (256-byte aligned, >= mm_workspace_bytes).
+ * Uploads the twiddle table and clears the device state; synchronises the stream. */
+int mm_set_workspace(mm_ctx* ctx, void* dev_ptr, size_t bytes);
+
+/*
+ * Material parameters (Sec. 2, Eq. 1 and Sec. 2.1): saturation magnetisation
+ * Ms (A/m, > 0), exchange stiffness Aex (J/m, >= 0; Eq. 3), uniaxial constant
+ * Ku (J/m^3; Eq. 4) with easy axis easy_axis[3] (normalised here; may be
+ * NULL when Ku == 0), damping alpha (>= 0), gyromagnetic ratio gamma0
+ * (m/(A s), > 0; pass 0 for 2.211e5), temperature (K, >= 0; Eq. 6) with the
+ * Philox seed of the thermal noise, applied flux density B_applied_T[3] (T).
+ * The applied field enters as H = B/mu0.
+ */
+int mm_set_material(mm_ctx* ctx, double Ms, double Aex, double Ku, const double easy_axis[3],
+                    double alpha, double gamma0, double temperature, uint64_t seed,
+                    const double B_applied_T[3]);
+
+/*
+ * Enable (1) or disable (0) the magnetostatic term.  Enabled by default; when
+ * enabled, mm_demag_kernel must have run before any evaluation.  Disabling it
+ * leaves exchange, anisotropy, Zeeman and thermal terms (used for uncoupled
+ * macrospin ensembles and for testing the local terms alone).
+ */
+int mm_set_demag(mm_ctx* ctx, int enabled);
+
+/*
+ * Build the demagnetising kernel (Sec. 2.1.1 Eq. 2; Sec. 3.2: symmetric
+ * kernel whose transform is real): the cell-averaged tensor N_ab of every
+ * source-target offset is computed in FP64 on the GPU (closed form near the
+ * origin, tent-weighted Gauss-Legendre quadrature of the dipole kernel far
+ * away; periodic images summed), wrapped into the padded grid, transformed
+ * with an FP64 FFT, and its real part times -1/(Px Py Pz) stored in float32
+ * on the non-negative-frequency octant.  Uses the workspace's stage buffers as
+ * scratch (so it invalidates any loaded state).  Synchronises the stream.
+ * out_tensor_host: optional (may be NULL) host buffer of
+ *   6 * Oz * Oy * Ox doubles receiving the real-space tensor on the
+ *   non-negative offsets, components in the order xx, yy, zz, xy, xz, yz,
+ *   layout [comp][oz][oy][ox]; O = n for an open axis, n/2+1 for a periodic
+ *   one (periodic entries hold the image sums).
+ */
+int mm_demag_kernel(mm_ctx* ctx, double* out_tensor_host);
+
+/* Number of doubles mm_demag_kernel writes to out_tensor_host. */
+size_t mm_demag_tensor_len(const mm_ctx* ctx);
+
+/*
+ * One effective-field evaluation (Sec. 2.1: H_eff = H_ms + H_exch + H_anis +
+ * H_applied + H_thermal) at the given m (not renormalised).
+ *   m          device, [3][nz][ny][nx] float32 (read only)
+ *   h_out      device, same layout, H_eff in A/m (may be NULL)
+ *   torque_out device, same layout, dm/dt of Eq. 1 divided by Ms in 1/s (may be NULL)
+ *   energy_J_host  host double receiving the total energy in J (thermal field
+ *              excluded); may be NULL.  Non-NULL synchronises the stream.
+ * The thermal term uses the clock set by mm_set_thermal_clock.
+ */
+int mm_eval_heff(mm_ctx* ctx, const float* m, float* h_out, float* torque_out, double* energy_J_host);
+
+/* Thermal-noise clock used by mm_eval_heff: step index and the step dt (s) of Eq. 6. */
+int mm_set_thermal_clock(mm_ctx* ctx, uint64_t step_index, double dt_s);
+
+/*
+ * Load m (device, float32 SoA) as the integrator state, normalised to |m| = 1,
+ * set the simulated time to t0_s and the step counter to step_index.  The
+ * derivative reused by the first-same-as-last property is invalidated.
+ */
+int mm_load(mm_ctx* ctx, const float* m, double t0_s, uint64_t step_index);
+
+/* Copy the current state m (device) out.  Asynchronous. */
+int mm_store(mm_ctx* ctx, float* m);
+
+/*
+ * Enqueue nsteps time steps on the stream without waiting (device-side step
+ * control, Sec. 2.2).  method = MM_EULER or MM_HEUN with the fixed step
+ * dt_s > 0; or MM_RKDP (Dormand-Prince 5(4), adaptive, first same as last)
+ * with per-step error bound tol (max over cells of |dm|) and the proposed
+ * step dt_s (> 0 sets it; <= 0 keeps the current one, 100 fs after mm_load).
+ * tol < 0 selects fixed Dormand-Prince steps of dt_s (no step control; the
+ * error estimate is still computed and reported).  t_end_s > 0 stops the
+ * run exactly at t_end_s (the last step is shortened); torque_tol > 0 stops
+ * it once max |m x H|/Ms < torque_tol (relaxation).  Once stopped, queued
+ * steps do no work.  The thermal field (T > 0) needs MM_EULER or MM_HEUN.
+ */
+int mm_advance(mm_ctx* ctx, int method, long nsteps, double dt_s, double tol,
+               double t_end_s, double torque_tol);
+
+/* Synchronise the stream and read the device-side counters (stats may be NULL). */
+int mm_get_stats(mm_ctx* ctx, mm_stats* stats);
+
+/*
+ * One step (Sec. 2.2) from m (device, in/out): loads m at time *t_s, takes
+ * one step of `method` with the proposed/fixed step *dt_s (and error bound
+ * tol for MM_RKDP), stores the result back into m and synchronises.
+ * On return *accepted = 1/0, *t_s is the new time and *dt_s the next step.
+ */
+int mm_step(mm_ctx* ctx, float* m, int method, double* t_s, double* dt_s, double tol, int* accepted);
+
+/*
+ * Relax m (device, in/out) with adaptive Dormand-Prince until
+ * max_i |m_i x H_i|/Ms < torque_tol or max_steps attempted steps; err_tol is
+ * the per-step error bound.  The host polls the device every 64 steps.
+ * Returns MM_ENOTCONVERGED if the torque bound was not reached.
+ */
+int mm_relax(mm_ctx* ctx, float* m, double torque_tol, double err_tol, long max_steps,
+             long* steps_out, double* torque_out);
+
+/*
+ * Host-buffer variant for callers without device memory: copies m_host
+ * (pinned or pageable host, [3][nz][ny][nx] float32) to the device, runs
+ * nsteps as mm_advance would, and copies the result back into m_host.
+ * Synchronises the stream.
+ */
+int mm_run_host(mm_ctx* ctx, float* m_host, int method, long nsteps, double dt_s, double tol);
+
+/*
+ * Per-pass timing (a diagnostic with no counterpart in the paper).  While
+ * enabled, every kernel launch of mm_eval_heff / mm_advance is bracketed by
+ * CUDA events on the context's stream.  mm_pass_times synchronises and returns,
+ * per pass, the summed event time in ms and the number of launches since
+ * mm_profile(ctx, 1); arrays of MM_NPASS entries in the order
+ * x forward, y conv (2-D), y forward, z conv, y inverse (3-D), x inverse +
+ * local terms, stage-2 combine, local terms without demag.
+ */
+enum { MM_NPASS = 8 };
+int mm_profile(mm_ctx* ctx, int enable);
+int mm_pass_times(mm_ctx* ctx, double* ms_out, long long* count_out);
+
+/* Message describing the last failure of a call on this context (never NULL). */
+const char* mm_last_error(const mm_ctx* ctx);
+
+/* Free the context (not the caller's workspace).  NULL is accepted. */
+void mm_destroy(mm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MM_H */

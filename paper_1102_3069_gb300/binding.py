@@ -1,0 +1,300 @@
+"""Thin ctypes binding of libmm.so (include/mm.h): same names, argument marshalling only.
+
+Every numerical step runs in the CUDA kernels of ``csrc/``; this module only
+converts Python/torch arguments into the plain pointers and sizes of the C ABI.
+If the shared library has not been built the first call raises - there is no
+fallback of any kind.
+
+``Solver`` is a convenience owner of one context: it allocates the device
+workspace with torch (the library itself never allocates device memory) and
+forwards to the mm_* calls.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmm.so")
+
+MM_OK, MM_EINVAL, MM_ENOMEM, MM_ECUDA = 0, -1, -2, -3
+MM_ENOTCONVERGED, MM_ENONFINITE, MM_ETIMEOUT, MM_ESTATE = -4, -5, -6, -7
+MM_EULER, MM_HEUN, MM_RKDP = 1, 2, 5
+
+STATUS_NAMES = {0: "MM_OK", -1: "MM_EINVAL", -2: "MM_ENOMEM", -3: "MM_ECUDA", -4: "MM_ENOTCONVERGED",
+                -5: "MM_ENONFINITE", -6: "MM_ETIMEOUT", -7: "MM_ESTATE"}
+
+
+class MMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class mm_stats(ctypes.Structure):
+    _fields_ = [("evals", ctypes.c_longlong), ("accepted", ctypes.c_longlong), ("rejected", ctypes.c_longlong),
+                ("step_index", ctypes.c_longlong), ("t", ctypes.c_double), ("dt", ctypes.c_double),
+                ("last_err", ctypes.c_double), ("max_torque", ctypes.c_double), ("energy", ctypes.c_double),
+                ("status", ctypes.c_int), ("done", ctypes.c_int)]
+
+
+_lib = None
+_vp, _dp, _i, _l, _d, _sz, _u64 = (ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_long,
+                                   ctypes.c_double, ctypes.c_size_t, ctypes.c_uint64)
+
+_SIGS = {
+    "mm_init_geometry": (_i, [ctypes.POINTER(_vp), _i, _i, _i, _d, _d, _d, _i, _i, _i, _i, _vp]),
+    "mm_workspace_bytes": (_sz, [_vp]),
+    "mm_set_workspace": (_i, [_vp, _vp, _sz]),
+    "mm_set_material": (_i, [_vp, _d, _d, _d, _dp, _d, _d, _d, _u64, _dp]),
+    "mm_set_demag": (_i, [_vp, _i]),
+    "mm_demag_kernel": (_i, [_vp, _dp]),
+    "mm_demag_tensor_len": (_sz, [_vp]),
+    "mm_eval_heff": (_i, [_vp, _vp, _vp, _vp, _dp]),
+    "mm_set_thermal_clock": (_i, [_vp, _u64, _d]),
+    "mm_load": (_i, [_vp, _vp, _d, _u64]),
+    "mm_store": (_i, [_vp, _vp]),
+    "mm_advance": (_i, [_vp, _i, _l, _d, _d, _d, _d]),
+    "mm_get_stats": (_i, [_vp, ctypes.POINTER(mm_stats)]),
+    "mm_step": (_i, [_vp, _vp, _i, _dp, _dp, _d, ctypes.POINTER(_i)]),
+    "mm_relax": (_i, [_vp, _vp, _d, _d, _l, ctypes.POINTER(_l), _dp]),
+    "mm_run_host": (_i, [_vp, _vp, _i, _l, _d, _d]),
+    "mm_profile": (_i, [_vp, _i]),
+    "mm_pass_times": (_i, [_vp, _dp, ctypes.POINTER(ctypes.c_longlong)]),
+    "mm_last_error": (ctypes.c_char_p, [_vp]),
+    "mm_destroy": (None, [_vp]),
+}
+
+
+def lib():
+    """Load libmm.so (built in-tree by ``__graft_entry__.build()``); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                               "(there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _ptr(x):
+    """Device/host pointer of a torch tensor, a numpy array or an int address."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _check(ctx, rc):
+    if rc != MM_OK:
+        msg = lib().mm_last_error(ctx)
+        raise MMError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _d3(v):
+    if v is None:
+        return None
+    a = (ctypes.c_double * 3)(*[float(x) for x in v])
+    return ctypes.cast(a, _dp), a
+
+
+# ---- one-to-one wrappers (same names as the C ABI) --------------------------
+
+def mm_init_geometry(nx, ny, nz, dx, dy, dz, pbc=(0, 0, 0), pbc_images=10, stream=None):
+    ctx = _vp()
+    rc = lib().mm_init_geometry(ctypes.byref(ctx), int(nx), int(ny), int(nz), float(dx), float(dy), float(dz),
+                                int(bool(pbc[0])), int(bool(pbc[1])), int(bool(pbc[2])), int(pbc_images),
+                                _vp(stream) if stream else None)
+    if rc != MM_OK:
+        raise MMError(rc, "mm_init_geometry rejected the geometry")
+    return ctx
+
+
+def mm_workspace_bytes(ctx):
+    return int(lib().mm_workspace_bytes(ctx))
+
+
+def mm_set_workspace(ctx, dev_ptr, nbytes):
+    return _check(ctx, lib().mm_set_workspace(ctx, _ptr(dev_ptr), int(nbytes)))
+
+
+def mm_set_material(ctx, Ms, Aex, Ku=0.0, easy_axis=(1.0, 0.0, 0.0), alpha=0.02, gamma0=0.0, temperature=0.0,
+                    seed=0, B=(0.0, 0.0, 0.0)):
+    u, _keep_u = _d3(easy_axis) if easy_axis is not None else (None, None)
+    b, _keep_b = _d3(B)
+    return _check(ctx, lib().mm_set_material(ctx, float(Ms), float(Aex), float(Ku), u, float(alpha), float(gamma0),
+                                             float(temperature), int(seed) & 0xFFFFFFFFFFFFFFFF, b))
+
+
+def mm_set_demag(ctx, enabled):
+    return _check(ctx, lib().mm_set_demag(ctx, int(bool(enabled))))
+
+
+def mm_demag_tensor_len(ctx):
+    return int(lib().mm_demag_tensor_len(ctx))
+
+
+def mm_demag_kernel(ctx, dump=False):
+    """Build the kernel; with dump=True return the FP64 real-space octant as numpy."""
+    if dump:
+        out = np.zeros(mm_demag_tensor_len(ctx), dtype=np.float64)
+        _check(ctx, lib().mm_demag_kernel(ctx, out.ctypes.data_as(_dp)))
+        return out
+    _check(ctx, lib().mm_demag_kernel(ctx, None))
+    return None
+
+
+def mm_eval_heff(ctx, m, h_out=None, torque_out=None, energy=False):
+    e = ctypes.c_double(0.0)
+    _check(ctx, lib().mm_eval_heff(ctx, _ptr(m), _ptr(h_out), _ptr(torque_out), ctypes.byref(e) if energy else None))
+    return e.value if energy else None
+
+
+def mm_set_thermal_clock(ctx, step_index, dt_s):
+    return _check(ctx, lib().mm_set_thermal_clock(ctx, int(step_index), float(dt_s)))
+
+
+def mm_load(ctx, m, t0_s=0.0, step_index=0):
+    return _check(ctx, lib().mm_load(ctx, _ptr(m), float(t0_s), int(step_index)))
+
+
+def mm_store(ctx, m):
+    return _check(ctx, lib().mm_store(ctx, _ptr(m)))
+
+
+def mm_advance(ctx, method, nsteps, dt_s=0.0, tol=1e-6, t_end_s=0.0, torque_tol=0.0):
+    return _check(ctx, lib().mm_advance(ctx, int(method), int(nsteps), float(dt_s), float(tol), float(t_end_s),
+                                        float(torque_tol)))
+
+
+def mm_get_stats(ctx):
+    s = mm_stats()
+    _check(ctx, lib().mm_get_stats(ctx, ctypes.byref(s)))
+    return {f: getattr(s, f) for f, _ in mm_stats._fields_}
+
+
+def mm_step(ctx, m, method, t_s, dt_s, tol=1e-6):
+    t = ctypes.c_double(t_s)
+    dt = ctypes.c_double(dt_s)
+    acc = ctypes.c_int(0)
+    _check(ctx, lib().mm_step(ctx, _ptr(m), int(method), ctypes.byref(t), ctypes.byref(dt), float(tol),
+                              ctypes.byref(acc)))
+    return bool(acc.value), t.value, dt.value
+
+
+def mm_relax(ctx, m, torque_tol=1e-4, err_tol=1e-5, max_steps=100000):
+    steps = ctypes.c_long(0)
+    tq = ctypes.c_double(0.0)
+    rc = lib().mm_relax(ctx, _ptr(m), float(torque_tol), float(err_tol), int(max_steps), ctypes.byref(steps),
+                        ctypes.byref(tq))
+    _check(ctx, rc)
+    return steps.value, tq.value
+
+
+def mm_run_host(ctx, m_host, method, nsteps, dt_s=0.0, tol=1e-6):
+    return _check(ctx, lib().mm_run_host(ctx, _ptr(m_host), int(method), int(nsteps), float(dt_s), float(tol)))
+
+
+PASS_NAMES = ["k_xfwd", "k_yconv", "k_yfwd", "k_zconv", "k_yinv", "k_xinv_local", "k_combine2", "k_local"]
+
+
+def mm_profile(ctx, enable):
+    return _check(ctx, lib().mm_profile(ctx, int(bool(enable))))
+
+
+def mm_pass_times(ctx):
+    ms = (ctypes.c_double * 8)()
+    n = (ctypes.c_longlong * 8)()
+    _check(ctx, lib().mm_pass_times(ctx, ms, n))
+    return {PASS_NAMES[i]: {"ms_total": ms[i], "launches": n[i],
+                            "ms_per_launch": ms[i] / n[i] if n[i] else 0.0} for i in range(8) if n[i]}
+
+
+def pass_times(ctx, fn):
+    """Run fn() with per-pass event timing on and return mm_pass_times."""
+    mm_profile(ctx, True)
+    try:
+        fn()
+        return mm_pass_times(ctx)
+    finally:
+        mm_profile(ctx, False)
+
+
+def mm_last_error(ctx):
+    msg = lib().mm_last_error(ctx)
+    return msg.decode() if msg else ""
+
+
+def mm_destroy(ctx):
+    lib().mm_destroy(ctx)
+
+
+# ---- convenience owner ------------------------------------------------------
+
+class Solver:
+    """One geometry + material on the current CUDA device; workspace from torch.
+
+    shape = (nx, ny, nz), cell = (dx, dy, dz) in m; material keywords as in
+    mm_set_material.  ``demag=False`` disables the magnetostatic term.
+    """
+
+    def __init__(self, shape, cell, pbc=(0, 0, 0), images=10, demag=True, stream=None, **material):
+        import torch
+        self.torch = torch
+        self.shape = tuple(int(v) for v in shape)
+        self.cell = tuple(float(v) for v in cell)
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = stream
+        self.ctx = mm_init_geometry(*self.shape, *self.cell, pbc, images, stream)
+        nbytes = mm_workspace_bytes(self.ctx)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        mm_set_workspace(self.ctx, aligned, nbytes)
+        mm_set_material(self.ctx, **material)
+        mm_set_demag(self.ctx, demag)
+        self.tensor = None
+        if demag:
+            self.tensor = mm_demag_kernel(self.ctx, dump=True)
+
+    @property
+    def mshape(self):
+        nx, ny, nz = self.shape
+        return (3, nz, ny, nx)
+
+    def set_material(self, **material):
+        mm_set_material(self.ctx, **material)
+
+    def heff(self, m, torque=False, energy=False):
+        h = self.torch.empty_like(m)
+        tq = self.torch.empty_like(m) if torque else None
+        e = mm_eval_heff(self.ctx, m, h, tq, energy)
+        return h, tq, e
+
+    def close(self):
+        if self.ctx is not None:
+            mm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,655 @@
+// api.cu - the C ABI of include/mm.h: context, workspace layout, argument
+// checks and the order of kernel launches for an evaluation or a step.
+#include "mm.h"
+#include "mm_internal.cuh"
+#include "fft32.cuh"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+namespace {
+
+constexpr double MU0 = 4.0e-7 * M_PI;
+constexpr double KB = 1.380649e-23;
+constexpr double DEFAULT_GAMMA0 = 2.211e5;
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+int ilog2(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
+int next_pow2(int v) { int p = 1; while (p < v) p <<= 1; return p; }
+
+// Gauss-Legendre nodes/weights on [-1, 1] (Newton iteration on P_n)
+void gauss_legendre(int n, double* t, double* w) {
+    for (int i = 0; i < n; ++i) {
+        double x = cos(M_PI * (i + 0.75) / (n + 0.5));
+        double dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (x * p1 - p0) / (x * x - 1.0);
+            const double dx = p1 / dp;
+            x -= dx;
+            if (fabs(dx) < 1e-16) break;
+        }
+        t[i] = x;
+        w[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+    }
+}
+
+}  // namespace
+
+struct mm_ctx {
+    // geometry
+    int nx = 0, ny = 0, nz = 0;
+    double dx = 0, dy = 0, dz = 0;
+    int pbc[3] = {0, 0, 0};
+    int images = 0;
+    int px = 1, py = 1, pz = 1, logpx = 0, logpy = 0, logpz = 0;
+    int hx = 1, hyk = 1, hzk = 1, nyp = 16, nzp = 1, ty = 2, tz = 1, tky = 1, kxb = 1, ncomp = 4;
+    int ox = 1, oy = 1, oz = 1;
+    long long ncell = 0;
+    cudaStream_t stream = nullptr;
+    // material
+    bool have_material = false;
+    double Ms = 0, Aex = 0, Ku = 0, u[3] = {1, 0, 0}, alpha = 0, gamma0 = DEFAULT_GAMMA0, T = 0;
+    uint64_t seed = 0;
+    double B[3] = {0, 0, 0};
+    bool demag = true;
+    bool kernel_ready = false;
+    // workspace
+    char* ws = nullptr;
+    size_t ws_size = 0;
+    size_t off_st = 0, off_tw = 0, off_kt = 0, off_s1 = 0, off_s2 = 0, off_union = 0;
+    size_t sz_kt = 0, sz_s1 = 0, sz_s2 = 0, sz_rk = 0, sz_setup = 0, total = 0;
+    // integrator bookkeeping
+    bool state_loaded = false;
+    bool k1_valid = false;
+    bool rk_h_set = false;          // an RKDP step size has been given since mm_load
+    int last_method = 0;
+    double last_fixed_dt = 0.0;     // internal units
+    long long step_counter = 0;
+    uint64_t th_step = 0;
+    double th_dt = 0.0;            // seconds
+    std::vector<float2> tw_host;
+    std::string err;
+    // per-pass event timing (mm_profile / mm_pass_times)
+    struct Rec { int pass; cudaEvent_t a, b; };
+    bool profiling = false;
+    std::vector<Rec> prof;
+    double pass_ms[mm::NPASS] = {0};
+    long long pass_n[mm::NPASS] = {0};
+};
+
+namespace {
+
+int fail(mm_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_fail(mm_ctx* c, cudaError_t e, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(c, MM_ECUDA, m);
+}
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);   \
+    } while (0)
+
+void layout(mm_ctx* c) {
+    const long long n3 = 3 * c->ncell;
+    c->sz_kt = (size_t)c->ncomp * c->hx * c->hyk * c->hzk * sizeof(float);
+    c->sz_s1 = (size_t)3 * c->hx * c->nz * c->nyp * sizeof(float2);
+    c->sz_s2 = c->nz > 1 ? (size_t)3 * c->hx * c->py * c->nzp * sizeof(float2) : 0;
+    // ms[2], ks[2], k2..k6, mstage[2]: 11 arrays of 3*ncell floats
+    c->sz_rk = 11 * align256((size_t)n3 * sizeof(float));
+    c->sz_setup = align256((size_t)6 * c->ox * c->oy * c->oz * sizeof(double)) +
+                  align256((size_t)c->px * c->py * c->pz * sizeof(double2));
+    size_t off = 0;
+    c->off_st = off; off += align256(sizeof(mm::DevState));
+    c->off_tw = off; off += align256((size_t)mmfft::TWN * sizeof(float2));
+    c->off_kt = off; off += align256(c->sz_kt);
+    c->off_s1 = off; off += align256(c->sz_s1);
+    c->off_s2 = off; off += align256(c->sz_s2);
+    c->off_union = off; off += (c->sz_rk > c->sz_setup ? c->sz_rk : c->sz_setup);
+    c->total = off;
+}
+
+mm::DevState* dstate(mm_ctx* c) { return reinterpret_cast<mm::DevState*>(c->ws + c->off_st); }
+float* rk_array(mm_ctx* c, int i) {
+    const size_t each = align256((size_t)3 * c->ncell * sizeof(float));
+    return reinterpret_cast<float*>(c->ws + c->off_union + i * each);
+}
+
+int check_ready(mm_ctx* ctx, bool need_kernel) {
+    if (!ctx) return MM_EINVAL;
+    if (!ctx->ws) return fail(ctx, MM_ENOMEM, "workspace not set (mm_set_workspace)");
+    if (!ctx->have_material) return fail(ctx, MM_ESTATE, "material not set (mm_set_material)");
+    if (need_kernel && ctx->demag && !ctx->kernel_ready)
+        return fail(ctx, MM_ESTATE, "demag kernel not built (mm_demag_kernel) or demag not disabled");
+    return MM_OK;
+}
+
+mm::HotParams hot_params(mm_ctx* c, double dt_internal, bool thermal) {
+    mm::HotParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.nx = c->nx; p.ny = c->ny; p.nz = c->nz;
+    p.px = c->px; p.py = c->py; p.pz = c->pz;
+    p.logpx = c->logpx; p.logpy = c->logpy; p.logpz = c->logpz;
+    p.hx = c->hx; p.hyk = c->hyk; p.hzk = c->hzk;
+    p.nyp = c->nyp; p.nzp = c->nzp;
+    p.ty = c->ty; p.tz = c->tz; p.tky = c->tky; p.kxb = c->kxb;
+    for (int i = 0; i < 3; ++i) p.pbc[i] = c->pbc[i];
+    p.ncomp = c->ncomp;
+    p.ncell = c->ncell;
+    const double Ms = c->Ms;
+    const double ex = 2.0 * c->Aex / (MU0 * Ms * Ms);
+    p.cex[0] = (float)(ex / (c->dx * c->dx));
+    p.cex[1] = (float)(ex / (c->dy * c->dy));
+    p.cex[2] = (float)(ex / (c->dz * c->dz));
+    p.kan = (float)(2.0 * c->Ku / (MU0 * Ms * Ms));
+    p.ux = (float)c->u[0]; p.uy = (float)c->u[1]; p.uz = (float)c->u[2];
+    p.hzx = (float)(c->B[0] / (MU0 * Ms));
+    p.hzy = (float)(c->B[1] / (MU0 * Ms));
+    p.hzz = (float)(c->B[2] / (MU0 * Ms));
+    p.alpha = (float)c->alpha;
+    p.llpref = (float)(1.0 / (1.0 + c->alpha * c->alpha));
+    p.seed = c->seed;
+    p.demag = c->demag ? 1 : 0;
+    p.dt_d = dt_internal;
+    if (thermal && c->T > 0.0 && dt_internal > 0.0) {
+        const double dt_s = dt_internal / (c->gamma0 * Ms);
+        const double V = c->dx * c->dy * c->dz;
+        const double sigma = std::sqrt(2.0 * c->alpha * KB * c->T / (c->gamma0 * MU0 * Ms * V * dt_s));
+        p.sigma_th = (float)(sigma / Ms);
+    }
+    p.h_scale = (float)Ms;
+    p.t_scale = (float)(c->gamma0 * Ms);
+    p.tw = reinterpret_cast<const float2*>(c->ws + c->off_tw);
+    p.kt = reinterpret_cast<const float*>(c->ws + c->off_kt);
+    p.s1 = reinterpret_cast<float2*>(c->ws + c->off_s1);
+    p.s2 = reinterpret_cast<float2*>(c->ws + c->off_s2);
+    p.st = dstate(c);
+    p.ms[0] = rk_array(c, 0); p.ms[1] = rk_array(c, 1);
+    p.ks[0] = rk_array(c, 2); p.ks[1] = rk_array(c, 3);
+    for (int j = 2; j <= 6; ++j) p.kb[j] = rk_array(c, 2 + j);    // 4..8
+    p.mstage[0] = rk_array(c, 9); p.mstage[1] = rk_array(c, 10);
+    return p;
+}
+
+// run parameters are written by a one-thread kernel so that mm_advance stays asynchronous
+__global__ void k_set_run(mm::DevState* st, double tol, double t_end, double torque_tol, double h,
+                          double h_min, int reset_done, int fixed_h) {
+    st->tol = tol;
+    st->fixed_h = fixed_h;
+    st->t_end = t_end;
+    st->torque_tol = torque_tol;
+    if (h > 0.0) st->h = h;
+    st->h_min = h_min;
+    if (reset_done) { st->done = 0; st->status = 0; }
+    if (st->t_end > 0.0 && st->h > st->t_end - st->t) st->h = st->t_end - st->t;
+}
+
+int eval(mm_ctx* ctx, const mm::HotParams& p, int src, int mode, int stage) {
+    mm::LaunchArgs a{src, mode, stage};
+    int ids[8];
+    const int n = mm::eval_passes(p, a, ids);
+    for (int i = 0; i < n; ++i) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (ctx->profiling) {
+            CK(cudaEventCreate(&e0));
+            CK(cudaEventCreate(&e1));
+            CK(cudaEventRecord(e0, ctx->stream));
+        }
+        CK(mm::launch_pass(p, a, ids[i], ctx->stream));
+        if (ctx->profiling) {
+            CK(cudaEventRecord(e1, ctx->stream));
+            ctx->prof.push_back({ids[i], e0, e1});
+        }
+    }
+    return MM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mm_init_geometry(mm_ctx** out, int nx, int ny, int nz, double dx, double dy, double dz, int pbc_x, int pbc_y,
+                     int pbc_z, int pbc_images, void* cuda_stream) {
+    if (!out) return MM_EINVAL;
+    *out = nullptr;
+    const int n[3] = {nx, ny, nz};
+    const int pb[3] = {pbc_x != 0, pbc_y != 0, pbc_z != 0};
+    int P[3];
+    for (int a = 0; a < 3; ++a) {
+        if (n[a] < 1) return MM_EINVAL;
+        if (pb[a]) {
+            if (!is_pow2(n[a]) || n[a] > 4096) return MM_EINVAL;
+            P[a] = n[a];
+        } else {
+            if (n[a] > 2048) return MM_EINVAL;
+            P[a] = next_pow2(2 * n[a] - 1);
+        }
+    }
+    if (!(dx > 0 && dy > 0 && dz > 0) || !std::isfinite(dx) || !std::isfinite(dy) || !std::isfinite(dz))
+        return MM_EINVAL;
+    if (pbc_images < 0 || pbc_images > 1000) return MM_EINVAL;
+    mm_ctx* c = new (std::nothrow) mm_ctx();
+    if (!c) return MM_ENOMEM;
+    c->nx = nx; c->ny = ny; c->nz = nz;
+    c->dx = dx; c->dy = dy; c->dz = dz;
+    for (int a = 0; a < 3; ++a) c->pbc[a] = pb[a];
+    c->images = pbc_images;
+    c->px = P[0]; c->py = P[1]; c->pz = P[2];
+    c->logpx = ilog2(P[0]); c->logpy = ilog2(P[1]); c->logpz = ilog2(P[2]);
+    c->hx = c->px / 2 + 1;
+    if (c->px == 1) c->hx = 1;
+    c->hyk = c->py / 2 + 1;
+    c->hzk = c->pz / 2 + 1;
+    c->ncomp = nz == 1 ? 4 : 6;
+    c->ncell = (long long)nx * ny * nz;
+    c->ox = pb[0] ? nx / 2 + 1 : nx;
+    c->oy = pb[1] ? ny / 2 + 1 : ny;
+    c->oz = pb[2] ? nz / 2 + 1 : nz;
+    // launch shapes: about 384 threads per block, one radix-16 butterfly each
+    auto nb = [](int logp) { return logp >= 4 ? (1 << logp) / 16 : 1; };
+    c->ty = 2;
+    while (c->ty < 16 && (3 * (2 * c->ty) / 2) * nb(c->logpx) <= 512) c->ty *= 2;
+    c->nyp = (ny + 15) / 16 * 16;
+    c->kxb = 1;
+    while (c->kxb < 64 && 3 * (2 * c->kxb) * nb(c->logpy) <= 512) c->kxb *= 2;
+    c->tz = 1;
+    while (c->tz < 8 && c->tz < nz && 3 * (2 * c->tz) * nb(c->logpy) <= 512) c->tz *= 2;
+    c->nzp = (nz + c->tz - 1) / c->tz * c->tz;
+    c->tky = 1;
+    while (c->tky < 64 && 3 * (2 * c->tky) * nb(c->logpz) <= 512) c->tky *= 2;
+    c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    layout(c);
+    // twiddle table, rounded once from double
+    c->tw_host.resize(mmfft::TWN);
+    for (int t = 0; t < mmfft::TWN; ++t) {
+        const double a = -2.0 * M_PI * (double)t / (double)mmfft::TWN;
+        c->tw_host[t] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    *out = c;
+    return MM_OK;
+}
+
+size_t mm_workspace_bytes(const mm_ctx* ctx) { return ctx ? ctx->total : 0; }
+
+size_t mm_demag_tensor_len(const mm_ctx* ctx) { return ctx ? (size_t)6 * ctx->ox * ctx->oy * ctx->oz : 0; }
+
+int mm_set_workspace(mm_ctx* ctx, void* dev_ptr, size_t bytes) {
+    if (!ctx || !dev_ptr) return fail(ctx, MM_EINVAL, "null workspace");
+    if (reinterpret_cast<uintptr_t>(dev_ptr) & 255) return fail(ctx, MM_EINVAL, "workspace must be 256-byte aligned");
+    if (bytes < ctx->total) return fail(ctx, MM_ENOMEM, "workspace smaller than mm_workspace_bytes()");
+    // opt every hot kernel into large dynamic shared memory (once per process and device)
+    {
+        static int configured_mask = 0;
+        int dev = 0;
+        CK(cudaGetDevice(&dev));
+        if (dev < 31 && !(configured_mask & (1 << dev))) {
+            CK(mm::configure_hot_kernels());
+            configured_mask |= 1 << dev;
+        }
+    }
+    ctx->ws = static_cast<char*>(dev_ptr);
+    ctx->ws_size = bytes;
+    CK(cudaMemcpyAsync(ctx->ws + ctx->off_tw, ctx->tw_host.data(), mmfft::TWN * sizeof(float2),
+                       cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemsetAsync(ctx->ws + ctx->off_st, 0, sizeof(mm::DevState), ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->kernel_ready = false;
+    ctx->state_loaded = false;
+    return MM_OK;
+}
+
+int mm_set_material(mm_ctx* ctx, double Ms, double Aex, double Ku, const double easy_axis[3], double alpha,
+                    double gamma0, double temperature, uint64_t seed, const double B_applied_T[3]) {
+    if (!ctx) return MM_EINVAL;
+    if (!(Ms > 0) || !std::isfinite(Ms)) return fail(ctx, MM_EINVAL, "Ms must be > 0");
+    if (!(Aex >= 0) || !std::isfinite(Aex)) return fail(ctx, MM_EINVAL, "Aex must be >= 0");
+    if (!std::isfinite(Ku)) return fail(ctx, MM_EINVAL, "Ku must be finite");
+    if (!(alpha >= 0) || !std::isfinite(alpha)) return fail(ctx, MM_EINVAL, "alpha must be >= 0");
+    if (gamma0 == 0.0) gamma0 = DEFAULT_GAMMA0;
+    if (!(gamma0 > 0) || !std::isfinite(gamma0)) return fail(ctx, MM_EINVAL, "gamma0 must be > 0");
+    if (!(temperature >= 0) || !std::isfinite(temperature)) return fail(ctx, MM_EINVAL, "temperature must be >= 0");
+    double u[3] = {1, 0, 0};
+    if (Ku != 0.0) {
+        if (!easy_axis) return fail(ctx, MM_EINVAL, "easy axis needed when Ku != 0");
+        const double n = std::sqrt(easy_axis[0] * easy_axis[0] + easy_axis[1] * easy_axis[1] + easy_axis[2] * easy_axis[2]);
+        if (!(n > 0) || !std::isfinite(n)) return fail(ctx, MM_EINVAL, "easy axis must be a non-zero vector");
+        for (int i = 0; i < 3; ++i) u[i] = easy_axis[i] / n;
+    }
+    double B[3] = {0, 0, 0};
+    if (B_applied_T)
+        for (int i = 0; i < 3; ++i) {
+            if (!std::isfinite(B_applied_T[i])) return fail(ctx, MM_EINVAL, "applied field must be finite");
+            B[i] = B_applied_T[i];
+        }
+    const bool ms_changed = ctx->have_material && ctx->Ms != Ms;
+    ctx->Ms = Ms; ctx->Aex = Aex; ctx->Ku = Ku; ctx->alpha = alpha; ctx->gamma0 = gamma0; ctx->T = temperature;
+    ctx->seed = seed;
+    for (int i = 0; i < 3; ++i) { ctx->u[i] = u[i]; ctx->B[i] = B[i]; }
+    ctx->have_material = true;
+    if (ms_changed) ctx->state_loaded = false;     // internal time unit changed
+    ctx->k1_valid = false;
+    return MM_OK;
+}
+
+int mm_set_demag(mm_ctx* ctx, int enabled) {
+    if (!ctx) return MM_EINVAL;
+    ctx->demag = enabled != 0;
+    ctx->k1_valid = false;
+    return MM_OK;
+}
+
+int mm_demag_kernel(mm_ctx* ctx, double* out_tensor_host) {
+    if (!ctx) return MM_EINVAL;
+    if (!ctx->ws) return fail(ctx, MM_ENOMEM, "workspace not set (mm_set_workspace)");
+    mm::SetupParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.nx = ctx->nx; p.ny = ctx->ny; p.nz = ctx->nz;
+    p.px = ctx->px; p.py = ctx->py; p.pz = ctx->pz;
+    p.ox = ctx->ox; p.oy = ctx->oy; p.oz = ctx->oz;
+    for (int i = 0; i < 3; ++i) p.pbc[i] = ctx->pbc[i];
+    p.images = ctx->images;
+    p.ncomp = ctx->ncomp;
+    p.hx = ctx->hx; p.hyk = ctx->hyk; p.hzk = ctx->hzk;
+    const double dmax = std::fmax(ctx->dx, std::fmax(ctx->dy, ctx->dz));
+    p.dx = ctx->dx / dmax; p.dy = ctx->dy / dmax; p.dz = ctx->dz / dmax;
+    const int orders[4] = {3, 4, 6, 8};
+    for (int q = 0; q < 4; ++q) {
+        p.gl_n[q] = orders[q];
+        gauss_legendre(orders[q], p.gl_t[q], p.gl_w[q]);
+    }
+    const size_t oct_bytes = (size_t)6 * ctx->ox * ctx->oy * ctx->oz * sizeof(double);
+    p.oct = reinterpret_cast<double*>(ctx->ws + ctx->off_union);
+    p.work = reinterpret_cast<double2*>(ctx->ws + ctx->off_union + align256(oct_bytes));
+    p.kt = reinterpret_cast<float*>(ctx->ws + ctx->off_kt);
+    p.st = dstate(ctx);
+    ctx->state_loaded = false;
+    ctx->k1_valid = false;
+    CK(cudaMemsetAsync(&p.st->kre_bits, 0, 2 * sizeof(unsigned long long), ctx->stream));
+    CK(mm::launch_kernel_setup(p, ctx->stream));
+    if (out_tensor_host) CK(cudaMemcpyAsync(out_tensor_host, p.oct, oct_bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    unsigned long long bits[2];
+    CK(cudaMemcpyAsync(bits, &p.st->kre_bits, sizeof(bits), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    double re, im;
+    std::memcpy(&re, &bits[0], 8);
+    std::memcpy(&im, &bits[1], 8);
+    if (!(re > 0) || !std::isfinite(re) || !std::isfinite(im))
+        return fail(ctx, MM_ENONFINITE, "demag kernel setup produced non-finite values");
+    if (im > 1e-9 * re) {
+        char buf[128];
+        std::snprintf(buf, sizeof(buf), "demag kernel spectrum not real: |Im|/|Re| = %.3g", im / re);
+        return fail(ctx, MM_ENONFINITE, buf);
+    }
+    ctx->kernel_ready = true;
+    return MM_OK;
+}
+
+int mm_set_thermal_clock(mm_ctx* ctx, uint64_t step_index, double dt_s) {
+    if (!ctx) return MM_EINVAL;
+    if (!(dt_s >= 0) || !std::isfinite(dt_s)) return fail(ctx, MM_EINVAL, "dt must be >= 0");
+    ctx->th_step = step_index;
+    ctx->th_dt = dt_s;
+    return MM_OK;
+}
+
+int mm_eval_heff(mm_ctx* ctx, const float* m, float* h_out, float* torque_out, double* energy_J_host) {
+    int rc = check_ready(ctx, true);
+    if (rc) return rc;
+    if (!m) return fail(ctx, MM_EINVAL, "null m");
+    const double tu = ctx->gamma0 * ctx->Ms;
+    mm::HotParams p = hot_params(ctx, ctx->th_dt * tu, true);
+    p.m_eval = m;
+    p.h_out = h_out;
+    p.tq_out = torque_out;
+    p.want_energy = energy_J_host != nullptr;
+    p.thermal_step = (long long)ctx->th_step;
+    mm::DevState* st = dstate(ctx);
+    CK(cudaMemsetAsync(&st->energy_acc, 0, sizeof(double), ctx->stream));
+    CK(cudaMemsetAsync(&st->status, 0, sizeof(int), ctx->stream));
+    rc = eval(ctx, p, mm::SRC_PTR, mm::LM_EVAL, 0);
+    if (rc) return rc;
+    if (energy_J_host) {
+        double acc = 0.0;
+        int status = 0;
+        CK(cudaMemcpyAsync(&acc, &st->energy_acc, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(&status, &st->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        const double V = ctx->dx * ctx->dy * ctx->dz;
+        *energy_J_host = MU0 * ctx->Ms * ctx->Ms * V * acc;
+        if (status == MM_ENONFINITE) return fail(ctx, MM_ENONFINITE, "non-finite effective field");
+    }
+    return MM_OK;
+}
+
+int mm_load(mm_ctx* ctx, const float* m, double t0_s, uint64_t step_index) {
+    int rc = check_ready(ctx, false);
+    if (rc) return rc;
+    if (!m) return fail(ctx, MM_EINVAL, "null m");
+    if (!std::isfinite(t0_s)) return fail(ctx, MM_EINVAL, "t0 must be finite");
+    mm::DevState h;
+    std::memset(&h, 0, sizeof(h));
+    h.t = t0_s * ctx->gamma0 * ctx->Ms;
+    h.step_index = (long long)step_index;
+    mm::DevState* st = dstate(ctx);
+    CK(cudaMemcpyAsync(st, &h, sizeof(h), cudaMemcpyHostToDevice, ctx->stream));
+    mm::HotParams p = hot_params(ctx, 0.0, false);
+    CK(mm::launch_normalize_load(p, m, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));       // h lives on this stack frame
+    ctx->state_loaded = true;
+    ctx->k1_valid = false;
+    ctx->rk_h_set = false;
+    ctx->step_counter = (long long)step_index;
+    return MM_OK;
+}
+
+int mm_store(mm_ctx* ctx, float* m) {
+    if (!ctx) return MM_EINVAL;
+    if (!ctx->state_loaded) return fail(ctx, MM_ESTATE, "no state loaded (mm_load)");
+    if (!m) return fail(ctx, MM_EINVAL, "null m");
+    mm::HotParams p = hot_params(ctx, 0.0, false);
+    CK(mm::launch_copy_out(p, m, ctx->stream));
+    return MM_OK;
+}
+
+int mm_advance(mm_ctx* ctx, int method, long nsteps, double dt_s, double tol, double t_end_s, double torque_tol) {
+    int rc = check_ready(ctx, true);
+    if (rc) return rc;
+    if (!ctx->state_loaded) return fail(ctx, MM_ESTATE, "no state loaded (mm_load)");
+    if (nsteps < 0) return fail(ctx, MM_EINVAL, "nsteps must be >= 0");
+    if (!std::isfinite(dt_s) || !std::isfinite(tol) || !std::isfinite(t_end_s) || !std::isfinite(torque_tol))
+        return fail(ctx, MM_EINVAL, "non-finite argument");
+    const double tu = ctx->gamma0 * ctx->Ms;
+    if (method == MM_EULER || method == MM_HEUN) {
+        if (!(dt_s > 0)) return fail(ctx, MM_EINVAL, "fixed-step methods need dt > 0");
+    } else if (method == MM_RKDP) {
+        if (ctx->T > 0.0) return fail(ctx, MM_EINVAL, "thermal field needs MM_EULER or MM_HEUN (fixed dt)");
+        if (tol == 0.0) return fail(ctx, MM_EINVAL, "RKDP needs tol > 0 (or < 0 for fixed steps)");
+        if (tol < 0.0 && !(dt_s > 0)) return fail(ctx, MM_EINVAL, "fixed-step RKDP (tol < 0) needs dt > 0");
+    } else {
+        return fail(ctx, MM_EINVAL, "unknown method");
+    }
+    double dt = dt_s * tu;
+    if (method == MM_RKDP) {
+        if (dt > 0) ctx->rk_h_set = true;
+        else if (!ctx->rk_h_set) { dt = 1e-13 * tu; ctx->rk_h_set = true; }   // default first step 100 fs
+    }
+    ctx->last_method = method;
+    mm::HotParams p = hot_params(ctx, dt, true);
+    k_set_run<<<1, 1, 0, ctx->stream>>>(dstate(ctx), tol, t_end_s > 0 ? t_end_s * tu : 0.0,
+                                        torque_tol > 0 ? torque_tol : 0.0,
+                                        method == MM_RKDP ? (dt > 0 ? dt : 0.0) : 0.0, 1e-20 * tu, 1,
+                                        method == MM_RKDP && tol < 0.0 ? 1 : 0);
+    CK(cudaGetLastError());
+    if (method == MM_RKDP) {
+        if (!ctx->k1_valid) {
+            if ((rc = eval(ctx, p, mm::SRC_CUR, mm::LM_K1, 1))) return rc;
+            ctx->k1_valid = true;
+        }
+        for (long s = 0; s < nsteps; ++s) {
+            if ((rc = eval(ctx, p, mm::SRC_COMBINE2, mm::LM_RK, 2))) return rc;
+            if ((rc = eval(ctx, p, mm::SRC_STAGE1, mm::LM_RK, 3))) return rc;
+            if ((rc = eval(ctx, p, mm::SRC_STAGE0, mm::LM_RK, 4))) return rc;
+            if ((rc = eval(ctx, p, mm::SRC_STAGE1, mm::LM_RK, 5))) return rc;
+            if ((rc = eval(ctx, p, mm::SRC_STAGE0, mm::LM_RK, 6))) return rc;
+            if ((rc = eval(ctx, p, mm::SRC_NEXT, mm::LM_RKFINAL, 7))) return rc;
+        }
+    } else {
+        ctx->k1_valid = false;
+        ctx->last_fixed_dt = dt;
+        for (long s = 0; s < nsteps; ++s) {
+            if (method == MM_EULER) {
+                if ((rc = eval(ctx, p, mm::SRC_CUR, mm::LM_EULER, 0))) return rc;
+            } else {
+                if ((rc = eval(ctx, p, mm::SRC_CUR, mm::LM_HEUN1, 0))) return rc;
+                if ((rc = eval(ctx, p, mm::SRC_STAGE0, mm::LM_HEUN2, 0))) return rc;
+            }
+        }
+    }
+    return MM_OK;
+}
+
+int mm_get_stats(mm_ctx* ctx, mm_stats* stats) {
+    if (!ctx) return MM_EINVAL;
+    if (!ctx->ws) return fail(ctx, MM_ENOMEM, "workspace not set");
+    mm::DevState h;
+    CK(cudaMemcpyAsync(&h, dstate(ctx), sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const double tu = ctx->gamma0 * ctx->Ms;
+    ctx->step_counter = h.step_index;
+    if (stats) {
+        stats->evals = h.evals;
+        stats->accepted = h.accepted;
+        stats->rejected = h.rejected;
+        stats->step_index = h.step_index;
+        stats->t = h.t / tu;
+        stats->dt = (ctx->last_method == MM_RKDP ? h.h : ctx->last_fixed_dt) / tu;
+        stats->last_err = h.last_err;
+        stats->max_torque = h.max_torque;
+        const double V = ctx->dx * ctx->dy * ctx->dz;
+        stats->energy = MU0 * ctx->Ms * ctx->Ms * V * h.energy_acc;
+        stats->status = h.status;
+        stats->done = h.done;
+    }
+    return MM_OK;
+}
+
+int mm_step(mm_ctx* ctx, float* m, int method, double* t_s, double* dt_s, double tol, int* accepted) {
+    if (!ctx) return MM_EINVAL;
+    if (!m || !t_s || !dt_s) return fail(ctx, MM_EINVAL, "null argument");
+    int rc = mm_load(ctx, m, *t_s, (uint64_t)ctx->step_counter);
+    if (rc) return rc;
+    if ((rc = mm_advance(ctx, method, 1, *dt_s, tol, 0.0, 0.0))) return rc;
+    if ((rc = mm_store(ctx, m))) return rc;
+    mm_stats s;
+    if ((rc = mm_get_stats(ctx, &s))) return rc;
+    if (s.status) return fail(ctx, s.status, s.status == MM_ENONFINITE ? "non-finite values in the step"
+                                                                        : "step size underflow");
+    if (accepted) *accepted = s.accepted > 0;
+    *t_s = s.t;
+    *dt_s = s.dt;
+    return MM_OK;
+}
+
+int mm_relax(mm_ctx* ctx, float* m, double torque_tol, double err_tol, long max_steps, long* steps_out,
+             double* torque_out) {
+    if (!ctx) return MM_EINVAL;
+    if (!m) return fail(ctx, MM_EINVAL, "null m");
+    if (!(torque_tol > 0) || !(err_tol > 0) || max_steps < 0) return fail(ctx, MM_EINVAL, "bad relax arguments");
+    int rc = mm_load(ctx, m, 0.0, 0);
+    if (rc) return rc;
+    mm_stats s;
+    std::memset(&s, 0, sizeof(s));
+    long done_steps = 0;
+    bool first = true;
+    while (true) {
+        const long chunk = (max_steps - done_steps) < 64 ? (max_steps - done_steps) : 64;
+        if ((rc = mm_advance(ctx, MM_RKDP, chunk, first ? 1e-13 : 0.0, err_tol, 0.0, torque_tol))) return rc;
+        first = false;
+        done_steps += chunk;
+        if ((rc = mm_get_stats(ctx, &s))) return rc;
+        if (s.done || done_steps >= max_steps) break;
+    }
+    if ((rc = mm_store(ctx, m))) return rc;
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (steps_out) *steps_out = (long)(s.accepted + s.rejected);
+    if (torque_out) *torque_out = s.max_torque;
+    if (s.status) return fail(ctx, s.status, "relaxation failed on the device");
+    if (!(s.done && s.max_torque < torque_tol)) return fail(ctx, MM_ENOTCONVERGED, "torque bound not reached");
+    return MM_OK;
+}
+
+int mm_run_host(mm_ctx* ctx, float* m_host, int method, long nsteps, double dt_s, double tol) {
+    int rc = check_ready(ctx, true);
+    if (rc) return rc;
+    if (!m_host) return fail(ctx, MM_EINVAL, "null m");
+    const size_t bytes = (size_t)3 * ctx->ncell * sizeof(float);
+    // the second stage buffer doubles as the device copy of the caller's array
+    float* dev = rk_array(ctx, 10);
+    CK(cudaMemcpyAsync(dev, m_host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    if ((rc = mm_load(ctx, dev, 0.0, (uint64_t)ctx->step_counter))) return rc;
+    if ((rc = mm_advance(ctx, method, nsteps, dt_s, tol, 0.0, 0.0))) return rc;
+    if ((rc = mm_store(ctx, dev))) return rc;
+    CK(cudaMemcpyAsync(m_host, dev, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MM_OK;
+}
+
+int mm_profile(mm_ctx* ctx, int enable) {
+    if (!ctx) return MM_EINVAL;
+    ctx->profiling = enable != 0;
+    if (enable) {
+        for (int i = 0; i < mm::NPASS; ++i) { ctx->pass_ms[i] = 0.0; ctx->pass_n[i] = 0; }
+    }
+    return MM_OK;
+}
+
+int mm_pass_times(mm_ctx* ctx, double* ms_out, long long* count_out) {
+    if (!ctx) return MM_EINVAL;
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (auto& r : ctx->prof) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, r.a, r.b));
+        ctx->pass_ms[r.pass] += ms;
+        ctx->pass_n[r.pass] += 1;
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    ctx->prof.clear();
+    for (int i = 0; i < mm::NPASS; ++i) {
+        if (ms_out) ms_out[i] = ctx->pass_ms[i];
+        if (count_out) count_out[i] = ctx->pass_n[i];
+    }
+    return MM_OK;
+}
+
+const char* mm_last_error(const mm_ctx* ctx) {
+    if (!ctx) return "null context";
+    return ctx->err.c_str();
+}
+
+void mm_destroy(mm_ctx* ctx) {
+    if (!ctx) return;
+    for (auto& r : ctx->prof) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,786 @@
+// hotpath.cu - effective field + Landau-Lifshitz step on the GPU (float32).
+//
+// One evaluation of H_eff (Sec. 2.1) is the three-stage convolution of
+// Sec. 3.2 done as per-axis passes over HBM, each pass a batch of 1-D FFTs in
+// shared memory:
+//
+//   k_xfwd       rows of m (zero padded to Px) -> real-to-complex FFT along x;
+//                writes the half spectrum transposed, [c][kx][z][y] (y
+//                contiguous), so the next pass reads whole columns.  Padded
+//                rows (y >= ny, z >= nz) are never transformed (Sec. 3.2: no
+//                FFTs of all-zero arrays).
+//   k_yconv      2-D grids: per kx column, forward FFT along y, point-wise
+//                product with the real symmetric kernel (Sec. 3.2), inverse FFT
+//                along y - one pass instead of three.
+//   k_yfwd, k_zconv, k_yinv   3-D grids: y forward (writes [c][kx][ky][z]),
+//                fused z forward/product/inverse, y inverse.
+//   k_xinv_local complex-to-real FFT along x, crop, and the whole cell-local
+//                remainder of the step fused into its epilogue: exchange
+//                (Eq. 3), uniaxial anisotropy (Eq. 4), Zeeman, thermal field
+//                (Eq. 6), LL torque (Eq. 1), the Runge-Kutta stage combination
+//                (Sec. 2.2), the step-error and torque reductions and, in the
+//                last block to finish, the adaptive step controller.
+//
+// Nothing leaves the device between steps (Sec. 3.1): step size, time, the
+// slot holding m_n and the accept decision live in DevState.
+#include "mm_internal.cuh"
+#include "fft32.cuh"
+
+namespace mm {
+using namespace mmfft;
+
+// Dormand-Prince 5(4) tableau (Dormand & Prince 1980), double precision.
+// c_dpa[s][j]: weight of k_j in the input of stage s (s = 2..7, j = 1..6);
+// row 7 is the 5th-order solution b.  c_dpe[j] = b_j - b*_j.
+__constant__ double c_dpa[8][8] = {
+    {0}, {0},
+    {0, 1.0 / 5},
+    {0, 3.0 / 40, 9.0 / 40},
+    {0, 44.0 / 45, -56.0 / 15, 32.0 / 9},
+    {0, 19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729},
+    {0, 9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656},
+    {0, 35.0 / 384, 0.0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84},
+};
+__constant__ double c_dpe[8] = {
+    0,
+    35.0 / 384 - 5179.0 / 57600,
+    0.0,
+    500.0 / 1113 - 7571.0 / 16695,
+    125.0 / 192 - 393.0 / 640,
+    -2187.0 / 6784 + 92097.0 / 339200,
+    11.0 / 84 - 187.0 / 2100,
+    -1.0 / 40,
+};
+
+// ---------------------------------------------------------------------------
+// small helpers
+struct f3 { float x, y, z; };
+__device__ __forceinline__ f3 mk(float x, float y, float z) { return {x, y, z}; }
+__device__ __forceinline__ f3 operator+(f3 a, f3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ f3 operator-(f3 a, f3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ f3 operator*(float s, f3 a) { return {s * a.x, s * a.y, s * a.z}; }
+__device__ __forceinline__ float dot(f3 a, f3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ f3 cross(f3 a, f3 b) {
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ f3 ld3(const float* __restrict__ a, long long i, long long n) {
+    return {a[i], a[i + n], a[i + 2 * n]};
+}
+__device__ __forceinline__ void st3(float* __restrict__ a, long long i, long long n, f3 v) {
+    a[i] = v.x; a[i + n] = v.y; a[i + 2 * n] = v.z;
+}
+__device__ __forceinline__ f3 normalized(f3 v) {
+    float n = sqrtf(dot(v, v));
+    float inv = 1.0f / n;
+    return inv * v;
+}
+__device__ __forceinline__ bool finite3(f3 v) { return isfinite(v.x) && isfinite(v.y) && isfinite(v.z); }
+
+// a coefficient c (double) split as hi + lo floats, so that sums like
+// m + c k keep the coefficient exact to ~1e-14 (a single-precision c would
+// bias every step by the same relative amount)
+struct Coef { float hi, lo; };
+__device__ __forceinline__ Coef split(double c) {
+    float hi = (float)c;
+    return {hi, (float)(c - (double)hi)};
+}
+__device__ __forceinline__ f3 axpy(Coef c, f3 k, f3 acc) {
+    return {fmaf(c.lo, k.x, fmaf(c.hi, k.x, acc.x)), fmaf(c.lo, k.y, fmaf(c.hi, k.y, acc.y)),
+            fmaf(c.lo, k.z, fmaf(c.hi, k.z, acc.z))};
+}
+
+// ---- Philox-4x32-10 (Salmon et al., SC'11) and the Gaussian draw ----------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k.x += 0x9E3779B9u; k.y += 0xBB67AE85u; }
+        unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+__device__ __forceinline__ float u01(unsigned w) {         // (0,1), exact in float
+    return ((float)(w >> 9) + 0.5f) * 1.1920928955078125e-07f;
+}
+__device__ __forceinline__ f3 gauss3(long long cell, long long step, unsigned long long seed) {
+    uint4 w = philox4x32_10(make_uint4((unsigned)cell, (unsigned)step, (unsigned)((unsigned long long)step >> 32), 0u),
+                            make_uint2((unsigned)seed, (unsigned)(seed >> 32)));
+    float r01 = sqrtf(-2.0f * logf(u01(w.x)));
+    float r23 = sqrtf(-2.0f * logf(u01(w.z)));
+    float s1, c1, s3, c3;
+    sincospif(2.0f * u01(w.y), &s1, &c1);
+    sincospif(2.0f * u01(w.w), &s3, &c3);
+    return {r01 * c1, r01 * s1, r23 * c3};
+}
+
+__device__ __forceinline__ const float* src_ptr(const HotParams& p, int src, int cur) {
+    switch (src) {
+        case SRC_PTR: return p.m_eval;
+        case SRC_CUR: return p.ms[cur];
+        case SRC_NEXT: return p.ms[1 - cur];
+        case SRC_STAGE1: return p.mstage[1];
+        default: return p.mstage[0];      // SRC_STAGE0, SRC_COMBINE2 (materialised)
+    }
+}
+
+// ---------------------------------------------------------------------------
+// x forward pass: R2C along x of 3*TY real rows (pairs of rows share one
+// complex FFT: z = a + i b, A = (Z_k + conj Z_-k)/2, B = (Z_k - conj Z_-k)/(2i)).
+template <int LOGP>
+__global__ void __launch_bounds__(768) k_xfwd(HotParams p, LaunchArgs a) {
+    extern __shared__ float2 sm[];
+    constexpr int P = 1 << LOGP;
+    const int LS = padded_len(P);
+    const int TY = p.ty, NL = (3 * TY) >> 1;
+    const int y0 = blockIdx.x * TY, z = blockIdx.y;
+    DevState* st = p.st;
+    if (a.mode != LM_EVAL && st->done) return;
+    const int cur = st->cur;
+    const long long n = p.ncell;
+    const float* src = src_ptr(p, a.src, cur);
+    const float* k1 = p.ks[cur];
+    float* wout = p.mstage[0];
+    Coef c21 = {0.f, 0.f};
+    if (a.src == SRC_COMBINE2) {
+        src = p.ms[cur];
+        c21 = split(st->h * c_dpa[2][1]);
+    }
+    for (int idx = threadIdx.x; idx < TY * P; idx += blockDim.x) {
+        const int ty = idx >> LOGP, x = idx & (P - 1);
+        const int y = y0 + ty;
+        f3 v = mk(0.f, 0.f, 0.f);
+        if (x < p.nx && y < p.ny) {
+            const long long cell = ((long long)z * p.ny + y) * p.nx + x;
+            v = ld3(src, cell, n);
+            if (a.src == SRC_COMBINE2) {
+                v = axpy(c21, ld3(k1, cell, n), v);
+                st3(wout, cell, n, v);
+            }
+        }
+        const float vv[3] = {v.x, v.y, v.z};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int q = c * TY + ty;
+            reinterpret_cast<float*>(sm + (q >> 1) * LS + pad(x))[q & 1] = vv[c];
+        }
+    }
+    __syncthreads();
+    fft_lines<LOGP, false>(sm, NL, LS, p.tw);
+    const int HX = p.hx;
+    for (int idx = threadIdx.x; idx < NL * HX; idx += blockDim.x) {
+        const int l = idx % NL, k = idx / NL;
+        const float2 A = sm[l * LS + pad(k)];
+        const float2 B = cconj(sm[l * LS + pad((P - k) & (P - 1))]);
+        const float2 D = csub(A, B);
+        const float4 out = make_float4(0.5f * (A.x + B.x), 0.5f * (A.y + B.y), 0.5f * D.y, -0.5f * D.x);
+        const int q = 2 * l, c = q / TY, ty = q - c * TY;      // rows q, q+1: same component
+        float2* dst = p.s1 + ((long long)(c * HX + k) * p.nz + z) * p.nyp + y0 + ty;
+        *reinterpret_cast<float4*>(dst) = out;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 2-D column pass: y forward FFT, kernel product, y inverse FFT (in place).
+template <int LOGP>
+__global__ void __launch_bounds__(768) k_yconv(HotParams p, LaunchArgs a) {
+    extern __shared__ float2 sm[];
+    constexpr int P = 1 << LOGP;
+    const int LS = padded_len(P);
+    const int KXB = p.kxb, NL = 3 * KXB;
+    const int kx0 = blockIdx.x * KXB;
+    if (a.mode != LM_EVAL && p.st->done) return;
+    const int HX = p.hx, NY = p.ny;
+    for (int idx = threadIdx.x; idx < NL * P; idx += blockDim.x) {
+        const int l = idx >> LOGP, y = idx & (P - 1);
+        const int c = l / KXB, j = l - c * KXB, kx = kx0 + j;
+        float2 v = make_float2(0.f, 0.f);
+        if (kx < HX && y < NY) v = p.s1[(long long)(c * HX + kx) * p.nyp + y];
+        sm[l * LS + pad(y)] = v;
+    }
+    __syncthreads();
+    fft_lines<LOGP, false>(sm, NL, LS, p.tw);
+    const long long cs = (long long)HX * p.hyk;       // kernel component stride (hzk == 1)
+    for (int idx = threadIdx.x; idx < KXB * P; idx += blockDim.x) {
+        const int j = idx >> LOGP, ky = idx & (P - 1), kx = kx0 + j;
+        if (kx >= HX) continue;
+        const bool hi = ky > (P >> 1);
+        const int kq = hi ? P - ky : ky;
+        const long long b = (long long)kx * p.hyk + kq;
+        const float kxx = __ldg(p.kt + b), kyy = __ldg(p.kt + cs + b), kzz = __ldg(p.kt + 2 * cs + b);
+        const float kxy = hi ? -__ldg(p.kt + 3 * cs + b) : __ldg(p.kt + 3 * cs + b);
+        float2* mx = sm + (0 * KXB + j) * LS + pad(ky);
+        float2* my = sm + (1 * KXB + j) * LS + pad(ky);
+        float2* mz = sm + (2 * KXB + j) * LS + pad(ky);
+        const float2 X = *mx, Y = *my, Z = *mz;
+        *mx = make_float2(kxx * X.x + kxy * Y.x, kxx * X.y + kxy * Y.y);
+        *my = make_float2(kxy * X.x + kyy * Y.x, kxy * X.y + kyy * Y.y);
+        *mz = make_float2(kzz * Z.x, kzz * Z.y);
+    }
+    __syncthreads();
+    fft_lines<LOGP, true>(sm, NL, LS, p.tw);
+    for (int idx = threadIdx.x; idx < NL * NY; idx += blockDim.x) {
+        const int l = idx / NY, y = idx - l * NY;
+        const int c = l / KXB, j = l - c * KXB, kx = kx0 + j;
+        if (kx < HX) p.s1[(long long)(c * HX + kx) * p.nyp + y] = sm[l * LS + pad(y)];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 3-D: y forward pass.  s1 [c][kx][z][y]  ->  s2 [c][kx][ky][z]
+template <int LOGP>
+__global__ void __launch_bounds__(768) k_yfwd(HotParams p, LaunchArgs a) {
+    extern __shared__ float2 sm[];
+    constexpr int P = 1 << LOGP;
+    const int LS = padded_len(P);
+    const int TZ = p.tz, NL = 3 * TZ;
+    const int kx = blockIdx.x, z0 = blockIdx.y * TZ;
+    if (a.mode != LM_EVAL && p.st->done) return;
+    const int HX = p.hx, NY = p.ny, NZ = p.nz;
+    for (int idx = threadIdx.x; idx < NL * P; idx += blockDim.x) {
+        const int l = idx >> LOGP, y = idx & (P - 1);
+        const int c = l / TZ, zt = l - c * TZ, z = z0 + zt;
+        float2 v = make_float2(0.f, 0.f);
+        if (y < NY && z < NZ) v = p.s1[((long long)(c * HX + kx) * NZ + z) * p.nyp + y];
+        sm[l * LS + pad(y)] = v;
+    }
+    __syncthreads();
+    fft_lines<LOGP, false>(sm, NL, LS, p.tw);
+    for (int idx = threadIdx.x; idx < NL * P; idx += blockDim.x) {
+        const int zt = idx % TZ, r = idx / TZ, ky = r & (P - 1), c = r >> LOGP;
+        p.s2[((long long)(c * HX + kx) * P + ky) * p.nzp + z0 + zt] = sm[(c * TZ + zt) * LS + pad(ky)];
+    }
+}
+
+// 3-D: fused z pass (forward, kernel product, inverse) on s2 in place.
+template <int LOGP>
+__global__ void __launch_bounds__(768) k_zconv(HotParams p, LaunchArgs a) {
+    extern __shared__ float2 sm[];
+    constexpr int P = 1 << LOGP;
+    const int LS = padded_len(P);
+    const int TK = p.tky, NL = 3 * TK;
+    const int kx = blockIdx.x, ky0 = blockIdx.y * TK;
+    if (a.mode != LM_EVAL && p.st->done) return;
+    const int HX = p.hx, PY = p.py, NZ = p.nz;
+    for (int idx = threadIdx.x; idx < NL * P; idx += blockDim.x) {
+        const int l = idx >> LOGP, z = idx & (P - 1);
+        const int c = l / TK, j = l - c * TK, ky = ky0 + j;
+        float2 v = make_float2(0.f, 0.f);
+        if (ky < PY && z < NZ) v = p.s2[((long long)(c * HX + kx) * PY + ky) * p.nzp + z];
+        sm[l * LS + pad(z)] = v;
+    }
+    __syncthreads();
+    fft_lines<LOGP, false>(sm, NL, LS, p.tw);
+    const long long cs = (long long)HX * p.hyk * p.hzk;
+    for (int idx = threadIdx.x; idx < TK * P; idx += blockDim.x) {
+        const int j = idx >> LOGP, kz = idx & (P - 1), ky = ky0 + j;
+        if (ky >= PY) continue;
+        const bool yh = ky > (PY >> 1), zh = kz > (P >> 1);
+        const int kyq = yh ? PY - ky : ky, kzq = zh ? P - kz : kz;
+        const long long b = ((long long)kx * p.hyk + kyq) * p.hzk + kzq;
+        const float kxx = __ldg(p.kt + b), kyy = __ldg(p.kt + cs + b), kzz = __ldg(p.kt + 2 * cs + b);
+        float kxy = __ldg(p.kt + 3 * cs + b), kxz = __ldg(p.kt + 4 * cs + b), kyz = __ldg(p.kt + 5 * cs + b);
+        if (yh) { kxy = -kxy; kyz = -kyz; }
+        if (zh) { kxz = -kxz; kyz = -kyz; }
+        float2* mx = sm + (0 * TK + j) * LS + pad(kz);
+        float2* my = sm + (1 * TK + j) * LS + pad(kz);
+        float2* mz = sm + (2 * TK + j) * LS + pad(kz);
+        const float2 X = *mx, Y = *my, Z = *mz;
+        *mx = make_float2(kxx * X.x + kxy * Y.x + kxz * Z.x, kxx * X.y + kxy * Y.y + kxz * Z.y);
+        *my = make_float2(kxy * X.x + kyy * Y.x + kyz * Z.x, kxy * X.y + kyy * Y.y + kyz * Z.y);
+        *mz = make_float2(kxz * X.x + kyz * Y.x + kzz * Z.x, kxz * X.y + kyz * Y.y + kzz * Z.y);
+    }
+    __syncthreads();
+    fft_lines<LOGP, true>(sm, NL, LS, p.tw);
+    for (int idx = threadIdx.x; idx < NL * NZ; idx += blockDim.x) {
+        const int l = idx / NZ, z = idx - l * NZ;
+        const int c = l / TK, j = l - c * TK, ky = ky0 + j;
+        if (ky < PY) p.s2[((long long)(c * HX + kx) * PY + ky) * p.nzp + z] = sm[l * LS + pad(z)];
+    }
+}
+
+// 3-D: y inverse pass.  s2 [c][kx][ky][z]  ->  s1 [c][kx][z][y]
+template <int LOGP>
+__global__ void __launch_bounds__(768) k_yinv(HotParams p, LaunchArgs a) {
+    extern __shared__ float2 sm[];
+    constexpr int P = 1 << LOGP;
+    const int LS = padded_len(P);
+    const int TZ = p.tz, NL = 3 * TZ;
+    const int kx = blockIdx.x, z0 = blockIdx.y * TZ;
+    if (a.mode != LM_EVAL && p.st->done) return;
+    const int HX = p.hx, NY = p.ny, NZ = p.nz;
+    for (int idx = threadIdx.x; idx < NL * P; idx += blockDim.x) {
+        const int zt = idx % TZ, r = idx / TZ, ky = r & (P - 1), c = r >> LOGP;
+        sm[(c * TZ + zt) * LS + pad(ky)] = p.s2[((long long)(c * HX + kx) * P + ky) * p.nzp + z0 + zt];
+    }
+    __syncthreads();
+    fft_lines<LOGP, true>(sm, NL, LS, p.tw);
+    for (int idx = threadIdx.x; idx < NL * NY; idx += blockDim.x) {
+        const int l = idx / NY, y = idx - l * NY;
+        const int c = l / TZ, zt = l - c * TZ, z = z0 + zt;
+        if (z < NZ) p.s1[((long long)(c * HX + kx) * NZ + z) * p.nyp + y] = sm[l * LS + pad(y)];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// block reduction + last-block step control
+struct Partials {
+    float err, torque;
+    double energy;
+    unsigned bad;
+};
+
+__device__ void finalize(const HotParams& p, const LaunchArgs& a) {
+    DevState* st = p.st;
+    const float err = __uint_as_float(atomicExch(&st->err_bits, 0u));
+    const float tq = __uint_as_float(atomicExch(&st->torque_bits, 0u));
+    const unsigned bad = atomicExch(&st->bad, 0u);
+    st->blocks_done = 0u;
+    st->evals += 1;
+    switch (a.mode) {
+        case LM_EVAL:
+            st->max_torque = tq;
+            if (bad) st->status = -5;
+            break;
+        case LM_K1:
+            st->max_torque = tq;
+            if (bad) { st->status = -5; st->done = 1; }
+            else if (st->torque_tol > 0.0 && tq < st->torque_tol) st->done = 1;
+            break;
+        case LM_RKFINAL: {
+            st->last_err = err;
+            if (bad || !isfinite(err)) { st->status = -5; st->done = 1; break; }
+            const bool accept = st->fixed_h || (double)err <= st->tol;
+            double f = (err == 0.0f) ? 5.0 : 0.9 * pow(st->tol / (double)err, 0.2);
+            f = fmin(fmax(f, 0.2), 5.0);
+            if (st->fixed_h) f = 1.0;
+            if (accept) {
+                if (st->after_reject) f = fmin(f, 1.0);
+                st->t += st->h;
+                st->cur ^= 1;
+                st->accepted += 1;
+                st->max_torque = tq;
+                st->after_reject = 0;
+            } else {
+                f = fmin(f, 1.0);
+                st->rejected += 1;
+                st->after_reject = 1;
+            }
+            st->h *= f;
+            if (st->t_end > 0.0) {
+                const double left = st->t_end - st->t;
+                if (left <= 1e-12 * st->t_end) st->done = 1;
+                else st->h = fmin(st->h, left);
+            }
+            if (accept && st->torque_tol > 0.0 && tq < st->torque_tol) st->done = 1;
+            if (!st->done && st->h < st->h_min) { st->status = -4; st->done = 1; }
+            break;
+        }
+        case LM_EULER:
+        case LM_HEUN2:
+            if (bad) { st->status = -5; st->done = 1; break; }
+            st->t += p.dt_d;
+            st->cur ^= 1;
+            st->step_index += 1;
+            st->accepted += 1;
+            if (st->t_end > 0.0 && st->t >= st->t_end * (1.0 - 1e-12)) st->done = 1;
+            break;
+        default:
+            if (bad) { st->status = -5; st->done = 1; }
+            break;
+    }
+}
+
+__device__ void reduce_and_finish(const HotParams& p, const LaunchArgs& a, Partials pt) {
+    __shared__ float r_err[32], r_tq[32];
+    __shared__ double r_e[32];
+    __shared__ unsigned r_bad[32];
+    __shared__ int s_last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        pt.err = fmaxf(pt.err, __shfl_xor_sync(0xffffffffu, pt.err, o));
+        pt.torque = fmaxf(pt.torque, __shfl_xor_sync(0xffffffffu, pt.torque, o));
+        pt.energy += __shfl_xor_sync(0xffffffffu, pt.energy, o);
+        pt.bad |= __shfl_xor_sync(0xffffffffu, pt.bad, o);
+    }
+    if (lane == 0) { r_err[wid] = pt.err; r_tq[wid] = pt.torque; r_e[wid] = pt.energy; r_bad[wid] = pt.bad; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int w = 1; w < nw; ++w) {
+            pt.err = fmaxf(pt.err, r_err[w]);
+            pt.torque = fmaxf(pt.torque, r_tq[w]);
+            pt.energy += r_e[w];
+            pt.bad |= r_bad[w];
+        }
+        DevState* st = p.st;
+        if (pt.err > 0.f) atomicMax(&st->err_bits, __float_as_uint(pt.err));
+        if (pt.torque > 0.f) atomicMax(&st->torque_bits, __float_as_uint(pt.torque));
+        if (a.mode == LM_EVAL && p.want_energy) atomicAdd(&st->energy_acc, pt.energy);
+        if (pt.bad) atomicOr(&st->bad, 1u);
+        __threadfence();
+        const unsigned prev = atomicAdd(&st->blocks_done, 1u);
+        s_last = (prev == gridDim.x * gridDim.y - 1);
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        finalize(p, a);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Everything that happens to one cell once its demag field is known.
+struct StageCoefs {
+    Coef c[8];          // per mode: stage combination weights (see below)
+};
+
+__device__ __forceinline__ void cell_update(const HotParams& p, const LaunchArgs& a, int cur, const StageCoefs& sc,
+                                            const float* __restrict__ min, long long cell, int x, int y, int z,
+                                            f3 hd, long long tstep, Partials& pt) {
+    const long long n = p.ncell;
+    const f3 m = ld3(min, cell, n);
+    // exchange, 6-neighbour (4 in 2-D) Laplacian; a missing neighbour adds nothing
+    f3 hex = mk(0.f, 0.f, 0.f);
+    {
+        f3 s = mk(0.f, 0.f, 0.f);
+        if (x + 1 < p.nx) s = s + (ld3(min, cell + 1, n) - m);
+        else if (p.pbc[0]) s = s + (ld3(min, cell - (p.nx - 1), n) - m);
+        if (x > 0) s = s + (ld3(min, cell - 1, n) - m);
+        else if (p.pbc[0]) s = s + (ld3(min, cell + (p.nx - 1), n) - m);
+        hex = p.cex[0] * s;
+    }
+    if (p.ny > 1 || p.pbc[1]) {
+        const long long sy = p.nx;
+        f3 s = mk(0.f, 0.f, 0.f);
+        if (y + 1 < p.ny) s = s + (ld3(min, cell + sy, n) - m);
+        else if (p.pbc[1]) s = s + (ld3(min, cell - (long long)(p.ny - 1) * sy, n) - m);
+        if (y > 0) s = s + (ld3(min, cell - sy, n) - m);
+        else if (p.pbc[1]) s = s + (ld3(min, cell + (long long)(p.ny - 1) * sy, n) - m);
+        hex = hex + p.cex[1] * s;
+    }
+    if (p.nz > 1 || p.pbc[2]) {
+        const long long sz = (long long)p.nx * p.ny;
+        f3 s = mk(0.f, 0.f, 0.f);
+        if (z + 1 < p.nz) s = s + (ld3(min, cell + sz, n) - m);
+        else if (p.pbc[2]) s = s + (ld3(min, cell - (long long)(p.nz - 1) * sz, n) - m);
+        if (z > 0) s = s + (ld3(min, cell - sz, n) - m);
+        else if (p.pbc[2]) s = s + (ld3(min, cell + (long long)(p.nz - 1) * sz, n) - m);
+        hex = hex + p.cex[2] * s;
+    }
+    const f3 u = mk(p.ux, p.uy, p.uz);
+    const f3 han = (p.kan * dot(m, u)) * u;
+    const f3 hz = mk(p.hzx, p.hzy, p.hzz);
+    f3 h = hd + hex + han + hz;
+    if (p.sigma_th > 0.f) h = h + p.sigma_th * gauss3(cell, tstep, p.seed);
+    const f3 mxh = cross(m, h);
+    const f3 k = (-p.llpref) * (mxh + p.alpha * cross(m, mxh));
+    const float tq = sqrtf(dot(mxh, mxh));
+
+    switch (a.mode) {
+        case LM_EVAL: {
+            if (p.h_out) st3(p.h_out, cell, n, p.h_scale * h);
+            if (p.tq_out) st3(p.tq_out, cell, n, p.t_scale * k);
+            pt.torque = fmaxf(pt.torque, tq);
+            if (p.want_energy) pt.energy -= 0.5 * (double)dot(m, hd + hex + han) + (double)dot(m, hz);
+            pt.bad |= !finite3(h);
+            break;
+        }
+        case LM_K1:
+            st3(p.ks[cur], cell, n, k);
+            pt.torque = fmaxf(pt.torque, tq);
+            pt.bad |= !finite3(k);
+            break;
+        case LM_RK: {
+            const int s = a.stage;                       // 2..6
+            st3(p.kb[s], cell, n, k);
+            f3 acc = ld3(p.ms[cur], cell, n);
+            acc = axpy(sc.c[1], ld3(p.ks[cur], cell, n), acc);
+            for (int j = 2; j < s; ++j)
+                if (sc.c[j].hi != 0.f) acc = axpy(sc.c[j], ld3(p.kb[j], cell, n), acc);
+            acc = axpy(sc.c[s], k, acc);
+            if (s < 6) st3(p.mstage[(s + 1) & 1], cell, n, acc);
+            else st3(p.ms[1 - cur], cell, n, normalized(acc));
+            pt.bad |= !finite3(k);
+            break;
+        }
+        case LM_RKFINAL: {
+            st3(p.ks[1 - cur], cell, n, k);
+            f3 e = mk(0.f, 0.f, 0.f);
+            e = axpy(sc.c[1], ld3(p.ks[cur], cell, n), e);
+#pragma unroll
+            for (int j = 3; j <= 6; ++j) e = axpy(sc.c[j], ld3(p.kb[j], cell, n), e);
+            e = axpy(sc.c[7], k, e);
+            pt.err = fmaxf(pt.err, sqrtf(dot(e, e)));
+            pt.torque = fmaxf(pt.torque, tq);
+            pt.bad |= !finite3(k) || !finite3(e);
+            break;
+        }
+        case LM_EULER: {
+            f3 acc = axpy(sc.c[0], k, m);
+            const f3 mn = normalized(acc);
+            st3(p.ms[1 - cur], cell, n, mn);
+            pt.bad |= !finite3(mn);
+            break;
+        }
+        case LM_HEUN1: {
+            st3(p.ks[cur], cell, n, k);
+            st3(p.mstage[0], cell, n, axpy(sc.c[0], k, m));
+            pt.bad |= !finite3(k);
+            break;
+        }
+        case LM_HEUN2: {
+            f3 acc = ld3(p.ms[cur], cell, n);
+            acc = axpy(sc.c[0], ld3(p.ks[cur], cell, n), acc);
+            acc = axpy(sc.c[0], k, acc);
+            const f3 mn = normalized(acc);
+            st3(p.ms[1 - cur], cell, n, mn);
+            pt.bad |= !finite3(mn);
+            break;
+        }
+        default: break;
+    }
+}
+
+__device__ void stage_coefs(const HotParams& p, const LaunchArgs& a, const DevState* st, StageCoefs& sc) {
+    for (int j = 0; j < 8; ++j) sc.c[j] = {0.f, 0.f};
+    const double h = st->h;
+    switch (a.mode) {
+        case LM_RK:
+            for (int j = 1; j <= a.stage; ++j) sc.c[j] = split(h * c_dpa[a.stage + 1][j]);
+            break;
+        case LM_RKFINAL:
+            for (int j = 1; j <= 7; ++j) sc.c[j] = split(h * c_dpe[j]);
+            break;
+        case LM_EULER:
+        case LM_HEUN1:
+            sc.c[0] = split(p.dt_d);
+            break;
+        case LM_HEUN2:
+            sc.c[0] = split(0.5 * p.dt_d);
+            break;
+        default: break;
+    }
+}
+
+// inverse x pass (C2R) + crop + fused local epilogue.  DEMAG = false skips the
+// spectrum entirely (demag disabled).
+template <int LOGP, bool DEMAG>
+__global__ void __launch_bounds__(768) k_xinv_local(HotParams p, LaunchArgs a) {
+    extern __shared__ float2 sm[];
+    __shared__ StageCoefs s_sc;
+    __shared__ int s_cur;
+    __shared__ long long s_tstep;
+    constexpr int P = 1 << LOGP;
+    const int LS = padded_len(P);
+    const int TY = p.ty, NL = (3 * TY) >> 1;
+    const int y0 = blockIdx.x * TY, z = blockIdx.y;
+    DevState* st = p.st;
+    if (a.mode != LM_EVAL && st->done) return;
+    if (threadIdx.x == 0) {
+        stage_coefs(p, a, st, s_sc);
+        s_cur = st->cur;
+        s_tstep = (a.mode == LM_EVAL) ? p.thermal_step : st->step_index;
+    }
+    if constexpr (DEMAG) {
+        const int HX = p.hx;
+        for (int idx = threadIdx.x; idx < NL * HX; idx += blockDim.x) {
+            const int l = idx % NL, k = idx / NL;
+            const int q = 2 * l, c = q / TY, ty = q - c * TY;
+            const float4 v = *reinterpret_cast<const float4*>(
+                p.s1 + ((long long)(c * HX + k) * p.nz + z) * p.nyp + y0 + ty);
+            // Z = A + iB with A = (v.x, v.y), B = (v.z, v.w); Z[-k] = conj(A) + i conj(B)
+            sm[l * LS + pad(k)] = make_float2(v.x - v.w, v.y + v.z);
+            if (k > 0 && 2 * k < P) sm[l * LS + pad(P - k)] = make_float2(v.x + v.w, v.z - v.y);
+        }
+        __syncthreads();
+        fft_lines<LOGP, true>(sm, NL, LS, p.tw);
+    } else {
+        __syncthreads();
+    }
+    const int cur = s_cur;
+    const float* min = src_ptr(p, a.src, cur);
+    Partials pt = {0.f, 0.f, 0.0, 0u};
+    const StageCoefs sc = s_sc;
+    const int NX = p.nx;
+    for (int idx = threadIdx.x; idx < TY * NX; idx += blockDim.x) {
+        const int ty = idx / NX, x = idx - ty * NX, y = y0 + ty;
+        if (y >= p.ny) continue;
+        f3 hd = mk(0.f, 0.f, 0.f);
+        if constexpr (DEMAG) {
+            float v[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int q = c * TY + ty;
+                v[c] = reinterpret_cast<const float*>(sm + (q >> 1) * LS + pad(x))[q & 1];
+            }
+            hd = mk(v[0], v[1], v[2]);
+        }
+        const long long cell = ((long long)z * p.ny + y) * NX + x;
+        cell_update(p, a, cur, sc, min, cell, x, y, z, hd, s_tstep, pt);
+    }
+    reduce_and_finish(p, a, pt);
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_normalize_load(HotParams p, const float* __restrict__ m_user) {
+    const long long n = p.ncell;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        st3(p.ms[0], i, n, normalized(ld3(m_user, i, n)));
+}
+
+// m_2 = m_n + h a21 k1 into mstage[0] (used when there is no x pass to fuse it into)
+__global__ void k_combine2(HotParams p) {
+    const DevState* st = p.st;
+    if (st->done) return;
+    const long long n = p.ncell;
+    const int cur = st->cur;
+    const Coef c = split(st->h * c_dpa[2][1]);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        st3(p.mstage[0], i, n, axpy(c, ld3(p.ks[cur], i, n), ld3(p.ms[cur], i, n)));
+}
+
+__global__ void k_copy_out(HotParams p, float* __restrict__ m_user) {
+    const long long n = p.ncell;
+    const float* src = p.ms[p.st->cur];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 3 * n; i += (long long)gridDim.x * blockDim.x)
+        m_user[i] = src[i];
+}
+
+// ---------------------------------------------------------------------------
+// launch helpers
+static int threads_for(int nlines, int logp) {
+    const int nb = logp >= 4 ? (1 << logp) / 16 : 1;
+    int t = nlines * nb;
+    t = ((t + 31) / 32) * 32;
+    return t < 64 ? 64 : t;
+}
+static size_t smem_for(int nlines, int logp) { return (size_t)nlines * padded_len(1 << logp) * sizeof(float2); }
+
+template <int L>
+static cudaError_t set_attr_all() {
+    cudaError_t e;
+    const int mx = 200 * 1024;
+    if ((e = cudaFuncSetAttribute(k_xfwd<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_yconv<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_yfwd<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_zconv<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_yinv<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_xinv_local<L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if constexpr (L > 0) return set_attr_all<L - 1>();
+    return cudaSuccess;
+}
+
+cudaError_t configure_hot_kernels() { return set_attr_all<12>(); }
+
+#define MM_DISPATCH(LOGP, KERNEL, GRID, BLOCK, SMEM, STREAM, ...)                  \
+    switch (LOGP) {                                                                \
+        case 0: KERNEL<0><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__); break;     \
+        case 1: KERNEL<1><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__); break;     \
+        case 2: KERNEL<2><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__); break;     \
+        case 3: KERNEL<3><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__); break;     \
+        case 4: KERNEL<4><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__); break;     \
+        case 5: KERNEL<5><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__); break;     \
+        case 6: KERNEL<6><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__); break;     \
+        case 7: KERNEL<7><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__); break;     \
+        case 8: KERNEL<8><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__); break;     \
+        case 9: KERNEL<9><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__); break;     \
+        case 10: KERNEL<10><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__); break;   \
+        case 11: KERNEL<11><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__); break;   \
+        case 12: KERNEL<12><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__); break;   \
+        default: return cudaErrorInvalidValue;                                     \
+    }
+
+int eval_passes(const HotParams& p, const LaunchArgs& a, int* ids) {
+    int n = 0;
+    if (p.demag) {
+        ids[n++] = PASS_XFWD;
+        if (p.nz == 1) {
+            ids[n++] = PASS_YCONV;
+        } else {
+            ids[n++] = PASS_YFWD;
+            ids[n++] = PASS_ZCONV;
+            ids[n++] = PASS_YINV;
+        }
+        ids[n++] = PASS_XINV_LOCAL;
+    } else {
+        if (a.src == SRC_COMBINE2) ids[n++] = PASS_COMBINE2;   // no x pass to fold m_2 into
+        ids[n++] = PASS_LOCAL;
+    }
+    return n;
+}
+
+cudaError_t launch_pass(const HotParams& p, const LaunchArgs& a, int pass, cudaStream_t s) {
+    const int NL = 3 * p.ty / 2;
+    const dim3 gx((p.ny + p.ty - 1) / p.ty, p.nz);
+    switch (pass) {
+        case PASS_XFWD:
+            MM_DISPATCH(p.logpx, k_xfwd, gx, threads_for(NL, p.logpx), smem_for(NL, p.logpx), s, p, a);
+            break;
+        case PASS_YCONV: {
+            const int nl = 3 * p.kxb;
+            const dim3 g((p.hx + p.kxb - 1) / p.kxb);
+            MM_DISPATCH(p.logpy, k_yconv, g, threads_for(nl, p.logpy), smem_for(nl, p.logpy), s, p, a);
+            break;
+        }
+        case PASS_YFWD:
+        case PASS_YINV: {
+            const int nl = 3 * p.tz;
+            const dim3 gy(p.hx, (p.nz + p.tz - 1) / p.tz);
+            if (pass == PASS_YFWD) {
+                MM_DISPATCH(p.logpy, k_yfwd, gy, threads_for(nl, p.logpy), smem_for(nl, p.logpy), s, p, a);
+            } else {
+                MM_DISPATCH(p.logpy, k_yinv, gy, threads_for(nl, p.logpy), smem_for(nl, p.logpy), s, p, a);
+            }
+            break;
+        }
+        case PASS_ZCONV: {
+            const int nlz = 3 * p.tky;
+            const dim3 gz(p.hx, (p.py + p.tky - 1) / p.tky);
+            MM_DISPATCH(p.logpz, k_zconv, gz, threads_for(nlz, p.logpz), smem_for(nlz, p.logpz), s, p, a);
+            break;
+        }
+        case PASS_XINV_LOCAL: {
+            const int th = threads_for(NL, p.logpx);
+            switch (p.logpx) {
+                case 0: k_xinv_local<0, true><<<gx, th, smem_for(NL, 0), s>>>(p, a); break;
+                case 1: k_xinv_local<1, true><<<gx, th, smem_for(NL, 1), s>>>(p, a); break;
+                case 2: k_xinv_local<2, true><<<gx, th, smem_for(NL, 2), s>>>(p, a); break;
+                case 3: k_xinv_local<3, true><<<gx, th, smem_for(NL, 3), s>>>(p, a); break;
+                case 4: k_xinv_local<4, true><<<gx, th, smem_for(NL, 4), s>>>(p, a); break;
+                case 5: k_xinv_local<5, true><<<gx, th, smem_for(NL, 5), s>>>(p, a); break;
+                case 6: k_xinv_local<6, true><<<gx, th, smem_for(NL, 6), s>>>(p, a); break;
+                case 7: k_xinv_local<7, true><<<gx, th, smem_for(NL, 7), s>>>(p, a); break;
+                case 8: k_xinv_local<8, true><<<gx, th, smem_for(NL, 8), s>>>(p, a); break;
+                case 9: k_xinv_local<9, true><<<gx, th, smem_for(NL, 9), s>>>(p, a); break;
+                case 10: k_xinv_local<10, true><<<gx, th, smem_for(NL, 10), s>>>(p, a); break;
+                case 11: k_xinv_local<11, true><<<gx, th, smem_for(NL, 11), s>>>(p, a); break;
+                case 12: k_xinv_local<12, true><<<gx, th, smem_for(NL, 12), s>>>(p, a); break;
+                default: return cudaErrorInvalidValue;
+            }
+            break;
+        }
+        case PASS_COMBINE2:
+            k_combine2<<<4 * 152, 256, 0, s>>>(p);
+            break;
+        case PASS_LOCAL:
+            k_xinv_local<0, false><<<gx, 256, 0, s>>>(p, a);
+            break;
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_normalize_load(const HotParams& p, const float* m_user, cudaStream_t s) {
+    k_normalize_load<<<4 * 152, 256, 0, s>>>(p, m_user);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_out(const HotParams& p, float* m_user, cudaStream_t s) {
+    k_copy_out<<<4 * 152, 256, 0, s>>>(p, m_user);
+    return cudaGetLastError();
+}
+
+}  // namespace mm

@@ -1,0 +1,146 @@
+// mm_internal.cuh - types shared by the CUDA translation units of libmm.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mm {
+
+// Device-resident integrator state (lives in the caller's workspace).  All
+// times are in internal units (1/(gamma0 Ms)); fields in units of Ms.
+struct DevState {
+    double t;             // simulated time
+    double h;             // adaptive step (RKDP)
+    double t_end;         // stop time (<= 0: none)
+    double tol;           // RKDP error bound per step
+    double torque_tol;    // relaxation target (<= 0: none)
+    double h_min;         // smallest admissible step
+    double last_err;      // last RKDP error estimate
+    double max_torque;    // max |m x h| of the last accepted state
+    double energy_acc;    // sum of energy densities (EVAL mode)
+    unsigned long long kre_bits;  // max |Re K^| seen by the kernel setup (double bits)
+    unsigned long long kim_bits;  // max |Im K^| seen by the kernel setup (double bits)
+    long long step_index; // thermal clock (Euler/Heun)
+    long long accepted;
+    long long rejected;
+    long long evals;
+    unsigned int err_bits;     // atomicMax of non-negative float bits
+    unsigned int torque_bits;  // atomicMax of non-negative float bits
+    unsigned int blocks_done;  // last-block detection
+    unsigned int bad;          // non-finite value seen
+    int cur;              // which of the two state slots holds m_n / k1
+    int after_reject;     // previous RKDP attempt was rejected
+    int done;             // run finished (t_end, torque target, failure)
+    int status;           // 0 or a negative mm_status
+    int fixed_h;          // RKDP without step control: every step accepted, h kept
+    int pad_;
+};
+
+// Local epilogue modes (what the inverse-x kernel does with H_eff and dm/dt).
+enum LocalMode : int {
+    LM_EVAL = 0,      // write H (A/m) and dm/dt (1/s); optional energy
+    LM_K1 = 1,        // k1 = f(m_n) into the current k slot; torque check
+    LM_RK = 2,        // Dormand-Prince stage s = 2..6: k_s and m_{s+1}
+    LM_RKFINAL = 3,   // stage 7 (FSAL): k7, error, torque, step control
+    LM_EULER = 4,
+    LM_HEUN1 = 5,
+    LM_HEUN2 = 6,
+};
+
+// Where an evaluation reads its magnetisation from.
+enum Source : int {
+    SRC_PTR = 0,      // HotParams::m_eval (user array)
+    SRC_CUR = 1,      // state slot ms[cur]  (m_n)
+    SRC_NEXT = 2,     // state slot ms[1-cur] (candidate m_{n+1})
+    SRC_STAGE0 = 3,   // mstage[0]
+    SRC_STAGE1 = 4,   // mstage[1]
+    SRC_COMBINE2 = 5, // m_n + h a21 k1, also written to mstage[0]
+};
+
+struct HotParams {
+    // geometry
+    int nx, ny, nz;
+    int px, py, pz;          // FFT lengths
+    int logpx, logpy, logpz;
+    int hx;                  // px/2 + 1
+    int hyk, hzk;            // stored kernel extents along y and z (P/2 + 1)
+    int nyp;                 // y extent stored in the x-spectrum (multiple of 16)
+    int nzp;                 // z extent stored in the y-spectrum (multiple of 8)
+    int ty;                  // rows per block in the x kernels
+    int tz;                  // z lines per block in the 3-D y kernels
+    int tky;                 // ky lines per block in the 3-D z kernel
+    int kxb;                 // kx columns per block in the 2-D y kernel
+    int pbc[3];
+    int ncomp;               // 4 (nz == 1) or 6 stored kernel components
+    long long ncell;
+    // material, internal units
+    float cex[3];            // 2A/(mu0 Ms^2 d^2) per axis
+    float kan;               // 2Ku/(mu0 Ms^2)
+    float ux, uy, uz;        // easy axis
+    float hzx, hzy, hzz;     // B/(mu0 Ms)
+    float alpha;
+    float llpref;            // 1/(1+alpha^2)
+    float sigma_th;          // thermal sigma / Ms for the current dt (0: off)
+    unsigned long long seed;
+    long long thermal_step;  // EVAL-mode thermal clock
+    int demag;
+    // step (internal units)
+    double dt_d;             // Euler/Heun fixed step
+    // output scales
+    float h_scale;           // Ms (A/m)
+    float t_scale;           // gamma0 Ms (1/s)
+    // buffers
+    const float2* tw;
+    const float* kt;
+    float2* s1;
+    float2* s2;
+    DevState* st;
+    float* ms[2];
+    float* ks[2];
+    float* kb[8];            // k2..k6 at kb[2..6]
+    float* mstage[2];
+    const float* m_eval;
+    float* h_out;
+    float* tq_out;
+    int want_energy;
+};
+
+struct LaunchArgs {
+    int src;                 // Source of the evaluation input
+    int mode;                // LocalMode
+    int stage;               // RK stage (2..7)
+};
+
+// passes of one evaluation (the kernels of hotpath.cu), in launch order
+enum Pass : int {
+    PASS_XFWD = 0, PASS_YCONV = 1, PASS_YFWD = 2, PASS_ZCONV = 3, PASS_YINV = 4,
+    PASS_XINV_LOCAL = 5, PASS_COMBINE2 = 6, PASS_LOCAL = 7, NPASS = 8
+};
+
+// hot path (hotpath.cu)
+cudaError_t launch_normalize_load(const HotParams& p, const float* m_user, cudaStream_t s);
+cudaError_t launch_copy_out(const HotParams& p, float* m_user, cudaStream_t s);
+int eval_passes(const HotParams& p, const LaunchArgs& a, int* ids);     // fills <= 5 pass ids
+cudaError_t launch_pass(const HotParams& p, const LaunchArgs& a, int pass, cudaStream_t s);
+cudaError_t configure_hot_kernels();
+
+// kernel setup (setup.cu)
+struct SetupParams {
+    int nx, ny, nz;
+    int px, py, pz;
+    int ox, oy, oz;          // octant extents of the real-space tensor
+    int pbc[3];
+    int images;
+    int ncomp;
+    int hx, hyk, hzk;
+    double dx, dy, dz;       // cell edges scaled so that max edge = 1
+    double gl_t[4][8];       // Gauss-Legendre nodes on [-1, 1] for the orders below
+    double gl_w[4][8];
+    int gl_n[4];             // node counts, increasing; gl_n[3] used nearest
+    double* oct;             // [6][oz][oy][ox] FP64 tensor octant
+    double2* work;           // px*py*pz complex FP64 scratch
+    float* kt;               // [ncomp][hx][hyk][hzk] float32 result
+    DevState* st;
+};
+cudaError_t launch_kernel_setup(const SetupParams& p, cudaStream_t s);
+
+}  // namespace mm

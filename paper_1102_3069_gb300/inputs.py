@@ -1,0 +1,110 @@
+"""Seeded synthetic inputs shared by the tests, the bench and the oracle runs.
+
+This module holds no step of the method: only geometries, material constants
+and initial magnetisations drawn from numpy's PCG64 with a given seed.  Arrays
+are float32 with shape (3, nz, ny, nx) (component, z, y, x; x fastest), unit
+vectors.  The named workloads follow the configurations the solver is
+measured on:
+
+* ``film_64x16``      64 x 16 x 1 cells of 4 nm, Ms 8.6e5 A/m, A 1.3e-11 J/m,
+                      Ku 0, alpha 0.02, Bz = 10 mT, random unit vectors;
+* ``film_1024x1024``  1024 x 1024 x 1 cells of 4 x 4 x 2 nm, Ms 8e5 A/m,
+                      A 1.3e-11 J/m, Ku 5e3 J/m^3 along x, alpha 0.01, open
+                      boundaries, vortex-plus-noise start, applied field of
+                      magnitude U[0, 50] mT in a uniformly random direction;
+* ``cube_256x256x64`` 256 x 256 x 64 cells of 3 nm, periodic in x and y,
+                      Ms 1.1e6 A/m, A 2e-11 J/m, Ku 2e4 J/m^3 (uniform easy
+                      axis tilted by U[0, 30] deg from z), alpha 0.05, 300 K,
+                      Heun with dt = 50 fs;
+* ``table1_N2`` / ``table1_N3``  square and cubic grids of the Euler-step
+                      timing table, 4 nm cells with the film_1024x1024
+                      material.
+"""
+
+import numpy as np
+
+
+def rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def random_unit(shape, seed):
+    """m = normalised N(0, I3) per cell; shape = (nx, ny, nz)."""
+    nx, ny, nz = shape
+    g = rng(seed)
+    m = g.standard_normal((3, nz, ny, nx))
+    m /= np.sqrt((m * m).sum(axis=0, keepdims=True))
+    return m.astype(np.float32)
+
+
+def vortex_noise(shape, cell, seed, core_radius=10e-9, noise=0.05, chirality=1, polarity=1):
+    """In-plane curling state with an out-of-plane core exp(-(r/r0)^2), plus
+    N(0, noise^2) per component, normalised."""
+    nx, ny, nz = shape
+    dx, dy, _ = cell
+    x = (np.arange(nx) - (nx - 1) / 2.0) * dx
+    y = (np.arange(ny) - (ny - 1) / 2.0) * dy
+    X, Y = np.meshgrid(x, y, indexing="xy")            # (ny, nx)
+    r = np.sqrt(X * X + Y * Y)
+    mz = polarity * np.exp(-(r / core_radius) ** 2)
+    phi = np.arctan2(Y, X)
+    s = np.sqrt(np.clip(1.0 - mz * mz, 0.0, 1.0))
+    mx = -chirality * np.sin(phi) * s
+    my = chirality * np.cos(phi) * s
+    m = np.stack([mx, my, mz])[:, None, :, :].repeat(nz, axis=1)
+    g = rng(seed)
+    m = m + noise * g.standard_normal(m.shape)
+    m /= np.sqrt((m * m).sum(axis=0, keepdims=True))
+    return m.astype(np.float32)
+
+
+def smooth_tilt(shape):
+    """Smooth large-amplitude state along +x with long-wavelength tilts
+    (m_y ~ 0.4 sin(2 pi x/Lx) + 0.2 cos(pi y/Ly), m_z ~ 0.3 sin(pi x/Lx) sin(pi y/Ly)),
+    normalised.  Its dynamics are not chaotic: a 1e-7 perturbation of it stays at
+    the 1e-7 level for 1000 Dormand-Prince steps of 100 fs on the 64 x 16 film,
+    whereas from random unit vectors it grows to O(1)."""
+    nx, ny, nz = shape
+    x = (np.arange(nx) + 0.5) / nx
+    y = (np.arange(ny) + 0.5) / ny
+    X, Y = np.meshgrid(x, y)
+    m = np.stack([np.ones_like(X), 0.4 * np.sin(2 * np.pi * X) + 0.2 * np.cos(np.pi * Y),
+                  0.3 * np.sin(np.pi * X) * np.sin(np.pi * Y)])[:, None, :, :].repeat(nz, axis=1)
+    m /= np.sqrt((m * m).sum(axis=0, keepdims=True))
+    return m.astype(np.float32)
+
+
+def random_direction(g):
+    v = g.standard_normal(3)
+    return v / np.linalg.norm(v)
+
+
+def workload(name, seed=0):
+    """Geometry, material and initial m of a named workload (dict)."""
+    g = rng(seed + 1000)
+    if name == "film_64x16":
+        shape, cell = (64, 16, 1), (4e-9, 4e-9, 4e-9)
+        mat = dict(Ms=8.6e5, Aex=1.3e-11, Ku=0.0, easy_axis=(1.0, 0.0, 0.0), alpha=0.02, B=(0.0, 0.0, 0.01))
+        return dict(name=name, shape=shape, cell=cell, pbc=(0, 0, 0), material=mat, m=random_unit(shape, seed))
+    if name == "film_1024x1024":
+        shape, cell = (1024, 1024, 1), (4e-9, 4e-9, 2e-9)
+        B = tuple(float(v) for v in g.uniform(0.0, 0.05) * random_direction(g))
+        mat = dict(Ms=8e5, Aex=1.3e-11, Ku=5e3, easy_axis=(1.0, 0.0, 0.0), alpha=0.01, B=B)
+        return dict(name=name, shape=shape, cell=cell, pbc=(0, 0, 0), material=mat,
+                    m=vortex_noise(shape, cell, seed))
+    if name == "cube_256x256x64":
+        shape, cell = (256, 256, 64), (3e-9, 3e-9, 3e-9)
+        th = np.deg2rad(g.uniform(0.0, 30.0))
+        ph = g.uniform(0.0, 2 * np.pi)
+        u = (float(np.sin(th) * np.cos(ph)), float(np.sin(th) * np.sin(ph)), float(np.cos(th)))
+        mat = dict(Ms=1.1e6, Aex=2e-11, Ku=2e4, easy_axis=u, alpha=0.05, temperature=300.0, seed=seed,
+                   B=(0.0, 0.0, 0.0))
+        return dict(name=name, shape=shape, cell=cell, pbc=(1, 1, 0), material=mat, m=random_unit(shape, seed),
+                    dt=50e-15)
+    if name.startswith("table1_N2_") or name.startswith("table1_N3_"):
+        n = int(name.rsplit("_", 1)[1])
+        shape = (n, n, 1) if name.startswith("table1_N2_") else (n, n, n)
+        cell = (4e-9, 4e-9, 4e-9)
+        mat = dict(Ms=8e5, Aex=1.3e-11, Ku=5e3, easy_axis=(1.0, 0.0, 0.0), alpha=0.01, B=(0.0, 0.0, 0.01))
+        return dict(name=name, shape=shape, cell=cell, pbc=(0, 0, 0), material=mat, m=random_unit(shape, seed))
+    raise KeyError(name)

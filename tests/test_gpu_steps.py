@@ -1,0 +1,211 @@
+"""GPU time steps (Euler, Heun, Dormand-Prince; fixed and adaptive; relaxation)
+vs the FP64 oracle, plus the failure paths (non-finite state, step-size
+underflow, unreached torque bound) reported as status codes."""
+
+import numpy as np
+import pytest
+
+from oracle import llg
+from paper_1102_3069_gb300 import binding as B
+from paper_1102_3069_gb300 import inputs
+
+from gpu_util import oracle, solver, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+W = inputs.workload("film_64x16")
+
+
+def _pair(w=W, demag=True, **over):
+    mat = dict(w["material"])
+    mat.update(over)
+    s = solver(w["shape"], w["cell"], pbc=w["pbc"], demag=demag, **mat)
+    p = oracle(w["shape"], w["cell"], pbc=w["pbc"], demag=demag, **mat)
+    return s, p
+
+
+def _m64(m):
+    m = m.astype(np.float64)
+    return m / np.sqrt((m * m).sum(axis=0, keepdims=True))
+
+
+@pytest.mark.parametrize("method,dt", [(B.MM_EULER, 1e-14), (B.MM_HEUN, 5e-14), (B.MM_RKDP, 1e-13)])
+def test_single_step(method, dt):
+    s, p = _pair()
+    m = W["m"]
+    md = to_dev(m)
+    acc, t, dt_next = B.mm_step(s.ctx, md, method, 0.0, dt, tol=1.0)
+    assert acc
+    assert t == pytest.approx(dt, rel=1e-12)
+    m0 = _m64(m)
+    if method == B.MM_EULER:
+        ref = llg.euler_step(p, m0, dt)
+    elif method == B.MM_HEUN:
+        ref = llg.heun_step(p, m0, dt)
+    else:
+        ref = llg.rkdp_stages(p, m0, dt)[0]
+    assert np.max(np.abs(to_np(md) - ref)) <= 1e-6
+
+
+def test_thermal_heun_steps_match_oracle():
+    w = inputs.workload("film_64x16")
+    s, p = _pair(w, temperature=300.0, seed=77, alpha=0.05)
+    m = w["m"]
+    md = to_dev(m)
+    dt = 20e-15
+    ref = _m64(m)
+    t = 0.0
+    for k in range(5):
+        acc, t, _ = B.mm_step(s.ctx, md, B.MM_HEUN, t, dt)
+        ref = llg.heun_step(p, ref, dt, step=k)
+    assert np.max(np.abs(to_np(md) - ref)) <= 2e-6
+
+
+def _fixed_run(m, nsteps, h=1e-13):
+    s, p = _pair()
+    md = to_dev(m)
+    B.mm_load(s.ctx, md)
+    B.mm_advance(s.ctx, B.MM_RKDP, nsteps, dt_s=h, tol=-1.0)
+    B.mm_store(s.ctx, md)
+    st = B.mm_get_stats(s.ctx)
+    assert st["accepted"] == nsteps and st["rejected"] == 0
+    assert st["t"] == pytest.approx(nsteps * h, rel=1e-12)
+    ref = llg.rkdp_fixed(p, _m64(m), h, nsteps)
+    return float(np.max(np.abs(to_np(md) - ref))), float(np.max(np.abs(ref - _m64(m))))
+
+
+def test_thousand_fixed_rkdp_steps():
+    """max |dm| <= 1e-5 after 1000 fixed Dormand-Prince steps of 100 fs on the
+    64 x 16 film, from a smooth state whose trajectory is not chaotic (it moves
+    by O(1) over the run)."""
+    err, moved = _fixed_run(inputs.smooth_tilt(W["shape"]), 1000)
+    print("max|dm| after 1000 fixed steps:", err, "state moved by", moved)
+    assert moved > 0.5
+    assert err <= 1e-5
+
+
+def test_fixed_rkdp_steps_from_random_state():
+    """From random unit vectors (alpha 0.02) the trajectory is chaotic: the FP64
+    oracle alone turns a 1e-7 perturbation into 6e-5 after 200 steps and O(1)
+    after 700.  The float32 path is held to 1e-5 over the first 50 steps."""
+    err, _ = _fixed_run(W["m"], 50)
+    print("max|dm| after 50 fixed steps from the random state:", err)
+    assert err <= 1e-5
+
+
+def test_adaptive_run_to_1ns_smooth_state():
+    s, p = _pair()
+    m = inputs.smooth_tilt(W["shape"])
+    md = to_dev(m)
+    B.mm_load(s.ctx, md)
+    B.mm_advance(s.ctx, B.MM_RKDP, 100000, dt_s=1e-13, tol=1e-6, t_end_s=1e-9)
+    B.mm_store(s.ctx, md)
+    st = B.mm_get_stats(s.ctx)
+    assert st["done"] == 1 and st["status"] == 0
+    assert st["t"] == pytest.approx(1e-9, rel=1e-12)
+    ref = llg.Stepper(p, _m64(m), h0=1e-13, tol=1e-6)
+    ref.run_until(1e-9)
+    mg = to_np(md)
+    print("steps gpu", st["accepted"], st["rejected"], "oracle", ref.accepted, ref.rejected,
+          "max|dm|", np.max(np.abs(mg - ref.m)))
+    assert abs(st["accepted"] - ref.accepted) <= 0.02 * ref.accepted + 2
+    assert np.max(np.abs(mg - ref.m)) <= 1e-4
+
+
+def test_adaptive_run_to_1ns_random_state():
+    """The 64 x 16 film from random unit vectors, RKDP tol 1e-6 for 1 ns: the
+    trajectory is chaotic, so only run-level quantities are compared."""
+    s, p = _pair()
+    m = W["m"]
+    md = to_dev(m)
+    B.mm_load(s.ctx, md)
+    B.mm_advance(s.ctx, B.MM_RKDP, 100000, dt_s=1e-13, tol=1e-6, t_end_s=1e-9)
+    B.mm_store(s.ctx, md)
+    st = B.mm_get_stats(s.ctx)
+    assert st["done"] == 1 and st["status"] == 0
+    assert st["t"] == pytest.approx(1e-9, rel=1e-12)
+    ref = llg.Stepper(p, _m64(m), h0=1e-13, tol=1e-6)
+    ref.run_until(1e-9)
+    mg = to_np(md)
+    print("steps gpu", st["accepted"], st["rejected"], "oracle", ref.accepted, ref.rejected)
+    assert abs(st["accepted"] - ref.accepted) <= 0.10 * ref.accepted
+    assert np.max(np.abs(np.sqrt((mg * mg).sum(axis=0)) - 1.0)) <= 1e-6
+    E0, Eg, Eo = p.energy(_m64(m)), p.energy(mg), p.energy(ref.m)
+    assert Eg < E0 and Eo < E0
+    assert abs(Eg - Eo) <= 0.05 * abs(E0 - Eo)
+
+
+def test_relax_reaches_bound_and_oracle_energy():
+    w = dict(W)
+    w["shape"] = (32, 8, 1)
+    m = inputs.random_unit(w["shape"], 5)
+    s, p = _pair(w, alpha=1.0)
+    md = to_dev(m)
+    steps, tq = B.mm_relax(s.ctx, md, torque_tol=1e-4, err_tol=1e-5, max_steps=20000)
+    assert tq < 1e-4
+    mg = to_np(md)
+    assert p.torque(mg) < 2e-4          # float32 state re-evaluated in float64
+    mo, _, _ = llg.relax(p, _m64(m), torque_tol=1e-4, tol=1e-5)
+    Eg, Eo = p.energy(mg), p.energy(mo)
+    assert Eg <= Eo + 1e-5 * abs(Eo)
+
+
+def test_nonfinite_state_stops_with_status():
+    s, _ = _pair()
+    m = W["m"].copy()
+    m[:, 0, 3, 5] = np.nan
+    md = to_dev(m)
+    with pytest.raises(B.MMError) as e:
+        B.mm_step(s.ctx, md, B.MM_RKDP, 0.0, 1e-13, tol=1e-6)
+    assert e.value.code == B.MM_ENONFINITE
+
+
+def test_step_size_underflow_is_reported():
+    s, _ = _pair()
+    md = to_dev(W["m"])
+    B.mm_load(s.ctx, md)
+    B.mm_advance(s.ctx, B.MM_RKDP, 200, dt_s=1e-13, tol=1e-30)
+    st = B.mm_get_stats(s.ctx)
+    assert st["status"] == B.MM_ENOTCONVERGED and st["done"] == 1
+    assert st["rejected"] > 5 and st["accepted"] == 0
+
+
+def test_relax_budget_exhausted():
+    s, _ = _pair(alpha=1.0)
+    md = to_dev(W["m"])
+    with pytest.raises(B.MMError) as e:
+        B.mm_relax(s.ctx, md, torque_tol=1e-9, err_tol=1e-5, max_steps=10)
+    assert e.value.code == B.MM_ENOTCONVERGED
+
+
+def test_thermal_with_adaptive_method_is_refused():
+    s, _ = _pair(temperature=300.0)
+    md = to_dev(W["m"])
+    B.mm_load(s.ctx, md)
+    with pytest.raises(B.MMError) as e:
+        B.mm_advance(s.ctx, B.MM_RKDP, 1, dt_s=1e-13, tol=1e-6)
+    assert e.value.code == B.MM_EINVAL
+
+
+def test_eval_without_kernel_is_refused():
+    ctx = B.mm_init_geometry(8, 8, 1, 4e-9, 4e-9, 4e-9)
+    import torch
+    ws = torch.empty(B.mm_workspace_bytes(ctx) + 256, dtype=torch.uint8, device="cuda")
+    B.mm_set_workspace(ctx, (ws.data_ptr() + 255) // 256 * 256, B.mm_workspace_bytes(ctx))
+    B.mm_set_material(ctx, Ms=8e5, Aex=1.3e-11)
+    m = to_dev(inputs.random_unit((8, 8, 1), 0))
+    with pytest.raises(B.MMError) as e:
+        B.mm_eval_heff(ctx, m, torch.empty_like(m))
+    assert e.value.code == B.MM_ESTATE
+    B.mm_destroy(ctx)
+
+
+def test_host_buffer_run_matches_device_run():
+    s, _ = _pair()
+    mh = W["m"].copy()
+    B.mm_run_host(s.ctx, mh, B.MM_RKDP, 5, dt_s=1e-13, tol=1e-6)
+    md = to_dev(W["m"])
+    B.mm_load(s.ctx, md)
+    B.mm_advance(s.ctx, B.MM_RKDP, 5, dt_s=1e-13, tol=1e-6)
+    B.mm_store(s.ctx, md)
+    assert np.array_equal(mh, md.cpu().numpy())
