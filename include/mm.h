@@ -208,6 +208,38 @@ enum { MM_NPASS = 8 };
 int mm_profile(mm_ctx* ctx, int enable);
 int mm_pass_times(mm_ctx* ctx, double* ms_out, long long* count_out);
 
+/*
+ * Allocation-free variant of mm_eval_heff (the paper has no counterpart).
+ *
+ * For callers that cannot allocate device memory at the point where they need
+ * a field evaluation: code running inside a host application or plugin that
+ * owns the whole device-memory budget and hands out only the buffers it
+ * created, and time-critical loops that forbid cudaMalloc after start-up
+ * because an allocation can block or synchronise the device.
+ *
+ * Same inputs and outputs as mm_eval_heff (m read-only; h_out in A/m and
+ * torque_out in 1/s, each may be NULL; no energy), but the scratch it needs -
+ * the FFT spectra, the twiddle table and the reduction counters - lives in
+ * one static device array of MM_STATIC_SCRATCH_BYTES per GPU, which every
+ * GPU that loads the library holds until the process exits.  The call
+ * allocates nothing (no cudaMalloc, cudaFree or allocating library routine).
+ *  - The context needs its material; with the magnetostatic term enabled it
+ *    also needs its kernel (mm_demag_kernel, which lives in the caller's
+ *    workspace); with mm_set_demag(ctx, 0) no workspace is needed at all.
+ *  - Grids whose spectra do not fit in the static scratch (roughly up to
+ *    1024 x 512 x 1 cells) are rejected with MM_ENOMEM and a message.
+ *  - The first call on a device looks up the array's device address and
+ *    fills its twiddle table (with that device current); make that first call
+ *    before any stream capture.
+ *  - All calls on a device share the one array and it keeps the last call's
+ *    contents (the counters are cleared on every call): calls whose work
+ *    overlaps on the GPU - on different streams, or from several contexts -
+ *    race with each other.  Serialise them.
+ * Asynchronous on the context's stream.
+ */
+#define MM_STATIC_SCRATCH_BYTES (16u << 20)
+int mm_eval_heff_static(mm_ctx* ctx, const float* m, float* h_out, float* torque_out);
+
 /* Message describing the last failure of a call on this context (never NULL). */
 const char* mm_last_error(const mm_ctx* ctx);
 

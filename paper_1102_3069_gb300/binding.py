@@ -60,6 +60,7 @@ _SIGS = {
     "mm_step": (_i, [_vp, _vp, _i, _dp, _dp, _d, ctypes.POINTER(_i)]),
     "mm_relax": (_i, [_vp, _vp, _d, _d, _l, ctypes.POINTER(_l), _dp]),
     "mm_run_host": (_i, [_vp, _vp, _i, _l, _d, _d]),
+    "mm_eval_heff_static": (_i, [_vp, _vp, _vp, _vp]),
     "mm_profile": (_i, [_vp, _i]),
     "mm_pass_times": (_i, [_vp, _dp, ctypes.POINTER(ctypes.c_longlong)]),
     "mm_last_error": (ctypes.c_char_p, [_vp]),
@@ -164,6 +165,11 @@ def mm_eval_heff(ctx, m, h_out=None, torque_out=None, energy=False):
     e = ctypes.c_double(0.0)
     _check(ctx, lib().mm_eval_heff(ctx, _ptr(m), _ptr(h_out), _ptr(torque_out), ctypes.byref(e) if energy else None))
     return e.value if energy else None
+
+
+def mm_eval_heff_static(ctx, m, h_out=None, torque_out=None):
+    """Allocation-free evaluation: scratch in the library's static device array."""
+    return _check(ctx, lib().mm_eval_heff_static(ctx, _ptr(m), _ptr(h_out), _ptr(torque_out)))
 
 
 def mm_set_thermal_clock(ctx, step_index, dt_s):

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -217,6 +218,40 @@ int eval(mm_ctx* ctx, const mm::HotParams& p, int src, int mode, int stage) {
             ctx->prof.push_back({ids[i], e0, e1});
         }
     }
+    return MM_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Scratch for mm_eval_heff_static: one fixed array per GPU, reserved when the
+// library's module is loaded on that device and held until the process exits.
+// Layout: [DevState | twiddle table | x spectrum | y spectrum (3-D only)].
+static __device__ __align__(256) unsigned char g_static_scratch[MM_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mutex;
+void* g_static_ptr[kMaxDevices] = {nullptr};
+
+// Once per device, with that device current: look up the device address of
+// the scratch array (in host code its name is only a host-side stand-in) and
+// fill the constant twiddle table it carries.
+int static_scratch_for_current_device(mm_ctx* ctx, char** out) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(ctx, MM_EINVAL, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_ptr[dev]) {
+        void* ptr = nullptr;
+        CK(cudaGetSymbolAddress(&ptr, g_static_scratch));
+        CK(mm::configure_hot_kernels());
+        CK(cudaMemcpy(static_cast<char*>(ptr) + align256(sizeof(mm::DevState)), ctx->tw_host.data(),
+                      mmfft::TWN * sizeof(float2), cudaMemcpyHostToDevice));
+        g_static_ptr[dev] = ptr;
+    }
+    *out = static_cast<char*>(g_static_ptr[dev]);
     return MM_OK;
 }
 
@@ -650,6 +685,51 @@ void mm_destroy(mm_ctx* ctx) {
         cudaEventDestroy(r.b);
     }
     delete ctx;
+}
+
+int mm_eval_heff_static(mm_ctx* ctx, const float* m, float* h_out, float* torque_out) {
+    if (!ctx) return MM_EINVAL;
+    if (!ctx->have_material) return fail(ctx, MM_ESTATE, "material not set (mm_set_material)");
+    if (ctx->demag && !ctx->kernel_ready)
+        return fail(ctx, MM_ESTATE, "demag kernel not built (mm_demag_kernel) or demag not disabled");
+    if (!m) return fail(ctx, MM_EINVAL, "null m");
+    const size_t off_tw = align256(sizeof(mm::DevState));
+    const size_t off_s1 = off_tw + align256((size_t)mmfft::TWN * sizeof(float2));
+    const size_t off_s2 = off_s1 + align256(ctx->sz_s1);
+    const size_t need = ctx->demag ? off_s2 + align256(ctx->sz_s2) : off_s1;    // no spectra without demag
+    if (need > (size_t)MM_STATIC_SCRATCH_BYTES) {
+        char buf[200];
+        std::snprintf(buf, sizeof(buf),
+                      "grid needs %zu bytes of scratch; the static scratch of mm_eval_heff_static holds %zu bytes "
+                      "(MM_STATIC_SCRATCH_BYTES): use mm_eval_heff with a workspace", need,
+                      (size_t)MM_STATIC_SCRATCH_BYTES);
+        return fail(ctx, MM_ENOMEM, buf);
+    }
+    char* base = nullptr;
+    int rc = static_scratch_for_current_device(ctx, &base);
+    if (rc) return rc;
+    const double tu = ctx->gamma0 * ctx->Ms;
+    mm::HotParams p = hot_params(ctx, ctx->th_dt * tu, true);
+    // everything the evaluation writes besides its outputs lives in the static array
+    p.st = reinterpret_cast<mm::DevState*>(base);
+    p.tw = reinterpret_cast<const float2*>(base + off_tw);
+    p.s1 = reinterpret_cast<float2*>(base + off_s1);
+    p.s2 = reinterpret_cast<float2*>(base + off_s2);
+    p.kt = ctx->demag ? reinterpret_cast<const float*>(ctx->ws + ctx->off_kt) : nullptr;
+    for (int i = 0; i < 2; ++i) { p.ms[i] = nullptr; p.ks[i] = nullptr; p.mstage[i] = nullptr; }
+    for (int j = 0; j < 8; ++j) p.kb[j] = nullptr;
+    p.m_eval = m;
+    p.h_out = h_out;
+    p.tq_out = torque_out;
+    p.want_energy = 0;
+    p.thermal_step = (long long)ctx->th_step;
+    // the reduction counters must start at zero; the spectra are fully rewritten
+    CK(cudaMemsetAsync(base, 0, sizeof(mm::DevState), ctx->stream));
+    mm::LaunchArgs a{mm::SRC_PTR, mm::LM_EVAL, 0};
+    int ids[8];
+    const int n = mm::eval_passes(p, a, ids);
+    for (int i = 0; i < n; ++i) CK(mm::launch_pass(p, a, ids[i], ctx->stream));
+    return MM_OK;
 }
 
 }  // extern "C"
