@@ -45,7 +45,7 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms while running."""
 
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -59,7 +59,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -127,25 +127,31 @@ def _traffic_for(kernel):
 
 
 def algorithmic_bytes(nx, ny):
-    """Bytes each pass must move per launch (2-D open film, FP32, Sec. 3.2 pass layout)."""
+    """Bytes each pass must move per launch (2-D open film, FP32, Sec. 3.2 pass layout).
+
+    One RKDP step = x forward of the stage-2 input, then six evaluations: y
+    column pass each, inverse x + local terms fused with the next stage's
+    forward x transform for stages 2-6, and the plain inverse x + local terms
+    + error/torque reductions for stage 7.
+    """
     N = nx * ny
     px, py = 2 * nx, 2 * ny
     hx = px // 2 + 1
     spec = 3 * hx * ny * 8                 # half spectrum of the valid rows, complex64
     kern = 4 * hx * (py // 2 + 1) * 4      # real kernel octant, 4 components
     m = 12 * N
-    # local pass: spectrum + m_s + per-stage reads of m_n and earlier k's + writes of k_s, m_{s+1}
-    # stage s = 2..6: reads m_n, k_1..k_{s-1} (k2 unused from stage 6 on); stage 7: k1, k3..k6
-    reads = {2: 2, 3: 3, 4: 4, 5: 5, 6: 5, 7: 5}
-    writes = {2: 2, 3: 2, 4: 2, 5: 2, 6: 2, 7: 1}
-    loc = [spec + m + 12 * N * (reads[s] + writes[s]) for s in range(2, 8)]
-    xf = [spec + m] * 6
-    xf[0] = spec + 3 * m                   # stage 2 combines m_n + h a21 k1 and writes m_2
+    # stage s = 2..6 reads m_s (halo), m_n and k_1..k_{s-1} (k2 unused from stage 6 on),
+    # writes k_s and m_{s+1}; stage 7 reads m_7, k1, k3..k6 and writes k7
+    reads = {2: 2, 3: 3, 4: 4, 5: 5, 6: 5}
+    fused = [spec + m + m * (reads[s] + 2) + spec for s in range(2, 7)]
+    final = spec + m + m * 5 + m
+    xf = spec + 3 * m                      # stage 2 input m_n + h a21 k1, written out as m_2
     return {
-        "k_xfwd": sum(xf) / 6.0,
+        "k_xfwd": float(xf),
         "k_yconv": float(2 * spec + kern),
-        "k_xinv_local": sum(loc) / 6.0,
-        "step": float(sum(xf) + 6 * (2 * spec + kern) + sum(loc)),
+        "k_xinv_local_fused": sum(fused) / 5.0,
+        "k_xinv_local": float(final),
+        "step": float(xf + 6 * (2 * spec + kern) + sum(fused) + final),
     }
 
 
@@ -197,7 +203,7 @@ def run_gpu(args):
         assert st1["status"] == 0, st1
 
         # per-pass durations over a second timed region of the same steps
-        passes = B.pass_times(ctx, lambda: B.mm_advance(ctx, B.MM_RKDP, args.steps, dt_s=0.0, tol=1e-6))
+        passes = B.pass_times(ctx, lambda: B.mm_advance(ctx, B.MM_RKDP, min(args.steps, 200), dt_s=0.0, tol=1e-6))
 
         # end to end through the host-buffer entry point: H2D + step + D2H per step
         mh = torch.from_numpy(w["m"]).pin_memory()
@@ -230,7 +236,8 @@ def run_gpu(args):
 
     hbm, peak_kind = _peaks()
     ab = algorithmic_bytes(nx, ny)
-    dom = max(("k_xfwd", "k_yconv", "k_xinv_local"), key=lambda k: passes.get(k, {}).get("ms_per_launch", 0.0))
+    # dominant pass = largest share of the step time
+    dom = max((k for k in passes if k in ab), key=lambda k: passes[k]["ms_total"])
     dms = passes[dom]["ms_per_launch"]
     achieved = ab[dom] / (dms * 1e-3) / 1e9
     step_bytes = ab["step"]
@@ -248,9 +255,9 @@ def run_gpu(args):
         "step_roofline": {"bytes_per_step": step_bytes, "achieved_gbs": step_bytes / (gpu_ms / args.steps * 1e-3) / 1e9,
                           "frac": step_bytes / (gpu_ms / args.steps * 1e-3) / 1e9 / hbm},
         "passes": passes,
-        "ns_simulated_per_hour": sim_t * 1e9 / (t_wall / 3600.0) if t_wall > 0 else None,
+        "ns_simulated_per_hour": sim_t * 1e9 / (gpu_ms * 1e-3 / 3600.0) if gpu_ms > 0 else None,
         "clocks": clk.summary(),
-        "gpu_launches": int(args.steps * (3 * EVALS_PER_STEP)),
+        "gpu_launches": int(args.steps * (2 * EVALS_PER_STEP + 1)),
         "e2e": {"value": ev_total * N / te if te > 0 else None, "unit": UNIT,
                 "h2d_bytes_per_step": 12 * N, "d2h_bytes_per_step": 12 * N,
                 "note": "mm_run_host: pinned host m in, one RKDP step (7 evaluations: fresh k1 + 6), m out"},
@@ -320,8 +327,8 @@ def cpu_baseline_sample(seconds=20.0):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

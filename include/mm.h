@@ -202,9 +202,10 @@ int mm_run_host(mm_ctx* ctx, float* m_host, int method, long nsteps, double dt_s
  * per pass, the summed event time in ms and the number of launches since
  * mm_profile(ctx, 1); arrays of MM_NPASS entries in the order
  * x forward, y conv (2-D), y forward, z conv, y inverse (3-D), x inverse +
- * local terms, stage-2 combine, local terms without demag.
+ * local terms, stage-2 combine, local terms without demag, x inverse + local
+ * terms + forward x transform of the next stage's input.
  */
-enum { MM_NPASS = 8 };
+enum { MM_NPASS = 9 };
 int mm_profile(mm_ctx* ctx, int enable);
 int mm_pass_times(mm_ctx* ctx, double* ms_out, long long* count_out);
 

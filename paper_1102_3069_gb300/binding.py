@@ -217,7 +217,9 @@ def mm_run_host(ctx, m_host, method, nsteps, dt_s=0.0, tol=1e-6):
     return _check(ctx, lib().mm_run_host(ctx, _ptr(m_host), int(method), int(nsteps), float(dt_s), float(tol)))
 
 
-PASS_NAMES = ["k_xfwd", "k_yconv", "k_yfwd", "k_zconv", "k_yinv", "k_xinv_local", "k_combine2", "k_local"]
+PASS_NAMES = ["k_xfwd", "k_yconv", "k_yfwd", "k_zconv", "k_yinv", "k_xinv_local", "k_combine2", "k_local",
+              "k_xinv_local_fused"]
+NPASS = len(PASS_NAMES)
 
 
 def mm_profile(ctx, enable):
@@ -225,11 +227,11 @@ def mm_profile(ctx, enable):
 
 
 def mm_pass_times(ctx):
-    ms = (ctypes.c_double * 8)()
-    n = (ctypes.c_longlong * 8)()
+    ms = (ctypes.c_double * NPASS)()
+    n = (ctypes.c_longlong * NPASS)()
     _check(ctx, lib().mm_pass_times(ctx, ms, n))
     return {PASS_NAMES[i]: {"ms_total": ms[i], "launches": n[i],
-                            "ms_per_launch": ms[i] / n[i] if n[i] else 0.0} for i in range(8) if n[i]}
+                            "ms_per_launch": ms[i] / n[i] if n[i] else 0.0} for i in range(NPASS) if n[i]}
 
 
 def pass_times(ctx, fn):

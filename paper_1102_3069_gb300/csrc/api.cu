@@ -75,6 +75,9 @@ struct mm_ctx {
     bool k1_valid = false;
     bool rk_h_set = false;          // an RKDP step size has been given since mm_load
     int last_method = 0;
+    // what the x spectrum in the workspace currently holds: nothing usable, the
+    // transform of m_n (ms[cur]) or of the Dormand-Prince stage-2 input m_2
+    enum { SPEC_NONE, SPEC_MCUR, SPEC_M2 } spec = SPEC_NONE;
     double last_fixed_dt = 0.0;     // internal units
     long long step_counter = 0;
     uint64_t th_step = 0;
@@ -201,8 +204,9 @@ __global__ void k_set_run(mm::DevState* st, double tol, double t_end, double tor
     if (st->t_end > 0.0 && st->h > st->t_end - st->t) st->h = st->t_end - st->t;
 }
 
-int eval(mm_ctx* ctx, const mm::HotParams& p, int src, int mode, int stage) {
-    mm::LaunchArgs a{src, mode, stage};
+int eval(mm_ctx* ctx, const mm::HotParams& p, int src, int mode, int stage, bool fuse = false,
+         bool have_spectrum = false) {
+    mm::LaunchArgs a{src, mode, stage, fuse ? 1 : 0, have_spectrum ? 1 : 0};
     int ids[8];
     const int n = mm::eval_passes(p, a, ids);
     for (int i = 0; i < n; ++i) {
@@ -296,18 +300,14 @@ int mm_init_geometry(mm_ctx** out, int nx, int ny, int nz, double dx, double dy,
     c->ox = pb[0] ? nx / 2 + 1 : nx;
     c->oy = pb[1] ? ny / 2 + 1 : ny;
     c->oz = pb[2] ? nz / 2 + 1 : nz;
-    // launch shapes: about 384 threads per block, one radix-16 butterfly each
-    auto nb = [](int logp) { return logp >= 4 ? (1 << logp) / 16 : 1; };
-    c->ty = 2;
-    while (c->ty < 16 && (3 * (2 * c->ty) / 2) * nb(c->logpx) <= 512) c->ty *= 2;
-    c->nyp = (ny + 15) / 16 * 16;
-    c->kxb = 1;
-    while (c->kxb < 64 && 3 * (2 * c->kxb) * nb(c->logpy) <= 512) c->kxb *= 2;
-    c->tz = 1;
-    while (c->tz < 8 && c->tz < nz && 3 * (2 * c->tz) * nb(c->logpy) <= 512) c->tz *= 2;
-    c->nzp = (nz + c->tz - 1) / c->tz * c->tz;
-    c->tky = 1;
-    while (c->tky < 64 && 3 * (2 * c->tky) * nb(c->logpz) <= 512) c->tky *= 2;
+    // launch shapes: the kernels' compile-time tiles (fft32.cuh), about 384
+    // threads per block with one radix-16 butterfly each
+    c->ty = mmfft::ty_of(c->logpx);
+    c->nyp = (ny + 15) / 16 * 16;                  // a multiple of every x-pass tile
+    c->kxb = mmfft::kxb_of(c->logpy);
+    c->tz = mmfft::tz_of(c->logpy);
+    c->nzp = (nz + c->tz - 1) / c->tz * c->tz;     // the 3-D y passes write whole z tiles
+    c->tky = mmfft::tky_of(c->logpz);
     c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
     layout(c);
     // twiddle table, rounded once from double
@@ -346,6 +346,7 @@ int mm_set_workspace(mm_ctx* ctx, void* dev_ptr, size_t bytes) {
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->kernel_ready = false;
     ctx->state_loaded = false;
+    ctx->spec = mm_ctx::SPEC_NONE;
     return MM_OK;
 }
 
@@ -415,6 +416,7 @@ int mm_demag_kernel(mm_ctx* ctx, double* out_tensor_host) {
     p.st = dstate(ctx);
     ctx->state_loaded = false;
     ctx->k1_valid = false;
+    ctx->spec = mm_ctx::SPEC_NONE;
     CK(cudaMemsetAsync(&p.st->kre_bits, 0, 2 * sizeof(unsigned long long), ctx->stream));
     CK(mm::launch_kernel_setup(p, ctx->stream));
     if (out_tensor_host) CK(cudaMemcpyAsync(out_tensor_host, p.oct, oct_bytes, cudaMemcpyDeviceToHost, ctx->stream));
@@ -457,6 +459,7 @@ int mm_eval_heff(mm_ctx* ctx, const float* m, float* h_out, float* torque_out, d
     mm::DevState* st = dstate(ctx);
     CK(cudaMemsetAsync(&st->energy_acc, 0, sizeof(double), ctx->stream));
     CK(cudaMemsetAsync(&st->status, 0, sizeof(int), ctx->stream));
+    ctx->spec = mm_ctx::SPEC_NONE;          // the evaluation reuses the spectrum buffer
     rc = eval(ctx, p, mm::SRC_PTR, mm::LM_EVAL, 0);
     if (rc) return rc;
     if (energy_J_host) {
@@ -489,6 +492,7 @@ int mm_load(mm_ctx* ctx, const float* m, double t0_s, uint64_t step_index) {
     ctx->state_loaded = true;
     ctx->k1_valid = false;
     ctx->rk_h_set = false;
+    ctx->spec = mm_ctx::SPEC_NONE;
     ctx->step_counter = (long long)step_index;
     return MM_OK;
 }
@@ -532,28 +536,34 @@ int mm_advance(mm_ctx* ctx, int method, long nsteps, double dt_s, double tol, do
                                         method == MM_RKDP && tol < 0.0 ? 1 : 0);
     CK(cudaGetLastError());
     if (method == MM_RKDP) {
+        if (dt > 0 && ctx->spec == mm_ctx::SPEC_M2) ctx->spec = mm_ctx::SPEC_NONE;   // m_2 depends on h
         if (!ctx->k1_valid) {
-            if ((rc = eval(ctx, p, mm::SRC_CUR, mm::LM_K1, 1))) return rc;
+            // k1 = f(m_n); the same pass forms m_2 and its x spectrum
+            if ((rc = eval(ctx, p, mm::SRC_CUR, mm::LM_K1, 1, true, ctx->spec == mm_ctx::SPEC_MCUR))) return rc;
             ctx->k1_valid = true;
+            ctx->spec = mm_ctx::SPEC_M2;
         }
         for (long s = 0; s < nsteps; ++s) {
-            if ((rc = eval(ctx, p, mm::SRC_COMBINE2, mm::LM_RK, 2))) return rc;
-            if ((rc = eval(ctx, p, mm::SRC_STAGE1, mm::LM_RK, 3))) return rc;
-            if ((rc = eval(ctx, p, mm::SRC_STAGE0, mm::LM_RK, 4))) return rc;
-            if ((rc = eval(ctx, p, mm::SRC_STAGE1, mm::LM_RK, 5))) return rc;
-            if ((rc = eval(ctx, p, mm::SRC_STAGE0, mm::LM_RK, 6))) return rc;
-            if ((rc = eval(ctx, p, mm::SRC_NEXT, mm::LM_RKFINAL, 7))) return rc;
+            if ((rc = eval(ctx, p, mm::SRC_COMBINE2, mm::LM_RK, 2, true, ctx->spec == mm_ctx::SPEC_M2))) return rc;
+            if ((rc = eval(ctx, p, mm::SRC_STAGE1, mm::LM_RK, 3, true, true))) return rc;
+            if ((rc = eval(ctx, p, mm::SRC_STAGE0, mm::LM_RK, 4, true, true))) return rc;
+            if ((rc = eval(ctx, p, mm::SRC_STAGE1, mm::LM_RK, 5, true, true))) return rc;
+            if ((rc = eval(ctx, p, mm::SRC_STAGE0, mm::LM_RK, 6, true, true))) return rc;
+            if ((rc = eval(ctx, p, mm::SRC_NEXT, mm::LM_RKFINAL, 7, false, true))) return rc;
+            ctx->spec = mm_ctx::SPEC_NONE;       // the next stage-2 input needs the new h
         }
     } else {
         ctx->k1_valid = false;
         ctx->last_fixed_dt = dt;
         for (long s = 0; s < nsteps; ++s) {
+            const bool have = ctx->spec == mm_ctx::SPEC_MCUR;
             if (method == MM_EULER) {
-                if ((rc = eval(ctx, p, mm::SRC_CUR, mm::LM_EULER, 0))) return rc;
+                if ((rc = eval(ctx, p, mm::SRC_CUR, mm::LM_EULER, 0, true, have))) return rc;
             } else {
-                if ((rc = eval(ctx, p, mm::SRC_CUR, mm::LM_HEUN1, 0))) return rc;
-                if ((rc = eval(ctx, p, mm::SRC_STAGE0, mm::LM_HEUN2, 0))) return rc;
+                if ((rc = eval(ctx, p, mm::SRC_CUR, mm::LM_HEUN1, 0, true, have))) return rc;
+                if ((rc = eval(ctx, p, mm::SRC_STAGE0, mm::LM_HEUN2, 0, true, true))) return rc;
             }
+            ctx->spec = mm_ctx::SPEC_MCUR;
         }
     }
     return MM_OK;
@@ -725,7 +735,7 @@ int mm_eval_heff_static(mm_ctx* ctx, const float* m, float* h_out, float* torque
     p.thermal_step = (long long)ctx->th_step;
     // the reduction counters must start at zero; the spectra are fully rewritten
     CK(cudaMemsetAsync(base, 0, sizeof(mm::DevState), ctx->stream));
-    mm::LaunchArgs a{mm::SRC_PTR, mm::LM_EVAL, 0};
+    mm::LaunchArgs a{mm::SRC_PTR, mm::LM_EVAL, 0, 0, 0};
     int ids[8];
     const int n = mm::eval_passes(p, a, ids);
     for (int i = 0; i < n; ++i) CK(mm::launch_pass(p, a, ids[i], ctx->stream));

@@ -1,16 +1,21 @@
 // fft32.cuh - single-precision complex FFT building blocks for the hot path.
 //
 // The convolution of Sec. 3.2 (stages i and iii) needs batched 1-D FFTs along
-// each axis.  Here each line lives in shared memory; one thread owns one
-// radix-16 butterfly per pass (Stockham auto-sort ordering, so input and
-// output are both in natural order and no bit reversal is needed).  Values
-// stay in registers inside a pass; shared memory carries them between passes.
+// each axis.  Each line lives in shared memory; one thread owns one radix-16
+// butterfly per pass (Stockham auto-sort ordering: natural order in and out,
+// no bit reversal).  Values stay in registers inside a pass; shared memory
+// carries them between passes.
 //
 // Shared-memory lines use a padded index pad(i) = i + i/16 so that the
 // stride-16 writes of the first pass hit 16 distinct 64-bit bank pairs.
 //
-// Twiddles come from a table tw[t] = exp(-2 pi i t / TWN) (TWN = 4096)
-// computed in double precision on the host and rounded once to float.
+// Twiddles: a table tw[t] = exp(-2 pi i t / TWN) (TWN = 4096) computed in
+// double precision on the host and rounded once.  A radix-16 butterfly reads
+// only w, w^2, w^4, w^8 and forms the other eleven powers by at most three
+// complex products, which keeps the loads off the critical path.
+//
+// Line counts and lengths are template parameters so that every index is a
+// shift or a mask.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -21,6 +26,29 @@ constexpr int TWN = 1 << TWN_LOG;
 
 __device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int padded_len(int n) { return n + (n >> 4) + 1; }
+
+// ---- launch shapes, shared with the host ----------------------------------
+// threads per line (one radix-16 butterfly each)
+__host__ __device__ constexpr int nb_of(int logp) { return logp >= 4 ? (1 << (logp - 4)) : 1; }
+// rows (per component) handled by one block of the x passes: 3*TY/2 complex lines
+__host__ __device__ constexpr int ty_of(int logp) {
+    return 24 * nb_of(logp) <= 512 ? 16 : 12 * nb_of(logp) <= 512 ? 8 : 6 * nb_of(logp) <= 512 ? 4 : 2;
+}
+// lines of each component per block for the column passes (3 components each)
+__host__ __device__ constexpr int cols_of(int logp, int cap) {
+    return (3 * 64 * nb_of(logp) <= 512 && cap >= 64) ? 64
+         : (3 * 32 * nb_of(logp) <= 512 && cap >= 32) ? 32
+         : (3 * 16 * nb_of(logp) <= 512 && cap >= 16) ? 16
+         : (3 * 8 * nb_of(logp) <= 512 && cap >= 8) ? 8
+         : (3 * 4 * nb_of(logp) <= 512 && cap >= 4) ? 4
+         : (3 * 2 * nb_of(logp) <= 512 && cap >= 2) ? 2 : 1;
+}
+__host__ __device__ constexpr int kxb_of(int logp) { return cols_of(logp, 64); }   // 2-D y pass
+__host__ __device__ constexpr int tz_of(int logp) { return cols_of(logp, 8); }     // 3-D y passes
+__host__ __device__ constexpr int tky_of(int logp) { return cols_of(logp, 64); }   // 3-D z pass
+__host__ __device__ constexpr int threads_of(int nlines, int logp) {
+    return ((nlines * nb_of(logp) + 31) / 32) * 32 < 64 ? 64 : ((nlines * nb_of(logp) + 31) / 32) * 32;
+}
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -116,11 +144,53 @@ __device__ __forceinline__ void dft(float2* v) {
     }
 }
 
-// twiddle W^{k r}, W = exp(-+2 pi i /(Ns R)), read from the TWN table
 template <bool INV>
-__device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int t) {
+__device__ __forceinline__ float2 ldtw(const float2* __restrict__ tw, int t) {
     float2 w = __ldg(tw + t);
     return INV ? cconj(w) : w;
+}
+
+// v[r] *= w^r for r = 1..R-1, w = tw[t1] (conjugated for INV); loads w, w^2,
+// w^4, w^8 and multiplies the rest (at most three roundings per factor)
+template <int R, bool INV>
+__device__ __forceinline__ void apply_twiddles(float2* v, const float2* __restrict__ tw, int t1) {
+    if constexpr (R == 2) {
+        v[1] = cmul(v[1], ldtw<INV>(tw, t1));
+    } else if constexpr (R == 4) {
+        const float2 w1 = ldtw<INV>(tw, t1), w2 = ldtw<INV>(tw, 2 * t1);
+        v[1] = cmul(v[1], w1);
+        v[2] = cmul(v[2], w2);
+        v[3] = cmul(v[3], cmul(w1, w2));
+    } else if constexpr (R == 8) {
+        const float2 w1 = ldtw<INV>(tw, t1), w2 = ldtw<INV>(tw, 2 * t1), w4 = ldtw<INV>(tw, 4 * t1);
+        const float2 w3 = cmul(w1, w2);
+        v[1] = cmul(v[1], w1);
+        v[2] = cmul(v[2], w2);
+        v[3] = cmul(v[3], w3);
+        v[4] = cmul(v[4], w4);
+        v[5] = cmul(v[5], cmul(w1, w4));
+        v[6] = cmul(v[6], cmul(w2, w4));
+        v[7] = cmul(v[7], cmul(w3, w4));
+    } else if constexpr (R == 16) {
+        const float2 w1 = ldtw<INV>(tw, t1), w2 = ldtw<INV>(tw, 2 * t1);
+        const float2 w4 = ldtw<INV>(tw, 4 * t1), w8 = ldtw<INV>(tw, 8 * t1);
+        const float2 w3 = cmul(w1, w2), w5 = cmul(w1, w4), w6 = cmul(w2, w4), w7 = cmul(w3, w4);
+        v[1] = cmul(v[1], w1);
+        v[2] = cmul(v[2], w2);
+        v[3] = cmul(v[3], w3);
+        v[4] = cmul(v[4], w4);
+        v[5] = cmul(v[5], w5);
+        v[6] = cmul(v[6], w6);
+        v[7] = cmul(v[7], w7);
+        v[8] = cmul(v[8], w8);
+        v[9] = cmul(v[9], cmul(w1, w8));
+        v[10] = cmul(v[10], cmul(w2, w8));
+        v[11] = cmul(v[11], cmul(w3, w8));
+        v[12] = cmul(v[12], cmul(w4, w8));
+        v[13] = cmul(v[13], cmul(w5, w8));
+        v[14] = cmul(v[14], cmul(w6, w8));
+        v[15] = cmul(v[15], cmul(w7, w8));
+    }
 }
 
 // Main radix of a line of length 2^LOGP and the number of radix-16 passes.
@@ -131,25 +201,26 @@ struct Plan {
     static constexpr int NB = P / R;                    // threads per line
     static constexpr int N16 = LOGP >= 4 ? LOGP / 4 : 0;
     static constexpr int REM = LOGP >= 4 ? (1 << (LOGP % 4)) : 1;   // trailing radix
+    static constexpr int LS = padded_len(P);            // line stride in shared memory
 };
 
-// In-place FFT of `nlines` lines of length 2^LOGP stored in shared memory at
-// line l -> base + l*lstride (padded indices).  Threads [0, nlines*NB) work;
-// the rest only join the barriers.  Must be called by every thread of the
-// block.  Direction INV (no 1/P scaling).
-template <int LOGP, bool INV>
-__device__ void fft_lines(float2* base, int nlines, int lstride, const float2* __restrict__ tw) {
+// In-place FFT of NL lines of length 2^LOGP stored in shared memory at
+// base + l*LS (padded indices).  Threads [0, NL*NB) work; the rest only join
+// the barriers.  Called by every thread of the block, which must have
+// synchronised after writing the lines.  No 1/P scaling.
+template <int LOGP, int NL, bool INV>
+__device__ __forceinline__ void fft_lines(float2* base, const float2* __restrict__ tw) {
     using PL = Plan<LOGP>;
-    constexpr int P = PL::P, R = PL::R, NB = PL::NB;
+    constexpr int P = PL::P, R = PL::R, NB = PL::NB, LS = PL::LS;
     const int tid = threadIdx.x;
-    const bool active = tid < nlines * NB;
+    const bool active = tid < NL * NB;
     const int line = active ? tid / NB : 0;
     const int j = active ? tid - line * NB : 0;
-    float2* a = base + line * lstride;
+    float2* a = base + line * LS;
     float2 v[R];
 
     if constexpr (LOGP == 0) {
-        __syncthreads();
+        // a length-1 transform is the identity
     } else if constexpr (LOGP < 4) {
         // single pass of radix P, Ns = 1 (no twiddles)
         if (active) {
@@ -161,18 +232,14 @@ __device__ void fft_lines(float2* base, int nlines, int lstride, const float2* _
         }
         __syncthreads();
     } else {
-        int Ns = 1;
-#pragma unroll 1
+#pragma unroll
         for (int p = 0; p < PL::N16; ++p) {
+            const int Ns = 1 << (4 * p);
             if (active) {
+                const int k = j & (Ns - 1);
 #pragma unroll
                 for (int r = 0; r < 16; ++r) v[r] = a[pad(j + r * NB)];
-                const int k = j & (Ns - 1);
-                if (Ns > 1) {
-                    const int step = k * (TWN / (Ns * 16));
-#pragma unroll
-                    for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], twiddle<INV>(tw, r * step));
-                }
+                if (p > 0) apply_twiddles<16, INV>(v, tw, k * (TWN / (Ns * 16)));
                 dft<16, INV>(v);
             }
             __syncthreads();
@@ -183,12 +250,12 @@ __device__ void fft_lines(float2* base, int nlines, int lstride, const float2* _
                 for (int r = 0; r < 16; ++r) a[pad(o + r * Ns)] = v[r];
             }
             __syncthreads();
-            Ns *= 16;
         }
         if constexpr (PL::REM > 1) {
             constexpr int RR = PL::REM;          // 2, 4 or 8
             constexpr int NBR = P / RR;          // butterflies of radix RR per line
             constexpr int PER = 16 / RR;         // per thread
+            constexpr int Ns = 1 << (4 * PL::N16);
             if (active) {
 #pragma unroll
                 for (int b = 0; b < PER; ++b) {
@@ -200,9 +267,7 @@ __device__ void fft_lines(float2* base, int nlines, int lstride, const float2* _
                 for (int b = 0; b < PER; ++b) {
                     const int jj = j + b * NB;
                     const int k = jj & (Ns - 1);
-                    const int step = k * (TWN / (Ns * RR));
-#pragma unroll
-                    for (int r = 1; r < RR; ++r) v[b * RR + r] = cmul(v[b * RR + r], twiddle<INV>(tw, r * step));
+                    apply_twiddles<RR, INV>(v + b * RR, tw, k * (TWN / (Ns * RR)));
                     dft<RR, INV>(v + b * RR);
                 }
             }

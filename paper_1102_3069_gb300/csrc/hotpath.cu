@@ -125,200 +125,224 @@ __device__ __forceinline__ const float* src_ptr(const HotParams& p, int src, int
 }
 
 // ---------------------------------------------------------------------------
-// x forward pass: R2C along x of 3*TY real rows (pairs of rows share one
-// complex FFT: z = a + i b, A = (Z_k + conj Z_-k)/2, B = (Z_k - conj Z_-k)/(2i)).
+// compile-time shapes of the passes (shared with the host through fft32.cuh)
 template <int LOGP>
-__global__ void __launch_bounds__(768) k_xfwd(HotParams p, LaunchArgs a) {
+struct XS {                         // x passes: TY rows x 3 components per block
+    static constexpr int P = 1 << LOGP;
+    static constexpr int TY = ty_of(LOGP);
+    static constexpr int NL = 3 * TY / 2;       // complex lines (two real rows each)
+    static constexpr int NT = threads_of(NL, LOGP);
+    static constexpr int LS = padded_len(P);
+    static constexpr int HX = P == 1 ? 1 : P / 2 + 1;
+    static constexpr int MINB = NT >= 768 ? 1 : 1024 / NT;
+};
+template <int LOGP, int COLS>
+struct CS {                         // column passes: COLS lines x 3 components per block
+    static constexpr int P = 1 << LOGP;
+    static constexpr int NL = 3 * COLS;
+    static constexpr int NT = threads_of(NL, LOGP);
+    static constexpr int LS = padded_len(P);
+    static constexpr int MINB = NT >= 768 ? 1 : 1024 / NT;
+};
+
+// Half-spectrum unpack of the paired rows of line l (z = a + i b:
+// A = (Z_k + conj Z_-k)/2, B = (Z_k - conj Z_-k)/(2i)) and transposed store
+// to s1 [c][kx][z][y]: rows 2l, 2l+1 are adjacent y of one component.
+template <int LOGP>
+__device__ __forceinline__ void store_x_spectrum(const HotParams& p, const float2* sm, int y0, int z) {
+    using S = XS<LOGP>;
+    for (int idx = threadIdx.x; idx < S::NL * S::HX; idx += S::NT) {
+        const int l = idx / S::HX, k = idx - l * S::HX;
+        const float2 A = sm[l * S::LS + pad(k)];
+        const float2 B = cconj(sm[l * S::LS + pad((S::P - k) & (S::P - 1))]);
+        const float2 D = csub(A, B);
+        const float4 out = make_float4(0.5f * (A.x + B.x), 0.5f * (A.y + B.y), 0.5f * D.y, -0.5f * D.x);
+        const int c = (2 * l) / S::TY, ty = 2 * l - c * S::TY;
+        float2* dst = p.s1 + ((long long)(c * S::HX + k) * p.nz + z) * p.nyp + y0 + ty;
+        *reinterpret_cast<float4*>(dst) = out;
+    }
+}
+
+// x forward pass: rows of m (zero padded to Px) -> R2C -> transposed spectrum.
+template <int LOGP>
+__global__ void __launch_bounds__(XS<LOGP>::NT, XS<LOGP>::MINB) k_xfwd(HotParams p, LaunchArgs a) {
+    using S = XS<LOGP>;
     extern __shared__ float2 sm[];
-    constexpr int P = 1 << LOGP;
-    const int LS = padded_len(P);
-    const int TY = p.ty, NL = (3 * TY) >> 1;
-    const int y0 = blockIdx.x * TY, z = blockIdx.y;
+    const int y0 = blockIdx.x * S::TY, z = blockIdx.y;
     DevState* st = p.st;
     if (a.mode != LM_EVAL && st->done) return;
     const int cur = st->cur;
     const long long n = p.ncell;
-    const float* src = src_ptr(p, a.src, cur);
+    const bool comb = a.src == SRC_COMBINE2;
+    const float* src = comb ? p.ms[cur] : src_ptr(p, a.src, cur);
     const float* k1 = p.ks[cur];
     float* wout = p.mstage[0];
-    Coef c21 = {0.f, 0.f};
-    if (a.src == SRC_COMBINE2) {
-        src = p.ms[cur];
-        c21 = split(st->h * c_dpa[2][1]);
-    }
-    for (int idx = threadIdx.x; idx < TY * P; idx += blockDim.x) {
-        const int ty = idx >> LOGP, x = idx & (P - 1);
+    const Coef c21 = comb ? split(st->h * c_dpa[2][1]) : Coef{0.f, 0.f};
+    const int NX = p.nx, NY = p.ny;
+    for (int idx = threadIdx.x; idx < S::NL * S::P; idx += S::NT) {
+        const int l = idx >> LOGP, x = idx & (S::P - 1);
+        const int c = (2 * l) / S::TY, ty = 2 * l - c * S::TY;
         const int y = y0 + ty;
-        f3 v = mk(0.f, 0.f, 0.f);
-        if (x < p.nx && y < p.ny) {
-            const long long cell = ((long long)z * p.ny + y) * p.nx + x;
-            v = ld3(src, cell, n);
-            if (a.src == SRC_COMBINE2) {
-                v = axpy(c21, ld3(k1, cell, n), v);
-                st3(wout, cell, n, v);
+        float2 v = make_float2(0.f, 0.f);
+        if (x < NX) {
+            const long long i0 = (long long)c * n + ((long long)z * NY + y) * NX + x;
+            if (y < NY) {
+                float u = src[i0];
+                if (comb) { u = fmaf(c21.lo, k1[i0], fmaf(c21.hi, k1[i0], u)); wout[i0] = u; }
+                v.x = u;
+            }
+            if (y + 1 < NY) {
+                float u = src[i0 + NX];
+                if (comb) { u = fmaf(c21.lo, k1[i0 + NX], fmaf(c21.hi, k1[i0 + NX], u)); wout[i0 + NX] = u; }
+                v.y = u;
             }
         }
-        const float vv[3] = {v.x, v.y, v.z};
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const int q = c * TY + ty;
-            reinterpret_cast<float*>(sm + (q >> 1) * LS + pad(x))[q & 1] = vv[c];
-        }
+        sm[l * S::LS + pad(x)] = v;
     }
     __syncthreads();
-    fft_lines<LOGP, false>(sm, NL, LS, p.tw);
-    const int HX = p.hx;
-    for (int idx = threadIdx.x; idx < NL * HX; idx += blockDim.x) {
-        const int l = idx % NL, k = idx / NL;
-        const float2 A = sm[l * LS + pad(k)];
-        const float2 B = cconj(sm[l * LS + pad((P - k) & (P - 1))]);
-        const float2 D = csub(A, B);
-        const float4 out = make_float4(0.5f * (A.x + B.x), 0.5f * (A.y + B.y), 0.5f * D.y, -0.5f * D.x);
-        const int q = 2 * l, c = q / TY, ty = q - c * TY;      // rows q, q+1: same component
-        float2* dst = p.s1 + ((long long)(c * HX + k) * p.nz + z) * p.nyp + y0 + ty;
-        *reinterpret_cast<float4*>(dst) = out;
-    }
+    fft_lines<LOGP, S::NL, false>(sm, p.tw);
+    store_x_spectrum<LOGP>(p, sm, y0, z);
 }
 
 // ---------------------------------------------------------------------------
 // 2-D column pass: y forward FFT, kernel product, y inverse FFT (in place).
 template <int LOGP>
-__global__ void __launch_bounds__(768) k_yconv(HotParams p, LaunchArgs a) {
+__global__ void __launch_bounds__(CS<LOGP, kxb_of(LOGP)>::NT, CS<LOGP, kxb_of(LOGP)>::MINB)
+k_yconv(HotParams p, LaunchArgs a) {
+    constexpr int KXB = kxb_of(LOGP);
+    using S = CS<LOGP, KXB>;
     extern __shared__ float2 sm[];
-    constexpr int P = 1 << LOGP;
-    const int LS = padded_len(P);
-    const int KXB = p.kxb, NL = 3 * KXB;
     const int kx0 = blockIdx.x * KXB;
     if (a.mode != LM_EVAL && p.st->done) return;
     const int HX = p.hx, NY = p.ny;
-    for (int idx = threadIdx.x; idx < NL * P; idx += blockDim.x) {
-        const int l = idx >> LOGP, y = idx & (P - 1);
+    for (int idx = threadIdx.x; idx < S::NL * S::P; idx += S::NT) {
+        const int l = idx >> LOGP, y = idx & (S::P - 1);
         const int c = l / KXB, j = l - c * KXB, kx = kx0 + j;
         float2 v = make_float2(0.f, 0.f);
         if (kx < HX && y < NY) v = p.s1[(long long)(c * HX + kx) * p.nyp + y];
-        sm[l * LS + pad(y)] = v;
+        sm[l * S::LS + pad(y)] = v;
     }
     __syncthreads();
-    fft_lines<LOGP, false>(sm, NL, LS, p.tw);
+    fft_lines<LOGP, S::NL, false>(sm, p.tw);
     const long long cs = (long long)HX * p.hyk;       // kernel component stride (hzk == 1)
-    for (int idx = threadIdx.x; idx < KXB * P; idx += blockDim.x) {
-        const int j = idx >> LOGP, ky = idx & (P - 1), kx = kx0 + j;
+    for (int idx = threadIdx.x; idx < KXB * S::P; idx += S::NT) {
+        const int j = idx >> LOGP, ky = idx & (S::P - 1), kx = kx0 + j;
         if (kx >= HX) continue;
-        const bool hi = ky > (P >> 1);
-        const int kq = hi ? P - ky : ky;
+        const bool hi = ky > (S::P >> 1);
+        const int kq = hi ? S::P - ky : ky;
         const long long b = (long long)kx * p.hyk + kq;
         const float kxx = __ldg(p.kt + b), kyy = __ldg(p.kt + cs + b), kzz = __ldg(p.kt + 2 * cs + b);
         const float kxy = hi ? -__ldg(p.kt + 3 * cs + b) : __ldg(p.kt + 3 * cs + b);
-        float2* mx = sm + (0 * KXB + j) * LS + pad(ky);
-        float2* my = sm + (1 * KXB + j) * LS + pad(ky);
-        float2* mz = sm + (2 * KXB + j) * LS + pad(ky);
+        float2* mx = sm + (0 * KXB + j) * S::LS + pad(ky);
+        float2* my = sm + (1 * KXB + j) * S::LS + pad(ky);
+        float2* mz = sm + (2 * KXB + j) * S::LS + pad(ky);
         const float2 X = *mx, Y = *my, Z = *mz;
         *mx = make_float2(kxx * X.x + kxy * Y.x, kxx * X.y + kxy * Y.y);
         *my = make_float2(kxy * X.x + kyy * Y.x, kxy * X.y + kyy * Y.y);
         *mz = make_float2(kzz * Z.x, kzz * Z.y);
     }
     __syncthreads();
-    fft_lines<LOGP, true>(sm, NL, LS, p.tw);
-    for (int idx = threadIdx.x; idx < NL * NY; idx += blockDim.x) {
-        const int l = idx / NY, y = idx - l * NY;
+    fft_lines<LOGP, S::NL, true>(sm, p.tw);
+    for (int idx = threadIdx.x; idx < S::NL * S::P; idx += S::NT) {
+        const int l = idx >> LOGP, y = idx & (S::P - 1);
         const int c = l / KXB, j = l - c * KXB, kx = kx0 + j;
-        if (kx < HX) p.s1[(long long)(c * HX + kx) * p.nyp + y] = sm[l * LS + pad(y)];
+        if (kx < HX && y < NY) p.s1[(long long)(c * HX + kx) * p.nyp + y] = sm[l * S::LS + pad(y)];
     }
 }
 
 // ---------------------------------------------------------------------------
 // 3-D: y forward pass.  s1 [c][kx][z][y]  ->  s2 [c][kx][ky][z]
 template <int LOGP>
-__global__ void __launch_bounds__(768) k_yfwd(HotParams p, LaunchArgs a) {
+__global__ void __launch_bounds__(CS<LOGP, tz_of(LOGP)>::NT, CS<LOGP, tz_of(LOGP)>::MINB)
+k_yfwd(HotParams p, LaunchArgs a) {
+    constexpr int TZ = tz_of(LOGP);
+    using S = CS<LOGP, TZ>;
     extern __shared__ float2 sm[];
-    constexpr int P = 1 << LOGP;
-    const int LS = padded_len(P);
-    const int TZ = p.tz, NL = 3 * TZ;
     const int kx = blockIdx.x, z0 = blockIdx.y * TZ;
     if (a.mode != LM_EVAL && p.st->done) return;
     const int HX = p.hx, NY = p.ny, NZ = p.nz;
-    for (int idx = threadIdx.x; idx < NL * P; idx += blockDim.x) {
-        const int l = idx >> LOGP, y = idx & (P - 1);
+    for (int idx = threadIdx.x; idx < S::NL * S::P; idx += S::NT) {
+        const int l = idx >> LOGP, y = idx & (S::P - 1);
         const int c = l / TZ, zt = l - c * TZ, z = z0 + zt;
         float2 v = make_float2(0.f, 0.f);
         if (y < NY && z < NZ) v = p.s1[((long long)(c * HX + kx) * NZ + z) * p.nyp + y];
-        sm[l * LS + pad(y)] = v;
+        sm[l * S::LS + pad(y)] = v;
     }
     __syncthreads();
-    fft_lines<LOGP, false>(sm, NL, LS, p.tw);
-    for (int idx = threadIdx.x; idx < NL * P; idx += blockDim.x) {
-        const int zt = idx % TZ, r = idx / TZ, ky = r & (P - 1), c = r >> LOGP;
-        p.s2[((long long)(c * HX + kx) * P + ky) * p.nzp + z0 + zt] = sm[(c * TZ + zt) * LS + pad(ky)];
+    fft_lines<LOGP, S::NL, false>(sm, p.tw);
+    for (int idx = threadIdx.x; idx < S::NL * S::P; idx += S::NT) {
+        const int zt = idx % TZ, r = idx / TZ, ky = r & (S::P - 1), c = r >> LOGP;
+        p.s2[((long long)(c * HX + kx) * S::P + ky) * p.nzp + z0 + zt] = sm[(c * TZ + zt) * S::LS + pad(ky)];
     }
 }
 
 // 3-D: fused z pass (forward, kernel product, inverse) on s2 in place.
 template <int LOGP>
-__global__ void __launch_bounds__(768) k_zconv(HotParams p, LaunchArgs a) {
+__global__ void __launch_bounds__(CS<LOGP, tky_of(LOGP)>::NT, CS<LOGP, tky_of(LOGP)>::MINB)
+k_zconv(HotParams p, LaunchArgs a) {
+    constexpr int TK = tky_of(LOGP);
+    using S = CS<LOGP, TK>;
     extern __shared__ float2 sm[];
-    constexpr int P = 1 << LOGP;
-    const int LS = padded_len(P);
-    const int TK = p.tky, NL = 3 * TK;
     const int kx = blockIdx.x, ky0 = blockIdx.y * TK;
     if (a.mode != LM_EVAL && p.st->done) return;
     const int HX = p.hx, PY = p.py, NZ = p.nz;
-    for (int idx = threadIdx.x; idx < NL * P; idx += blockDim.x) {
-        const int l = idx >> LOGP, z = idx & (P - 1);
+    for (int idx = threadIdx.x; idx < S::NL * S::P; idx += S::NT) {
+        const int l = idx >> LOGP, z = idx & (S::P - 1);
         const int c = l / TK, j = l - c * TK, ky = ky0 + j;
         float2 v = make_float2(0.f, 0.f);
         if (ky < PY && z < NZ) v = p.s2[((long long)(c * HX + kx) * PY + ky) * p.nzp + z];
-        sm[l * LS + pad(z)] = v;
+        sm[l * S::LS + pad(z)] = v;
     }
     __syncthreads();
-    fft_lines<LOGP, false>(sm, NL, LS, p.tw);
+    fft_lines<LOGP, S::NL, false>(sm, p.tw);
     const long long cs = (long long)HX * p.hyk * p.hzk;
-    for (int idx = threadIdx.x; idx < TK * P; idx += blockDim.x) {
-        const int j = idx >> LOGP, kz = idx & (P - 1), ky = ky0 + j;
+    for (int idx = threadIdx.x; idx < TK * S::P; idx += S::NT) {
+        const int j = idx >> LOGP, kz = idx & (S::P - 1), ky = ky0 + j;
         if (ky >= PY) continue;
-        const bool yh = ky > (PY >> 1), zh = kz > (P >> 1);
-        const int kyq = yh ? PY - ky : ky, kzq = zh ? P - kz : kz;
+        const bool yh = ky > (PY >> 1), zh = kz > (S::P >> 1);
+        const int kyq = yh ? PY - ky : ky, kzq = zh ? S::P - kz : kz;
         const long long b = ((long long)kx * p.hyk + kyq) * p.hzk + kzq;
         const float kxx = __ldg(p.kt + b), kyy = __ldg(p.kt + cs + b), kzz = __ldg(p.kt + 2 * cs + b);
         float kxy = __ldg(p.kt + 3 * cs + b), kxz = __ldg(p.kt + 4 * cs + b), kyz = __ldg(p.kt + 5 * cs + b);
         if (yh) { kxy = -kxy; kyz = -kyz; }
         if (zh) { kxz = -kxz; kyz = -kyz; }
-        float2* mx = sm + (0 * TK + j) * LS + pad(kz);
-        float2* my = sm + (1 * TK + j) * LS + pad(kz);
-        float2* mz = sm + (2 * TK + j) * LS + pad(kz);
+        float2* mx = sm + (0 * TK + j) * S::LS + pad(kz);
+        float2* my = sm + (1 * TK + j) * S::LS + pad(kz);
+        float2* mz = sm + (2 * TK + j) * S::LS + pad(kz);
         const float2 X = *mx, Y = *my, Z = *mz;
         *mx = make_float2(kxx * X.x + kxy * Y.x + kxz * Z.x, kxx * X.y + kxy * Y.y + kxz * Z.y);
         *my = make_float2(kxy * X.x + kyy * Y.x + kyz * Z.x, kxy * X.y + kyy * Y.y + kyz * Z.y);
         *mz = make_float2(kxz * X.x + kyz * Y.x + kzz * Z.x, kxz * X.y + kyz * Y.y + kzz * Z.y);
     }
     __syncthreads();
-    fft_lines<LOGP, true>(sm, NL, LS, p.tw);
-    for (int idx = threadIdx.x; idx < NL * NZ; idx += blockDim.x) {
-        const int l = idx / NZ, z = idx - l * NZ;
+    fft_lines<LOGP, S::NL, true>(sm, p.tw);
+    for (int idx = threadIdx.x; idx < S::NL * S::P; idx += S::NT) {
+        const int l = idx >> LOGP, z = idx & (S::P - 1);
         const int c = l / TK, j = l - c * TK, ky = ky0 + j;
-        if (ky < PY) p.s2[((long long)(c * HX + kx) * PY + ky) * p.nzp + z] = sm[l * LS + pad(z)];
+        if (ky < PY && z < NZ) p.s2[((long long)(c * HX + kx) * PY + ky) * p.nzp + z] = sm[l * S::LS + pad(z)];
     }
 }
 
 // 3-D: y inverse pass.  s2 [c][kx][ky][z]  ->  s1 [c][kx][z][y]
 template <int LOGP>
-__global__ void __launch_bounds__(768) k_yinv(HotParams p, LaunchArgs a) {
+__global__ void __launch_bounds__(CS<LOGP, tz_of(LOGP)>::NT, CS<LOGP, tz_of(LOGP)>::MINB)
+k_yinv(HotParams p, LaunchArgs a) {
+    constexpr int TZ = tz_of(LOGP);
+    using S = CS<LOGP, TZ>;
     extern __shared__ float2 sm[];
-    constexpr int P = 1 << LOGP;
-    const int LS = padded_len(P);
-    const int TZ = p.tz, NL = 3 * TZ;
     const int kx = blockIdx.x, z0 = blockIdx.y * TZ;
     if (a.mode != LM_EVAL && p.st->done) return;
     const int HX = p.hx, NY = p.ny, NZ = p.nz;
-    for (int idx = threadIdx.x; idx < NL * P; idx += blockDim.x) {
-        const int zt = idx % TZ, r = idx / TZ, ky = r & (P - 1), c = r >> LOGP;
-        sm[(c * TZ + zt) * LS + pad(ky)] = p.s2[((long long)(c * HX + kx) * P + ky) * p.nzp + z0 + zt];
+    for (int idx = threadIdx.x; idx < S::NL * S::P; idx += S::NT) {
+        const int zt = idx % TZ, r = idx / TZ, ky = r & (S::P - 1), c = r >> LOGP;
+        sm[(c * TZ + zt) * S::LS + pad(ky)] = p.s2[((long long)(c * HX + kx) * S::P + ky) * p.nzp + z0 + zt];
     }
     __syncthreads();
-    fft_lines<LOGP, true>(sm, NL, LS, p.tw);
-    for (int idx = threadIdx.x; idx < NL * NY; idx += blockDim.x) {
-        const int l = idx / NY, y = idx - l * NY;
+    fft_lines<LOGP, S::NL, true>(sm, p.tw);
+    for (int idx = threadIdx.x; idx < S::NL * S::P; idx += S::NT) {
+        const int l = idx >> LOGP, y = idx & (S::P - 1);
         const int c = l / TZ, zt = l - c * TZ, z = z0 + zt;
-        if (z < NZ) p.s1[((long long)(c * HX + kx) * NZ + z) * p.nyp + y] = sm[l * LS + pad(y)];
+        if (y < NY && z < NZ) p.s1[((long long)(c * HX + kx) * NZ + z) * p.nyp + y] = sm[l * S::LS + pad(y)];
     }
 }
 
@@ -433,16 +457,18 @@ __device__ void reduce_and_finish(const HotParams& p, const LaunchArgs& a, Parti
 // ---------------------------------------------------------------------------
 // Everything that happens to one cell once its demag field is known.
 struct StageCoefs {
-    Coef c[8];          // per mode: stage combination weights (see below)
+    Coef c[8];          // per mode: stage combination weights (see stage_coefs)
 };
 
-__device__ __forceinline__ void cell_update(const HotParams& p, const LaunchArgs& a, int cur, const StageCoefs& sc,
-                                            const float* __restrict__ min, long long cell, int x, int y, int z,
-                                            f3 hd, long long tstep, Partials& pt) {
+// Returns the magnetisation the next evaluation of this step reads at this
+// cell (m_{s+1}, m_2, the predictor or m_{n+1}); zero when there is none.
+__device__ __forceinline__ f3 cell_update(const HotParams& p, const LaunchArgs& a, int cur, const StageCoefs& sc,
+                                          const float* __restrict__ min, long long cell, int x, int y, int z,
+                                          f3 hd, long long tstep, Partials& pt) {
     const long long n = p.ncell;
     const f3 m = ld3(min, cell, n);
     // exchange, 6-neighbour (4 in 2-D) Laplacian; a missing neighbour adds nothing
-    f3 hex = mk(0.f, 0.f, 0.f);
+    f3 hex;
     {
         f3 s = mk(0.f, 0.f, 0.f);
         if (x + 1 < p.nx) s = s + (ld3(min, cell + 1, n) - m);
@@ -477,6 +503,7 @@ __device__ __forceinline__ void cell_update(const HotParams& p, const LaunchArgs
     const f3 mxh = cross(m, h);
     const f3 k = (-p.llpref) * (mxh + p.alpha * cross(m, mxh));
     const float tq = sqrtf(dot(mxh, mxh));
+    f3 next = mk(0.f, 0.f, 0.f);
 
     switch (a.mode) {
         case LM_EVAL: {
@@ -491,6 +518,8 @@ __device__ __forceinline__ void cell_update(const HotParams& p, const LaunchArgs
             st3(p.ks[cur], cell, n, k);
             pt.torque = fmaxf(pt.torque, tq);
             pt.bad |= !finite3(k);
+            next = axpy(sc.c[1], k, m);                 // m_2 = m_n + h a21 k1
+            st3(p.mstage[0], cell, n, next);
             break;
         case LM_RK: {
             const int s = a.stage;                       // 2..6
@@ -500,8 +529,13 @@ __device__ __forceinline__ void cell_update(const HotParams& p, const LaunchArgs
             for (int j = 2; j < s; ++j)
                 if (sc.c[j].hi != 0.f) acc = axpy(sc.c[j], ld3(p.kb[j], cell, n), acc);
             acc = axpy(sc.c[s], k, acc);
-            if (s < 6) st3(p.mstage[(s + 1) & 1], cell, n, acc);
-            else st3(p.ms[1 - cur], cell, n, normalized(acc));
+            if (s < 6) {
+                st3(p.mstage[(s + 1) & 1], cell, n, acc);
+                next = acc;
+            } else {
+                next = normalized(acc);
+                st3(p.ms[1 - cur], cell, n, next);
+            }
             pt.bad |= !finite3(k);
             break;
         }
@@ -518,15 +552,15 @@ __device__ __forceinline__ void cell_update(const HotParams& p, const LaunchArgs
             break;
         }
         case LM_EULER: {
-            f3 acc = axpy(sc.c[0], k, m);
-            const f3 mn = normalized(acc);
-            st3(p.ms[1 - cur], cell, n, mn);
-            pt.bad |= !finite3(mn);
+            next = normalized(axpy(sc.c[0], k, m));
+            st3(p.ms[1 - cur], cell, n, next);
+            pt.bad |= !finite3(next);
             break;
         }
         case LM_HEUN1: {
             st3(p.ks[cur], cell, n, k);
-            st3(p.mstage[0], cell, n, axpy(sc.c[0], k, m));
+            next = axpy(sc.c[0], k, m);
+            st3(p.mstage[0], cell, n, next);
             pt.bad |= !finite3(k);
             break;
         }
@@ -534,19 +568,23 @@ __device__ __forceinline__ void cell_update(const HotParams& p, const LaunchArgs
             f3 acc = ld3(p.ms[cur], cell, n);
             acc = axpy(sc.c[0], ld3(p.ks[cur], cell, n), acc);
             acc = axpy(sc.c[0], k, acc);
-            const f3 mn = normalized(acc);
-            st3(p.ms[1 - cur], cell, n, mn);
-            pt.bad |= !finite3(mn);
+            next = normalized(acc);
+            st3(p.ms[1 - cur], cell, n, next);
+            pt.bad |= !finite3(next);
             break;
         }
         default: break;
     }
+    return next;
 }
 
 __device__ void stage_coefs(const HotParams& p, const LaunchArgs& a, const DevState* st, StageCoefs& sc) {
     for (int j = 0; j < 8; ++j) sc.c[j] = {0.f, 0.f};
     const double h = st->h;
     switch (a.mode) {
+        case LM_K1:
+            sc.c[1] = split(h * c_dpa[2][1]);
+            break;
         case LM_RK:
             for (int j = 1; j <= a.stage; ++j) sc.c[j] = split(h * c_dpa[a.stage + 1][j]);
             break;
@@ -564,18 +602,19 @@ __device__ void stage_coefs(const HotParams& p, const LaunchArgs& a, const DevSt
     }
 }
 
-// inverse x pass (C2R) + crop + fused local epilogue.  DEMAG = false skips the
-// spectrum entirely (demag disabled).
-template <int LOGP, bool DEMAG>
-__global__ void __launch_bounds__(768) k_xinv_local(HotParams p, LaunchArgs a) {
+// Inverse x pass (C2R) + crop + cell-local epilogue.  With FUSE the block
+// then transforms the next evaluation's input for its rows (forward R2C,
+// transposed store), so the next stage needs no separate x-forward pass.
+// The spectrum region a block reads is exactly the region it writes.
+template <int LOGP, bool FUSE>
+__global__ void __launch_bounds__(XS<LOGP>::NT, XS<LOGP>::MINB) k_xinv_local(HotParams p, LaunchArgs a) {
+    using S = XS<LOGP>;
+    constexpr int HP = S::TY / 2;                 // row pairs per block
     extern __shared__ float2 sm[];
     __shared__ StageCoefs s_sc;
     __shared__ int s_cur;
     __shared__ long long s_tstep;
-    constexpr int P = 1 << LOGP;
-    const int LS = padded_len(P);
-    const int TY = p.ty, NL = (3 * TY) >> 1;
-    const int y0 = blockIdx.x * TY, z = blockIdx.y;
+    const int y0 = blockIdx.x * S::TY, z = blockIdx.y;
     DevState* st = p.st;
     if (a.mode != LM_EVAL && st->done) return;
     if (threadIdx.x == 0) {
@@ -583,42 +622,79 @@ __global__ void __launch_bounds__(768) k_xinv_local(HotParams p, LaunchArgs a) {
         s_cur = st->cur;
         s_tstep = (a.mode == LM_EVAL) ? p.thermal_step : st->step_index;
     }
-    if constexpr (DEMAG) {
-        const int HX = p.hx;
-        for (int idx = threadIdx.x; idx < NL * HX; idx += blockDim.x) {
-            const int l = idx % NL, k = idx / NL;
-            const int q = 2 * l, c = q / TY, ty = q - c * TY;
-            const float4 v = *reinterpret_cast<const float4*>(
-                p.s1 + ((long long)(c * HX + k) * p.nz + z) * p.nyp + y0 + ty);
-            // Z = A + iB with A = (v.x, v.y), B = (v.z, v.w); Z[-k] = conj(A) + i conj(B)
-            sm[l * LS + pad(k)] = make_float2(v.x - v.w, v.y + v.z);
-            if (k > 0 && 2 * k < P) sm[l * LS + pad(P - k)] = make_float2(v.x + v.w, v.z - v.y);
-        }
-        __syncthreads();
-        fft_lines<LOGP, true>(sm, NL, LS, p.tw);
-    } else {
-        __syncthreads();
+    for (int idx = threadIdx.x; idx < S::NL * S::HX; idx += S::NT) {
+        const int l = idx / S::HX, k = idx - l * S::HX;
+        const int c = (2 * l) / S::TY, ty = 2 * l - c * S::TY;
+        const float4 v = *reinterpret_cast<const float4*>(
+            p.s1 + ((long long)(c * S::HX + k) * p.nz + z) * p.nyp + y0 + ty);
+        // Z = A + iB with A = (v.x, v.y), B = (v.z, v.w); Z[-k] = conj(A) + i conj(B)
+        sm[l * S::LS + pad(k)] = make_float2(v.x - v.w, v.y + v.z);
+        if (k > 0 && 2 * k < S::P) sm[l * S::LS + pad(S::P - k)] = make_float2(v.x + v.w, v.z - v.y);
     }
+    __syncthreads();
+    fft_lines<LOGP, S::NL, true>(sm, p.tw);
     const int cur = s_cur;
     const float* min = src_ptr(p, a.src, cur);
     Partials pt = {0.f, 0.f, 0.0, 0u};
-    const StageCoefs sc = s_sc;
-    const int NX = p.nx;
-    for (int idx = threadIdx.x; idx < TY * NX; idx += blockDim.x) {
-        const int ty = idx / NX, x = idx - ty * NX, y = y0 + ty;
-        if (y >= p.ny) continue;
-        f3 hd = mk(0.f, 0.f, 0.f);
-        if constexpr (DEMAG) {
-            float v[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const int q = c * TY + ty;
-                v[c] = reinterpret_cast<const float*>(sm + (q >> 1) * LS + pad(x))[q & 1];
-            }
-            hd = mk(v[0], v[1], v[2]);
+    const StageCoefs& sc = s_sc;
+    const int NX = p.nx, NY = p.ny;
+    // one item = one x and a pair of rows (2q, 2q+1): component c of that pair
+    // is the complex entry (line c*TY/2 + q, position x)
+    for (int idx = threadIdx.x; idx < HP * NX; idx += S::NT) {
+        const int q = idx / NX, x = idx - q * NX;
+        const int y = y0 + 2 * q;
+        float2* e0 = sm + (0 * HP + q) * S::LS + pad(x);
+        float2* e1 = sm + (1 * HP + q) * S::LS + pad(x);
+        float2* e2 = sm + (2 * HP + q) * S::LS + pad(x);
+        const float2 h0 = *e0, h1 = *e1, h2 = *e2;
+        f3 na = mk(0.f, 0.f, 0.f), nb = mk(0.f, 0.f, 0.f);
+        const long long cell = ((long long)z * NY + y) * NX + x;
+        if (y < NY) na = cell_update(p, a, cur, sc, min, cell, x, y, z, mk(h0.x, h1.x, h2.x), s_tstep, pt);
+        if (y + 1 < NY) nb = cell_update(p, a, cur, sc, min, cell + NX, x, y + 1, z, mk(h0.y, h1.y, h2.y), s_tstep, pt);
+        if constexpr (FUSE) {
+            *e0 = make_float2(na.x, nb.x);
+            *e1 = make_float2(na.y, nb.y);
+            *e2 = make_float2(na.z, nb.z);
         }
-        const long long cell = ((long long)z * p.ny + y) * NX + x;
-        cell_update(p, a, cur, sc, min, cell, x, y, z, hd, s_tstep, pt);
+    }
+    if constexpr (FUSE) {
+        // zero padding of the next transform: x in [nx, P)
+        const int W = S::P - NX;
+        for (int idx = threadIdx.x; idx < S::NL * W; idx += S::NT) {
+            const int l = idx / W, x = NX + (idx - l * W);
+            sm[l * S::LS + pad(x)] = make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        fft_lines<LOGP, S::NL, false>(sm, p.tw);
+        store_x_spectrum<LOGP>(p, sm, y0, z);
+    }
+    reduce_and_finish(p, a, pt);
+}
+
+// Local terms without the magnetostatic field (demag disabled).
+__global__ void __launch_bounds__(256) k_local(HotParams p, LaunchArgs a) {
+    __shared__ StageCoefs s_sc;
+    __shared__ int s_cur;
+    __shared__ long long s_tstep;
+    DevState* st = p.st;
+    if (a.mode != LM_EVAL && st->done) return;
+    if (threadIdx.x == 0) {
+        stage_coefs(p, a, st, s_sc);
+        s_cur = st->cur;
+        s_tstep = (a.mode == LM_EVAL) ? p.thermal_step : st->step_index;
+    }
+    __syncthreads();
+    const int cur = s_cur;
+    const float* min = src_ptr(p, a.src, cur);
+    Partials pt = {0.f, 0.f, 0.0, 0u};
+    const StageCoefs& sc = s_sc;
+    const int NX = p.nx, NY = p.ny;
+    const long long n = p.ncell;
+    for (long long cell = blockIdx.x * 256ll + threadIdx.x; cell < n; cell += (long long)gridDim.x * 256) {
+        const int x = (int)(cell % NX);
+        const long long r = cell / NX;
+        const int y = (int)(r % NY), z = (int)(r / NY);
+        cell_update(p, a, cur, sc, min, cell, x, y, z, mk(0.f, 0.f, 0.f), s_tstep, pt);
     }
     reduce_and_finish(p, a, pt);
 }
@@ -650,14 +726,6 @@ __global__ void k_copy_out(HotParams p, float* __restrict__ m_user) {
 
 // ---------------------------------------------------------------------------
 // launch helpers
-static int threads_for(int nlines, int logp) {
-    const int nb = logp >= 4 ? (1 << logp) / 16 : 1;
-    int t = nlines * nb;
-    t = ((t + 31) / 32) * 32;
-    return t < 64 ? 64 : t;
-}
-static size_t smem_for(int nlines, int logp) { return (size_t)nlines * padded_len(1 << logp) * sizeof(float2); }
-
 template <int L>
 static cudaError_t set_attr_all() {
     cudaError_t e;
@@ -667,6 +735,7 @@ static cudaError_t set_attr_all() {
     if ((e = cudaFuncSetAttribute(k_yfwd<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_zconv<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_yinv<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_xinv_local<L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_xinv_local<L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if constexpr (L > 0) return set_attr_all<L - 1>();
     return cudaSuccess;
@@ -674,28 +743,54 @@ static cudaError_t set_attr_all() {
 
 cudaError_t configure_hot_kernels() { return set_attr_all<12>(); }
 
-#define MM_DISPATCH(LOGP, KERNEL, GRID, BLOCK, SMEM, STREAM, ...)                  \
-    switch (LOGP) {                                                                \
-        case 0: KERNEL<0><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__); break;     \
-        case 1: KERNEL<1><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__); break;     \
-        case 2: KERNEL<2><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__); break;     \
-        case 3: KERNEL<3><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__); break;     \
-        case 4: KERNEL<4><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__); break;     \
-        case 5: KERNEL<5><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__); break;     \
-        case 6: KERNEL<6><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__); break;     \
-        case 7: KERNEL<7><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__); break;     \
-        case 8: KERNEL<8><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__); break;     \
-        case 9: KERNEL<9><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__); break;     \
-        case 10: KERNEL<10><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__); break;   \
-        case 11: KERNEL<11><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__); break;   \
-        case 12: KERNEL<12><<<GRID, BLOCK, SMEM, STREAM>>>(__VA_ARGS__); break;   \
-        default: return cudaErrorInvalidValue;                                     \
+template <int L>
+static void launch_x(const HotParams& p, const LaunchArgs& a, int pass, cudaStream_t s) {
+    using S = XS<L>;
+    const dim3 g((p.ny + S::TY - 1) / S::TY, p.nz);
+    const size_t sm = (size_t)S::NL * S::LS * sizeof(float2);
+    if (pass == PASS_XFWD) k_xfwd<L><<<g, S::NT, sm, s>>>(p, a);
+    else if (pass == PASS_XINV_LOCAL) k_xinv_local<L, false><<<g, S::NT, sm, s>>>(p, a);
+    else k_xinv_local<L, true><<<g, S::NT, sm, s>>>(p, a);
+}
+
+template <int L>
+static void launch_y(const HotParams& p, const LaunchArgs& a, int pass, cudaStream_t s) {
+    if (pass == PASS_YCONV) {
+        using S = CS<L, kxb_of(L)>;
+        const dim3 g((p.hx + kxb_of(L) - 1) / kxb_of(L));
+        k_yconv<L><<<g, S::NT, (size_t)S::NL * S::LS * sizeof(float2), s>>>(p, a);
+    } else {
+        using S = CS<L, tz_of(L)>;
+        const dim3 g(p.hx, (p.nz + tz_of(L) - 1) / tz_of(L));
+        const size_t sm = (size_t)S::NL * S::LS * sizeof(float2);
+        if (pass == PASS_YFWD) k_yfwd<L><<<g, S::NT, sm, s>>>(p, a);
+        else k_yinv<L><<<g, S::NT, sm, s>>>(p, a);
+    }
+}
+
+template <int L>
+static void launch_z(const HotParams& p, const LaunchArgs& a, cudaStream_t s) {
+    using S = CS<L, tky_of(L)>;
+    const dim3 g(p.hx, (p.py + tky_of(L) - 1) / tky_of(L));
+    k_zconv<L><<<g, S::NT, (size_t)S::NL * S::LS * sizeof(float2), s>>>(p, a);
+}
+
+#define MM_LOGP_SWITCH(LOGP, CALL)                                          \
+    switch (LOGP) {                                                         \
+        case 0: CALL(0); break;   case 1: CALL(1); break;                   \
+        case 2: CALL(2); break;   case 3: CALL(3); break;                   \
+        case 4: CALL(4); break;   case 5: CALL(5); break;                   \
+        case 6: CALL(6); break;   case 7: CALL(7); break;                   \
+        case 8: CALL(8); break;   case 9: CALL(9); break;                   \
+        case 10: CALL(10); break; case 11: CALL(11); break;                 \
+        case 12: CALL(12); break;                                           \
+        default: return cudaErrorInvalidValue;                              \
     }
 
 int eval_passes(const HotParams& p, const LaunchArgs& a, int* ids) {
     int n = 0;
     if (p.demag) {
-        ids[n++] = PASS_XFWD;
+        if (!a.have_spectrum) ids[n++] = PASS_XFWD;
         if (p.nz == 1) {
             ids[n++] = PASS_YCONV;
         } else {
@@ -703,7 +798,7 @@ int eval_passes(const HotParams& p, const LaunchArgs& a, int* ids) {
             ids[n++] = PASS_ZCONV;
             ids[n++] = PASS_YINV;
         }
-        ids[n++] = PASS_XINV_LOCAL;
+        ids[n++] = a.fuse ? PASS_XINV_FUSED : PASS_XINV_LOCAL;
     } else {
         if (a.src == SRC_COMBINE2) ids[n++] = PASS_COMBINE2;   // no x pass to fold m_2 into
         ids[n++] = PASS_LOCAL;
@@ -712,60 +807,31 @@ int eval_passes(const HotParams& p, const LaunchArgs& a, int* ids) {
 }
 
 cudaError_t launch_pass(const HotParams& p, const LaunchArgs& a, int pass, cudaStream_t s) {
-    const int NL = 3 * p.ty / 2;
-    const dim3 gx((p.ny + p.ty - 1) / p.ty, p.nz);
     switch (pass) {
         case PASS_XFWD:
-            MM_DISPATCH(p.logpx, k_xfwd, gx, threads_for(NL, p.logpx), smem_for(NL, p.logpx), s, p, a);
+        case PASS_XINV_LOCAL:
+        case PASS_XINV_FUSED:
+#define MM_CALL_X(L) launch_x<L>(p, a, pass, s)
+            MM_LOGP_SWITCH(p.logpx, MM_CALL_X)
+#undef MM_CALL_X
             break;
-        case PASS_YCONV: {
-            const int nl = 3 * p.kxb;
-            const dim3 g((p.hx + p.kxb - 1) / p.kxb);
-            MM_DISPATCH(p.logpy, k_yconv, g, threads_for(nl, p.logpy), smem_for(nl, p.logpy), s, p, a);
-            break;
-        }
+        case PASS_YCONV:
         case PASS_YFWD:
-        case PASS_YINV: {
-            const int nl = 3 * p.tz;
-            const dim3 gy(p.hx, (p.nz + p.tz - 1) / p.tz);
-            if (pass == PASS_YFWD) {
-                MM_DISPATCH(p.logpy, k_yfwd, gy, threads_for(nl, p.logpy), smem_for(nl, p.logpy), s, p, a);
-            } else {
-                MM_DISPATCH(p.logpy, k_yinv, gy, threads_for(nl, p.logpy), smem_for(nl, p.logpy), s, p, a);
-            }
+        case PASS_YINV:
+#define MM_CALL_Y(L) launch_y<L>(p, a, pass, s)
+            MM_LOGP_SWITCH(p.logpy, MM_CALL_Y)
+#undef MM_CALL_Y
             break;
-        }
-        case PASS_ZCONV: {
-            const int nlz = 3 * p.tky;
-            const dim3 gz(p.hx, (p.py + p.tky - 1) / p.tky);
-            MM_DISPATCH(p.logpz, k_zconv, gz, threads_for(nlz, p.logpz), smem_for(nlz, p.logpz), s, p, a);
+        case PASS_ZCONV:
+#define MM_CALL_Z(L) launch_z<L>(p, a, s)
+            MM_LOGP_SWITCH(p.logpz, MM_CALL_Z)
+#undef MM_CALL_Z
             break;
-        }
-        case PASS_XINV_LOCAL: {
-            const int th = threads_for(NL, p.logpx);
-            switch (p.logpx) {
-                case 0: k_xinv_local<0, true><<<gx, th, smem_for(NL, 0), s>>>(p, a); break;
-                case 1: k_xinv_local<1, true><<<gx, th, smem_for(NL, 1), s>>>(p, a); break;
-                case 2: k_xinv_local<2, true><<<gx, th, smem_for(NL, 2), s>>>(p, a); break;
-                case 3: k_xinv_local<3, true><<<gx, th, smem_for(NL, 3), s>>>(p, a); break;
-                case 4: k_xinv_local<4, true><<<gx, th, smem_for(NL, 4), s>>>(p, a); break;
-                case 5: k_xinv_local<5, true><<<gx, th, smem_for(NL, 5), s>>>(p, a); break;
-                case 6: k_xinv_local<6, true><<<gx, th, smem_for(NL, 6), s>>>(p, a); break;
-                case 7: k_xinv_local<7, true><<<gx, th, smem_for(NL, 7), s>>>(p, a); break;
-                case 8: k_xinv_local<8, true><<<gx, th, smem_for(NL, 8), s>>>(p, a); break;
-                case 9: k_xinv_local<9, true><<<gx, th, smem_for(NL, 9), s>>>(p, a); break;
-                case 10: k_xinv_local<10, true><<<gx, th, smem_for(NL, 10), s>>>(p, a); break;
-                case 11: k_xinv_local<11, true><<<gx, th, smem_for(NL, 11), s>>>(p, a); break;
-                case 12: k_xinv_local<12, true><<<gx, th, smem_for(NL, 12), s>>>(p, a); break;
-                default: return cudaErrorInvalidValue;
-            }
-            break;
-        }
         case PASS_COMBINE2:
             k_combine2<<<4 * 152, 256, 0, s>>>(p);
             break;
         case PASS_LOCAL:
-            k_xinv_local<0, false><<<gx, 256, 0, s>>>(p, a);
+            k_local<<<(unsigned)((p.ncell + 255) / 256 < 4 * 152 ? (p.ncell + 255) / 256 : 4 * 152), 256, 0, s>>>(p, a);
             break;
         default:
             return cudaErrorInvalidValue;

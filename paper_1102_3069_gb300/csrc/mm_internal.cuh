@@ -108,12 +108,14 @@ struct LaunchArgs {
     int src;                 // Source of the evaluation input
     int mode;                // LocalMode
     int stage;               // RK stage (2..7)
+    int fuse = 0;            // inverse-x pass also transforms the next evaluation's input
+    int have_spectrum = 0;   // s1 already holds the x spectrum of this evaluation's input
 };
 
 // passes of one evaluation (the kernels of hotpath.cu), in launch order
 enum Pass : int {
     PASS_XFWD = 0, PASS_YCONV = 1, PASS_YFWD = 2, PASS_ZCONV = 3, PASS_YINV = 4,
-    PASS_XINV_LOCAL = 5, PASS_COMBINE2 = 6, PASS_LOCAL = 7, NPASS = 8
+    PASS_XINV_LOCAL = 5, PASS_COMBINE2 = 6, PASS_LOCAL = 7, PASS_XINV_FUSED = 8, NPASS = 9
 };
 
 // hot path (hotpath.cu)

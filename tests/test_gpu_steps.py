@@ -113,8 +113,11 @@ def test_adaptive_run_to_1ns_smooth_state():
 
 
 def test_adaptive_run_to_1ns_random_state():
-    """The 64 x 16 film from random unit vectors, RKDP tol 1e-6 for 1 ns: the
-    trajectory is chaotic, so only run-level quantities are compared."""
+    """The 64 x 16 film from random unit vectors, RKDP tol 1e-6 for 1 ns.  The
+    trajectory is chaotic, so only run-level quantities are compared.  The
+    oracle itself, restarted from 1e-7 perturbations of this state or rounded
+    to float32 after every step, ends with 2809-3101 accepted steps and a
+    dissipated energy (E0 - E)/|E0| of 0.9906-0.9964 (measured)."""
     s, p = _pair()
     m = W["m"]
     md = to_dev(m)
@@ -127,12 +130,13 @@ def test_adaptive_run_to_1ns_random_state():
     ref = llg.Stepper(p, _m64(m), h0=1e-13, tol=1e-6)
     ref.run_until(1e-9)
     mg = to_np(md)
-    print("steps gpu", st["accepted"], st["rejected"], "oracle", ref.accepted, ref.rejected)
-    assert abs(st["accepted"] - ref.accepted) <= 0.10 * ref.accepted
-    assert np.max(np.abs(np.sqrt((mg * mg).sum(axis=0)) - 1.0)) <= 1e-6
     E0, Eg, Eo = p.energy(_m64(m)), p.energy(mg), p.energy(ref.m)
+    print("steps gpu", st["accepted"], st["rejected"], "oracle", ref.accepted, ref.rejected,
+          "dissipated gpu", (E0 - Eg) / abs(E0), "oracle", (E0 - Eo) / abs(E0))
+    assert abs(st["accepted"] - ref.accepted) <= 0.20 * ref.accepted
+    assert np.max(np.abs(np.sqrt((mg * mg).sum(axis=0)) - 1.0)) <= 1e-6
     assert Eg < E0 and Eo < E0
-    assert abs(Eg - Eo) <= 0.05 * abs(E0 - Eo)
+    assert abs(Eg - Eo) <= 0.02 * abs(E0 - Eo)
 
 
 def test_relax_reaches_bound_and_oracle_energy():
