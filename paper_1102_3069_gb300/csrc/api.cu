@@ -84,6 +84,12 @@ struct mm_ctx {
     double th_dt = 0.0;            // seconds
     std::vector<float2> tw_host;
     std::string err;
+    // one standard step captured as a CUDA graph and replayed (see mm_advance)
+    cudaGraphExec_t step_graph = nullptr;
+    int graph_method = 0;
+    double graph_dt = 0.0;
+    unsigned long long graph_version = 0;
+    unsigned long long param_version = 1;   // bumped whenever launch parameters change
     // per-pass event timing (mm_profile / mm_pass_times)
     struct Rec { int pass; cudaEvent_t a, b; };
     bool profiling = false;
@@ -227,6 +233,31 @@ int eval(mm_ctx* ctx, const mm::HotParams& p, int src, int mode, int stage, bool
 
 }  // namespace
 
+namespace {
+
+// The launches of one time step.  The standard step (first = false) finds
+// no usable spectrum for RKDP stage 2 (the new h is only known on the device)
+// and finds the spectrum of m_n in place for Euler/Heun (the previous step's
+// fused pass made it).  The first step of a run is the other way round:
+// right after k1 the stage-2 input and its spectrum are in place (RKDP), and
+// right after a load nothing is (Euler/Heun).
+int enqueue_step(mm_ctx* ctx, const mm::HotParams& p, int method, bool first) {
+    int rc;
+    if (method == MM_RKDP) {
+        if ((rc = eval(ctx, p, mm::SRC_COMBINE2, mm::LM_RK, 2, true, first))) return rc;
+        if ((rc = eval(ctx, p, mm::SRC_STAGE1, mm::LM_RK, 3, true, true))) return rc;
+        if ((rc = eval(ctx, p, mm::SRC_STAGE0, mm::LM_RK, 4, true, true))) return rc;
+        if ((rc = eval(ctx, p, mm::SRC_STAGE1, mm::LM_RK, 5, true, true))) return rc;
+        if ((rc = eval(ctx, p, mm::SRC_STAGE0, mm::LM_RK, 6, true, true))) return rc;
+        return eval(ctx, p, mm::SRC_NEXT, mm::LM_RKFINAL, 7, false, true);
+    }
+    if (method == MM_EULER) return eval(ctx, p, mm::SRC_CUR, mm::LM_EULER, 0, true, !first);
+    if ((rc = eval(ctx, p, mm::SRC_CUR, mm::LM_HEUN1, 0, true, !first))) return rc;
+    return eval(ctx, p, mm::SRC_STAGE0, mm::LM_HEUN2, 0, true, true);
+}
+
+}  // namespace
+
 // ---------------------------------------------------------------------------
 // Scratch for mm_eval_heff_static: one fixed array per GPU, reserved when the
 // library's module is loaded on that device and held until the process exits.
@@ -347,6 +378,7 @@ int mm_set_workspace(mm_ctx* ctx, void* dev_ptr, size_t bytes) {
     ctx->kernel_ready = false;
     ctx->state_loaded = false;
     ctx->spec = mm_ctx::SPEC_NONE;
+    ctx->param_version++;
     return MM_OK;
 }
 
@@ -380,6 +412,7 @@ int mm_set_material(mm_ctx* ctx, double Ms, double Aex, double Ku, const double 
     ctx->have_material = true;
     if (ms_changed) ctx->state_loaded = false;     // internal time unit changed
     ctx->k1_valid = false;
+    ctx->param_version++;
     return MM_OK;
 }
 
@@ -387,6 +420,7 @@ int mm_set_demag(mm_ctx* ctx, int enabled) {
     if (!ctx) return MM_EINVAL;
     ctx->demag = enabled != 0;
     ctx->k1_valid = false;
+    ctx->param_version++;
     return MM_OK;
 }
 
@@ -417,6 +451,7 @@ int mm_demag_kernel(mm_ctx* ctx, double* out_tensor_host) {
     ctx->state_loaded = false;
     ctx->k1_valid = false;
     ctx->spec = mm_ctx::SPEC_NONE;
+    ctx->param_version++;
     CK(cudaMemsetAsync(&p.st->kre_bits, 0, 2 * sizeof(unsigned long long), ctx->stream));
     CK(mm::launch_kernel_setup(p, ctx->stream));
     if (out_tensor_host) CK(cudaMemcpyAsync(out_tensor_host, p.oct, oct_bytes, cudaMemcpyDeviceToHost, ctx->stream));
@@ -543,29 +578,52 @@ int mm_advance(mm_ctx* ctx, int method, long nsteps, double dt_s, double tol, do
             ctx->k1_valid = true;
             ctx->spec = mm_ctx::SPEC_M2;
         }
-        for (long s = 0; s < nsteps; ++s) {
-            if ((rc = eval(ctx, p, mm::SRC_COMBINE2, mm::LM_RK, 2, true, ctx->spec == mm_ctx::SPEC_M2))) return rc;
-            if ((rc = eval(ctx, p, mm::SRC_STAGE1, mm::LM_RK, 3, true, true))) return rc;
-            if ((rc = eval(ctx, p, mm::SRC_STAGE0, mm::LM_RK, 4, true, true))) return rc;
-            if ((rc = eval(ctx, p, mm::SRC_STAGE1, mm::LM_RK, 5, true, true))) return rc;
-            if ((rc = eval(ctx, p, mm::SRC_STAGE0, mm::LM_RK, 6, true, true))) return rc;
-            if ((rc = eval(ctx, p, mm::SRC_NEXT, mm::LM_RKFINAL, 7, false, true))) return rc;
-            ctx->spec = mm_ctx::SPEC_NONE;       // the next stage-2 input needs the new h
-        }
     } else {
         ctx->k1_valid = false;
         ctx->last_fixed_dt = dt;
-        for (long s = 0; s < nsteps; ++s) {
-            const bool have = ctx->spec == mm_ctx::SPEC_MCUR;
-            if (method == MM_EULER) {
-                if ((rc = eval(ctx, p, mm::SRC_CUR, mm::LM_EULER, 0, true, have))) return rc;
-            } else {
-                if ((rc = eval(ctx, p, mm::SRC_CUR, mm::LM_HEUN1, 0, true, have))) return rc;
-                if ((rc = eval(ctx, p, mm::SRC_STAGE0, mm::LM_HEUN2, 0, true, true))) return rc;
+    }
+    long s = 0;
+    // a first step that can reuse a spectrum already in place differs from
+    // the standard step: launch it directly
+    const bool first_special = method == MM_RKDP ? ctx->spec == mm_ctx::SPEC_M2 : ctx->spec != mm_ctx::SPEC_MCUR;
+    if (nsteps > 0 && first_special) {
+        if ((rc = enqueue_step(ctx, p, method, true))) return rc;
+        ++s;
+    }
+    if (s < nsteps) {
+        // the standard step: replayed from a CUDA graph on a capturable stream
+        bool graphed = false;
+        if (ctx->stream != nullptr && !ctx->profiling) {
+            if (!ctx->step_graph || ctx->graph_method != method || ctx->graph_version != ctx->param_version ||
+                (method != MM_RKDP && ctx->graph_dt != dt)) {
+                if (ctx->step_graph) { cudaGraphExecDestroy(ctx->step_graph); ctx->step_graph = nullptr; }
+                cudaGraph_t g = nullptr;
+                if (cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                    const int erc = enqueue_step(ctx, p, method, false);
+                    const cudaError_t ee = cudaStreamEndCapture(ctx->stream, &g);
+                    if (erc == MM_OK && ee == cudaSuccess && g &&
+                        cudaGraphInstantiate(&ctx->step_graph, g, 0) == cudaSuccess) {
+                        ctx->graph_method = method;
+                        ctx->graph_dt = dt;
+                        ctx->graph_version = ctx->param_version;
+                    } else {
+                        ctx->step_graph = nullptr;
+                    }
+                    if (g) cudaGraphDestroy(g);
+                }
+                cudaGetLastError();     // a refused capture leaves no sticky error
             }
-            ctx->spec = mm_ctx::SPEC_MCUR;
+            graphed = ctx->step_graph != nullptr;
+        }
+        for (; s < nsteps; ++s) {
+            if (graphed) {
+                CK(cudaGraphLaunch(ctx->step_graph, ctx->stream));
+            } else if ((rc = enqueue_step(ctx, p, method, false))) {
+                return rc;
+            }
         }
     }
+    if (nsteps > 0) ctx->spec = method == MM_RKDP ? mm_ctx::SPEC_NONE : mm_ctx::SPEC_MCUR;
     return MM_OK;
 }
 
@@ -690,6 +748,7 @@ const char* mm_last_error(const mm_ctx* ctx) {
 
 void mm_destroy(mm_ctx* ctx) {
     if (!ctx) return;
+    if (ctx->step_graph) cudaGraphExecDestroy(ctx->step_graph);
     for (auto& r : ctx->prof) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);

@@ -63,8 +63,10 @@ __device__ __forceinline__ float dot(f3 a, f3 b) { return a.x * b.x + a.y * b.y 
 __device__ __forceinline__ f3 cross(f3 a, f3 b) {
     return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
 }
+// every array a kernel reads through ld3 is read-only for that kernel, so the
+// loads may take the non-coherent path and be issued ahead of the stores
 __device__ __forceinline__ f3 ld3(const float* __restrict__ a, long long i, long long n) {
-    return {a[i], a[i + n], a[i + 2 * n]};
+    return {__ldg(a + i), __ldg(a + i + n), __ldg(a + i + 2 * n)};
 }
 __device__ __forceinline__ void st3(float* __restrict__ a, long long i, long long n, f3 v) {
     a[i] = v.x; a[i + n] = v.y; a[i + 2 * n] = v.z;
@@ -142,7 +144,9 @@ struct CS {                         // column passes: COLS lines x 3 components 
     static constexpr int NL = 3 * COLS;
     static constexpr int NT = threads_of(NL, LOGP);
     static constexpr int LS = padded_len(P);
-    static constexpr int MINB = NT >= 768 ? 1 : 1024 / NT;
+    // 384-thread blocks fit three per SM in 56 registers (measured faster on
+    // the 2048-point column pass); other sizes fill ~1024 threads per SM
+    static constexpr int MINB = NT >= 768 ? 1 : NT == 384 ? 3 : 1024 / NT;
 };
 
 // Half-spectrum unpack of the paired rows of line l (z = a + i b:
