@@ -335,10 +335,10 @@ int mm_init_geometry(mm_ctx** out, int nx, int ny, int nz, double dx, double dy,
     // threads per block with one radix-16 butterfly each
     c->ty = mmfft::ty_of(c->logpx);
     c->nyp = (ny + 15) / 16 * 16;                  // a multiple of every x-pass tile
-    c->kxb = mmfft::kxb_of(c->logpy);
+    c->kxb = 1;                                    // column passes size their own blocks
     c->tz = mmfft::tz_of(c->logpy);
     c->nzp = (nz + c->tz - 1) / c->tz * c->tz;     // the 3-D y passes write whole z tiles
-    c->tky = mmfft::tky_of(c->logpz);
+    c->tky = 1;
     c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
     layout(c);
     // twiddle table, rounded once from double

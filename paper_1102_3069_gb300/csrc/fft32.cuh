@@ -43,9 +43,7 @@ __host__ __device__ constexpr int cols_of(int logp, int cap) {
          : (3 * 4 * nb_of(logp) <= 512 && cap >= 4) ? 4
          : (3 * 2 * nb_of(logp) <= 512 && cap >= 2) ? 2 : 1;
 }
-__host__ __device__ constexpr int kxb_of(int logp) { return cols_of(logp, 64); }   // 2-D y pass
 __host__ __device__ constexpr int tz_of(int logp) { return cols_of(logp, 8); }     // 3-D y passes
-__host__ __device__ constexpr int tky_of(int logp) { return cols_of(logp, 64); }   // 3-D z pass
 __host__ __device__ constexpr int threads_of(int nlines, int logp) {
     return ((nlines * nb_of(logp) + 31) / 32) * 32 < 64 ? 64 : ((nlines * nb_of(logp) + 31) / 32) * 32;
 }
@@ -287,4 +285,124 @@ __device__ __forceinline__ void fft_lines(float2* base, const float2* __restrict
     }
 }
 
+}  // namespace mmfft
+
+// ---------------------------------------------------------------------------
+// Radix-8 passes with several lines per thread (used by the column passes).
+//
+// A thread owns the same butterflies of NC lines (the three field components
+// of one column), so a point-wise 3x3 product between components needs no
+// shared memory.  Forward transforms use the radix order 8, 8, ..., REM and
+// inverse transforms the reversed order REM, 8, ..., 8 (REM = 2^(LOGP mod 3)).
+// In Stockham order the last pass of a transform leaves butterfly jj's
+// outputs at positions jj + r*P/R - exactly the inputs of a first pass of the
+// same radix - so "forward, product, inverse" keeps the data in registers
+// across the product.
+namespace mmfft {
+namespace r8 {
+
+template <int LOGP>
+struct Plan8 {
+    static constexpr int P = 1 << LOGP;
+    static constexpr int N8 = LOGP >= 3 ? LOGP / 3 : 0;
+    static constexpr int REM = LOGP >= 3 ? (1 << (LOGP % 3)) : P;
+    static constexpr int NPASS = LOGP >= 3 ? N8 + (REM > 1 ? 1 : 0) : (LOGP > 0 ? 1 : 0);
+    static constexpr int NB = LOGP >= 3 ? P / 8 : 1;          // threads per line
+    static constexpr int LS = padded_len(P);
+};
+
+// radix of pass p (REV: reversed order)
+template <int LOGP, bool REV>
+__host__ __device__ constexpr int radix_at(int p) {
+    using PL = Plan8<LOGP>;
+    if (LOGP < 3) return PL::P;
+    if (PL::REM == 1) return 8;
+    if (!REV) return p < PL::N8 ? 8 : PL::REM;
+    return p == 0 ? PL::REM : 8;
+}
+// product of the radices before pass p
+template <int LOGP, bool REV>
+__host__ __device__ constexpr int ns_at(int p) {
+    int ns = 1;
+    for (int q = 0; q < p; ++q) ns *= radix_at<LOGP, REV>(q);
+    return ns;
+}
+// butterflies per thread in a pass of radix R
+template <int LOGP>
+__host__ __device__ constexpr int bpt_of(int R) { return LOGP >= 3 ? 8 / R : 1; }
+
+// position of register value i (= b*R + r) at the input / output of pass PI
+template <int LOGP, bool REV, int PI>
+__device__ __forceinline__ int in_pos(int j, int i) {
+    constexpr int R = radix_at<LOGP, REV>(PI);
+    const int b = i / R, r = i - b * R;
+    return j + b * Plan8<LOGP>::NB + r * (Plan8<LOGP>::P / R);
+}
+template <int LOGP, bool REV, int PI>
+__device__ __forceinline__ int out_pos(int j, int i) {
+    constexpr int R = radix_at<LOGP, REV>(PI), NS = ns_at<LOGP, REV>(PI);
+    const int b = i / R, r = i - b * R;
+    const int jj = j + b * Plan8<LOGP>::NB, k = jj & (NS - 1);
+    return (jj - k) * R + k + r * NS;
+}
+// number of register values in use
+template <int LOGP>
+__host__ __device__ constexpr int nval() { return LOGP >= 3 ? 8 : (1 << LOGP); }
+
+template <int LOGP, bool REV, bool INV, int PI>
+__device__ __forceinline__ void compute(float2* v, int j, const float2* __restrict__ tw) {
+    constexpr int R = radix_at<LOGP, REV>(PI), NS = ns_at<LOGP, REV>(PI), BPT = bpt_of<LOGP>(R);
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+        if constexpr (NS > 1) {
+            const int jj = j + b * Plan8<LOGP>::NB, k = jj & (NS - 1);
+            apply_twiddles<R, INV>(v + b * R, tw, k * (TWN / (NS * R)));
+        }
+        dft<R, INV>(v + b * R);
+    }
+}
+template <int LOGP, bool REV, int PI>
+__device__ __forceinline__ void load(const float2* a, float2* v, int j) {
+#pragma unroll
+    for (int i = 0; i < nval<LOGP>(); ++i) v[i] = a[pad(in_pos<LOGP, REV, PI>(j, i))];
+}
+template <int LOGP, bool REV, int PI>
+__device__ __forceinline__ void store(float2* a, const float2* v, int j) {
+#pragma unroll
+    for (int i = 0; i < nval<LOGP>(); ++i) a[pad(out_pos<LOGP, REV, PI>(j, i))] = v[i];
+}
+
+// Passes PI..NPASS-1 of NC lines held by this thread; on entry the values of
+// pass PI's inputs are in shared memory (LOAD = true) or already in registers
+// (LOAD = false, only for PI == 0 or straight after the previous pass).  On
+// return the last pass's outputs are in registers.  Every thread of the block
+// must call it (barriers inside).
+template <int LOGP, bool REV, bool INV, int PI, int NC>
+__device__ __forceinline__ void run(float2* const* a, float2 (*v)[8], int j, bool active,
+                                    const float2* __restrict__ tw, bool from_smem) {
+    using PL = Plan8<LOGP>;
+    if constexpr (PI < PL::NPASS) {
+        if (from_smem) {
+            if (active) {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) load<LOGP, REV, PI>(a[c], v[c], j);
+            }
+        }
+        if (active) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) compute<LOGP, REV, INV, PI>(v[c], j, tw);
+        }
+        if constexpr (PI + 1 < PL::NPASS) {
+            __syncthreads();
+            if (active) {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) store<LOGP, REV, PI>(a[c], v[c], j);
+            }
+            __syncthreads();
+            run<LOGP, REV, INV, PI + 1, NC>(a, v, j, active, tw, true);
+        }
+    }
+}
+
+}  // namespace r8
 }  // namespace mmfft

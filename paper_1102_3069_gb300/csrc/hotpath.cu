@@ -9,11 +9,12 @@
 //                contiguous), so the next pass reads whole columns.  Padded
 //                rows (y >= ny, z >= nz) are never transformed (Sec. 3.2: no
 //                FFTs of all-zero arrays).
-//   k_yconv      2-D grids: per kx column, forward FFT along y, point-wise
-//                product with the real symmetric kernel (Sec. 3.2), inverse FFT
-//                along y - one pass instead of three.
-//   k_yfwd, k_zconv, k_yinv   3-D grids: y forward (writes [c][kx][ky][z]),
-//                fused z forward/product/inverse, y inverse.
+//   k_colconv    the last transformed axis (y for 2-D grids, z for 3-D
+//                grids): forward FFT, point-wise product with the real
+//                symmetric kernel (Sec. 3.2), inverse FFT, in one pass; the
+//                product happens in registers between the two transforms.
+//   k_yfwd, k_yinv   3-D grids only: y forward (writes [c][kx][ky][z]) before
+//                and y inverse after the z column pass.
 //   k_xinv_local complex-to-real FFT along x, crop, and the whole cell-local
 //                remainder of the step fused into its epilogue: exchange
 //                (Eq. 3), uniaxial anisotropy (Eq. 4), Zeeman, thermal field
@@ -28,6 +29,7 @@
 
 namespace mm {
 using namespace mmfft;
+namespace r8 = mmfft::r8;
 
 // Dormand-Prince 5(4) tableau (Dormand & Prince 1980), double precision.
 // c_dpa[s][j]: weight of k_j in the input of stage s (s = 2..7, j = 1..6);
@@ -209,48 +211,113 @@ __global__ void __launch_bounds__(XS<LOGP>::NT, XS<LOGP>::MINB) k_xfwd(HotParams
 }
 
 // ---------------------------------------------------------------------------
-// 2-D column pass: y forward FFT, kernel product, y inverse FFT (in place).
+// Column pass with the kernel product in registers (Sec. 3.2 stages i-iii
+// along the last transformed axis): forward FFT, product with the real
+// symmetric kernel, inverse FFT.  MODE 0: 2-D grids, lines along y of s1
+// (kernel components xx yy zz xy; xy odd in ky).  MODE 1: 3-D grids, lines
+// along z of s2 (six components; xy, yz odd in ky; xz, yz odd in kz).
+// Every thread owns the same radix-8 butterflies of the three components of
+// one column; the first forward pass reads global memory directly and the
+// last inverse pass writes it directly.
 template <int LOGP>
-__global__ void __launch_bounds__(CS<LOGP, kxb_of(LOGP)>::NT, CS<LOGP, kxb_of(LOGP)>::MINB)
-k_yconv(HotParams p, LaunchArgs a) {
-    constexpr int KXB = kxb_of(LOGP);
-    using S = CS<LOGP, KXB>;
+struct CC {
+    using PL = r8::Plan8<LOGP>;
+    static constexpr int P = PL::P, NB = PL::NB, LS = PL::LS;
+    static constexpr int COLS = NB >= 256 ? 1 : (256 / NB > 64 ? 64 : 256 / NB);
+    static constexpr int NT = (COLS * NB + 31) / 32 * 32 < 64 ? 64 : (COLS * NB + 31) / 32 * 32;
+    static constexpr int LASTF = PL::NPASS > 0 ? PL::NPASS - 1 : 0;
+};
+
+template <int LOGP, bool REV>
+__device__ __forceinline__ int last_out_pos(int j, int i) {
+    if constexpr (r8::Plan8<LOGP>::NPASS == 0) return 0;
+    else return r8::out_pos<LOGP, REV, CC<LOGP>::LASTF>(j, i);
+}
+
+template <int LOGP, int MODE>
+__global__ void __launch_bounds__(CC<LOGP>::NT, CC<LOGP>::NT <= 256 ? 3 : 1) k_colconv(HotParams p, LaunchArgs a) {
+    using S = CC<LOGP>;
+    constexpr int NV = r8::nval<LOGP>();
     extern __shared__ float2 sm[];
-    const int kx0 = blockIdx.x * KXB;
     if (a.mode != LM_EVAL && p.st->done) return;
-    const int HX = p.hx, NY = p.ny;
-    for (int idx = threadIdx.x; idx < S::NL * S::P; idx += S::NT) {
-        const int l = idx >> LOGP, y = idx & (S::P - 1);
-        const int c = l / KXB, j = l - c * KXB, kx = kx0 + j;
-        float2 v = make_float2(0.f, 0.f);
-        if (kx < HX && y < NY) v = p.s1[(long long)(c * HX + kx) * p.nyp + y];
-        sm[l * S::LS + pad(y)] = v;
+    const int tid = threadIdx.x;
+    int cl = tid / S::NB;
+    const int j = tid - cl * S::NB;
+    const bool inblock = cl < S::COLS;
+    if (!inblock) cl = 0;
+    const int HX = p.hx, PY = p.py;
+    int kx, ky = 0, nvalid;
+    bool valid;
+    long long base, cstride;
+    float2* buf;
+    if constexpr (MODE == 0) {
+        kx = blockIdx.x * S::COLS + cl;
+        valid = kx < HX;
+        base = (long long)kx * p.nyp;
+        cstride = (long long)HX * p.nyp;
+        nvalid = p.ny;
+        buf = p.s1;
+    } else {
+        kx = blockIdx.x;
+        ky = blockIdx.y * S::COLS + cl;
+        valid = ky < PY;
+        base = ((long long)kx * PY + ky) * p.nzp;
+        cstride = (long long)HX * PY * p.nzp;
+        nvalid = p.nz;
+        buf = p.s2;
     }
-    __syncthreads();
-    fft_lines<LOGP, S::NL, false>(sm, p.tw);
-    const long long cs = (long long)HX * p.hyk;       // kernel component stride (hzk == 1)
-    for (int idx = threadIdx.x; idx < KXB * S::P; idx += S::NT) {
-        const int j = idx >> LOGP, ky = idx & (S::P - 1), kx = kx0 + j;
-        if (kx >= HX) continue;
-        const bool hi = ky > (S::P >> 1);
-        const int kq = hi ? S::P - ky : ky;
-        const long long b = (long long)kx * p.hyk + kq;
-        const float kxx = __ldg(p.kt + b), kyy = __ldg(p.kt + cs + b), kzz = __ldg(p.kt + 2 * cs + b);
-        const float kxy = hi ? -__ldg(p.kt + 3 * cs + b) : __ldg(p.kt + 3 * cs + b);
-        float2* mx = sm + (0 * KXB + j) * S::LS + pad(ky);
-        float2* my = sm + (1 * KXB + j) * S::LS + pad(ky);
-        float2* mz = sm + (2 * KXB + j) * S::LS + pad(ky);
-        const float2 X = *mx, Y = *my, Z = *mz;
-        *mx = make_float2(kxx * X.x + kxy * Y.x, kxx * X.y + kxy * Y.y);
-        *my = make_float2(kxy * X.x + kyy * Y.x, kxy * X.y + kyy * Y.y);
-        *mz = make_float2(kzz * Z.x, kzz * Z.y);
+    const bool act = inblock && valid;
+    float2* lines[3] = {sm + (0 * S::COLS + cl) * S::LS, sm + (1 * S::COLS + cl) * S::LS,
+                        sm + (2 * S::COLS + cl) * S::LS};
+    float2 v[3][8];
+    if (act) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int i = 0; i < NV; ++i) {
+                const int pos = S::PL::NPASS > 0 ? r8::in_pos<LOGP, false, 0>(j, i) : 0;
+                v[c][i] = pos < nvalid ? buf[base + c * cstride + pos] : make_float2(0.f, 0.f);
+            }
     }
-    __syncthreads();
-    fft_lines<LOGP, S::NL, true>(sm, p.tw);
-    for (int idx = threadIdx.x; idx < S::NL * S::P; idx += S::NT) {
-        const int l = idx >> LOGP, y = idx & (S::P - 1);
-        const int c = l / KXB, j = l - c * KXB, kx = kx0 + j;
-        if (kx < HX && y < NY) p.s1[(long long)(c * HX + kx) * p.nyp + y] = sm[l * S::LS + pad(y)];
+    r8::run<LOGP, false, false, 0, 3>(lines, v, j, act, p.tw, false);
+    if (act) {
+        const long long cs = (long long)HX * p.hyk * p.hzk;
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            const int pos = last_out_pos<LOGP, false>(j, i);
+            const bool hi = pos > (S::P >> 1);
+            const int kq = hi ? S::P - pos : pos;
+            const float2 X = v[0][i], Y = v[1][i], Z = v[2][i];
+            if constexpr (MODE == 0) {
+                const long long b = (long long)kx * p.hyk + kq;
+                const float kxx = __ldg(p.kt + b), kyy = __ldg(p.kt + cs + b), kzz = __ldg(p.kt + 2 * cs + b);
+                const float kxy = hi ? -__ldg(p.kt + 3 * cs + b) : __ldg(p.kt + 3 * cs + b);
+                v[0][i] = make_float2(kxx * X.x + kxy * Y.x, kxx * X.y + kxy * Y.y);
+                v[1][i] = make_float2(kxy * X.x + kyy * Y.x, kxy * X.y + kyy * Y.y);
+                v[2][i] = make_float2(kzz * Z.x, kzz * Z.y);
+            } else {
+                const bool yh = ky > (PY >> 1);
+                const int kyq = yh ? PY - ky : ky;
+                const long long b = ((long long)kx * p.hyk + kyq) * p.hzk + kq;
+                const float kxx = __ldg(p.kt + b), kyy = __ldg(p.kt + cs + b), kzz = __ldg(p.kt + 2 * cs + b);
+                float kxy = __ldg(p.kt + 3 * cs + b), kxz = __ldg(p.kt + 4 * cs + b), kyz = __ldg(p.kt + 5 * cs + b);
+                if (yh) { kxy = -kxy; kyz = -kyz; }
+                if (hi) { kxz = -kxz; kyz = -kyz; }
+                v[0][i] = make_float2(kxx * X.x + kxy * Y.x + kxz * Z.x, kxx * X.y + kxy * Y.y + kxz * Z.y);
+                v[1][i] = make_float2(kxy * X.x + kyy * Y.x + kyz * Z.x, kxy * X.y + kyy * Y.y + kyz * Z.y);
+                v[2][i] = make_float2(kxz * X.x + kyz * Y.x + kzz * Z.x, kxz * X.y + kyz * Y.y + kzz * Z.y);
+            }
+        }
+    }
+    r8::run<LOGP, true, true, 0, 3>(lines, v, j, act, p.tw, false);
+    if (act) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int i = 0; i < NV; ++i) {
+                const int pos = last_out_pos<LOGP, true>(j, i);
+                if (pos < nvalid) buf[base + c * cstride + pos] = v[c][i];
+            }
     }
 }
 
@@ -277,53 +344,6 @@ k_yfwd(HotParams p, LaunchArgs a) {
     for (int idx = threadIdx.x; idx < S::NL * S::P; idx += S::NT) {
         const int zt = idx % TZ, r = idx / TZ, ky = r & (S::P - 1), c = r >> LOGP;
         p.s2[((long long)(c * HX + kx) * S::P + ky) * p.nzp + z0 + zt] = sm[(c * TZ + zt) * S::LS + pad(ky)];
-    }
-}
-
-// 3-D: fused z pass (forward, kernel product, inverse) on s2 in place.
-template <int LOGP>
-__global__ void __launch_bounds__(CS<LOGP, tky_of(LOGP)>::NT, CS<LOGP, tky_of(LOGP)>::MINB)
-k_zconv(HotParams p, LaunchArgs a) {
-    constexpr int TK = tky_of(LOGP);
-    using S = CS<LOGP, TK>;
-    extern __shared__ float2 sm[];
-    const int kx = blockIdx.x, ky0 = blockIdx.y * TK;
-    if (a.mode != LM_EVAL && p.st->done) return;
-    const int HX = p.hx, PY = p.py, NZ = p.nz;
-    for (int idx = threadIdx.x; idx < S::NL * S::P; idx += S::NT) {
-        const int l = idx >> LOGP, z = idx & (S::P - 1);
-        const int c = l / TK, j = l - c * TK, ky = ky0 + j;
-        float2 v = make_float2(0.f, 0.f);
-        if (ky < PY && z < NZ) v = p.s2[((long long)(c * HX + kx) * PY + ky) * p.nzp + z];
-        sm[l * S::LS + pad(z)] = v;
-    }
-    __syncthreads();
-    fft_lines<LOGP, S::NL, false>(sm, p.tw);
-    const long long cs = (long long)HX * p.hyk * p.hzk;
-    for (int idx = threadIdx.x; idx < TK * S::P; idx += S::NT) {
-        const int j = idx >> LOGP, kz = idx & (S::P - 1), ky = ky0 + j;
-        if (ky >= PY) continue;
-        const bool yh = ky > (PY >> 1), zh = kz > (S::P >> 1);
-        const int kyq = yh ? PY - ky : ky, kzq = zh ? S::P - kz : kz;
-        const long long b = ((long long)kx * p.hyk + kyq) * p.hzk + kzq;
-        const float kxx = __ldg(p.kt + b), kyy = __ldg(p.kt + cs + b), kzz = __ldg(p.kt + 2 * cs + b);
-        float kxy = __ldg(p.kt + 3 * cs + b), kxz = __ldg(p.kt + 4 * cs + b), kyz = __ldg(p.kt + 5 * cs + b);
-        if (yh) { kxy = -kxy; kyz = -kyz; }
-        if (zh) { kxz = -kxz; kyz = -kyz; }
-        float2* mx = sm + (0 * TK + j) * S::LS + pad(kz);
-        float2* my = sm + (1 * TK + j) * S::LS + pad(kz);
-        float2* mz = sm + (2 * TK + j) * S::LS + pad(kz);
-        const float2 X = *mx, Y = *my, Z = *mz;
-        *mx = make_float2(kxx * X.x + kxy * Y.x + kxz * Z.x, kxx * X.y + kxy * Y.y + kxz * Z.y);
-        *my = make_float2(kxy * X.x + kyy * Y.x + kyz * Z.x, kxy * X.y + kyy * Y.y + kyz * Z.y);
-        *mz = make_float2(kxz * X.x + kyz * Y.x + kzz * Z.x, kxz * X.y + kyz * Y.y + kzz * Z.y);
-    }
-    __syncthreads();
-    fft_lines<LOGP, S::NL, true>(sm, p.tw);
-    for (int idx = threadIdx.x; idx < S::NL * S::P; idx += S::NT) {
-        const int l = idx >> LOGP, z = idx & (S::P - 1);
-        const int c = l / TK, j = l - c * TK, ky = ky0 + j;
-        if (ky < PY && z < NZ) p.s2[((long long)(c * HX + kx) * PY + ky) * p.nzp + z] = sm[l * S::LS + pad(z)];
     }
 }
 
@@ -466,39 +486,70 @@ struct StageCoefs {
 
 // Returns the magnetisation the next evaluation of this step reads at this
 // cell (m_{s+1}, m_2, the predictor or m_{n+1}); zero when there is none.
+// All loads the cell needs - m, its neighbours and the stage inputs - are
+// issued before any arithmetic, so their latencies overlap.
 __device__ __forceinline__ f3 cell_update(const HotParams& p, const LaunchArgs& a, int cur, const StageCoefs& sc,
                                           const float* __restrict__ min, long long cell, int x, int y, int z,
                                           f3 hd, long long tstep, Partials& pt) {
     const long long n = p.ncell;
-    const f3 m = ld3(min, cell, n);
-    // exchange, 6-neighbour (4 in 2-D) Laplacian; a missing neighbour adds nothing
-    f3 hex;
-    {
-        f3 s = mk(0.f, 0.f, 0.f);
-        if (x + 1 < p.nx) s = s + (ld3(min, cell + 1, n) - m);
-        else if (p.pbc[0]) s = s + (ld3(min, cell - (p.nx - 1), n) - m);
-        if (x > 0) s = s + (ld3(min, cell - 1, n) - m);
-        else if (p.pbc[0]) s = s + (ld3(min, cell + (p.nx - 1), n) - m);
-        hex = p.cex[0] * s;
-    }
-    if (p.ny > 1 || p.pbc[1]) {
+    // neighbour indices; a missing neighbour (free boundary) points at the cell
+    // itself, so its difference is zero
+    long long ixp = cell, ixm = cell;
+    if (x + 1 < p.nx) ixp = cell + 1;
+    else if (p.pbc[0]) ixp = cell - (p.nx - 1);
+    if (x > 0) ixm = cell - 1;
+    else if (p.pbc[0]) ixm = cell + (p.nx - 1);
+    const bool usey = p.ny > 1 || p.pbc[1];
+    const bool usez = p.nz > 1 || p.pbc[2];
+    long long iyp = cell, iym = cell, izp = cell, izm = cell;
+    if (usey) {
         const long long sy = p.nx;
-        f3 s = mk(0.f, 0.f, 0.f);
-        if (y + 1 < p.ny) s = s + (ld3(min, cell + sy, n) - m);
-        else if (p.pbc[1]) s = s + (ld3(min, cell - (long long)(p.ny - 1) * sy, n) - m);
-        if (y > 0) s = s + (ld3(min, cell - sy, n) - m);
-        else if (p.pbc[1]) s = s + (ld3(min, cell + (long long)(p.ny - 1) * sy, n) - m);
-        hex = hex + p.cex[1] * s;
+        if (y + 1 < p.ny) iyp = cell + sy;
+        else if (p.pbc[1]) iyp = cell - (long long)(p.ny - 1) * sy;
+        if (y > 0) iym = cell - sy;
+        else if (p.pbc[1]) iym = cell + (long long)(p.ny - 1) * sy;
     }
-    if (p.nz > 1 || p.pbc[2]) {
+    if (usez) {
         const long long sz = (long long)p.nx * p.ny;
-        f3 s = mk(0.f, 0.f, 0.f);
-        if (z + 1 < p.nz) s = s + (ld3(min, cell + sz, n) - m);
-        else if (p.pbc[2]) s = s + (ld3(min, cell - (long long)(p.nz - 1) * sz, n) - m);
-        if (z > 0) s = s + (ld3(min, cell - sz, n) - m);
-        else if (p.pbc[2]) s = s + (ld3(min, cell + (long long)(p.nz - 1) * sz, n) - m);
-        hex = hex + p.cex[2] * s;
+        if (z + 1 < p.nz) izp = cell + sz;
+        else if (p.pbc[2]) izp = cell - (long long)(p.nz - 1) * sz;
+        if (z > 0) izm = cell - sz;
+        else if (p.pbc[2]) izm = cell + (long long)(p.nz - 1) * sz;
     }
+    const f3 m = ld3(min, cell, n);
+    const f3 mxp = ld3(min, ixp, n), mxm = ld3(min, ixm, n);
+    f3 myp = m, mym = m, mzp = m, mzm = m;
+    if (usey) { myp = ld3(min, iyp, n); mym = ld3(min, iym, n); }
+    if (usez) { mzp = ld3(min, izp, n); mzm = ld3(min, izm, n); }
+    // stage inputs: q[0] = m_n, q[1] = k1, q[j] = k_j
+    f3 q0 = mk(0.f, 0.f, 0.f), q1 = q0, q2 = q0, q3 = q0, q4 = q0, q5 = q0, q6 = q0;
+    const int s = a.stage;
+    switch (a.mode) {
+        case LM_RK:
+            q0 = ld3(p.ms[cur], cell, n);
+            q1 = ld3(p.ks[cur], cell, n);
+            if (s >= 3 && sc.c[2].hi != 0.f) q2 = ld3(p.kb[2], cell, n);
+            if (s >= 4) q3 = ld3(p.kb[3], cell, n);
+            if (s >= 5) q4 = ld3(p.kb[4], cell, n);
+            if (s >= 6) q5 = ld3(p.kb[5], cell, n);
+            break;
+        case LM_RKFINAL:
+            q1 = ld3(p.ks[cur], cell, n);
+            q3 = ld3(p.kb[3], cell, n);
+            q4 = ld3(p.kb[4], cell, n);
+            q5 = ld3(p.kb[5], cell, n);
+            q6 = ld3(p.kb[6], cell, n);
+            break;
+        case LM_HEUN2:
+            q0 = ld3(p.ms[cur], cell, n);
+            q1 = ld3(p.ks[cur], cell, n);
+            break;
+        default: break;
+    }
+    // exchange, 6-neighbour (4 in 2-D) Laplacian (Eq. 3)
+    f3 hex = p.cex[0] * ((mxp - m) + (mxm - m));
+    if (usey) hex = hex + p.cex[1] * ((myp - m) + (mym - m));
+    if (usez) hex = hex + p.cex[2] * ((mzp - m) + (mzm - m));
     const f3 u = mk(p.ux, p.uy, p.uz);
     const f3 han = (p.kan * dot(m, u)) * u;
     const f3 hz = mk(p.hzx, p.hzy, p.hzz);
@@ -525,13 +576,13 @@ __device__ __forceinline__ f3 cell_update(const HotParams& p, const LaunchArgs& 
             next = axpy(sc.c[1], k, m);                 // m_2 = m_n + h a21 k1
             st3(p.mstage[0], cell, n, next);
             break;
-        case LM_RK: {
-            const int s = a.stage;                       // 2..6
+        case LM_RK: {                                    // stages 2..6
             st3(p.kb[s], cell, n, k);
-            f3 acc = ld3(p.ms[cur], cell, n);
-            acc = axpy(sc.c[1], ld3(p.ks[cur], cell, n), acc);
-            for (int j = 2; j < s; ++j)
-                if (sc.c[j].hi != 0.f) acc = axpy(sc.c[j], ld3(p.kb[j], cell, n), acc);
+            f3 acc = axpy(sc.c[1], q1, q0);
+            if (s >= 3 && sc.c[2].hi != 0.f) acc = axpy(sc.c[2], q2, acc);
+            if (s >= 4) acc = axpy(sc.c[3], q3, acc);
+            if (s >= 5) acc = axpy(sc.c[4], q4, acc);
+            if (s >= 6) acc = axpy(sc.c[5], q5, acc);
             acc = axpy(sc.c[s], k, acc);
             if (s < 6) {
                 st3(p.mstage[(s + 1) & 1], cell, n, acc);
@@ -546,9 +597,11 @@ __device__ __forceinline__ f3 cell_update(const HotParams& p, const LaunchArgs& 
         case LM_RKFINAL: {
             st3(p.ks[1 - cur], cell, n, k);
             f3 e = mk(0.f, 0.f, 0.f);
-            e = axpy(sc.c[1], ld3(p.ks[cur], cell, n), e);
-#pragma unroll
-            for (int j = 3; j <= 6; ++j) e = axpy(sc.c[j], ld3(p.kb[j], cell, n), e);
+            e = axpy(sc.c[1], q1, e);
+            e = axpy(sc.c[3], q3, e);
+            e = axpy(sc.c[4], q4, e);
+            e = axpy(sc.c[5], q5, e);
+            e = axpy(sc.c[6], q6, e);
             e = axpy(sc.c[7], k, e);
             pt.err = fmaxf(pt.err, sqrtf(dot(e, e)));
             pt.torque = fmaxf(pt.torque, tq);
@@ -569,8 +622,7 @@ __device__ __forceinline__ f3 cell_update(const HotParams& p, const LaunchArgs& 
             break;
         }
         case LM_HEUN2: {
-            f3 acc = ld3(p.ms[cur], cell, n);
-            acc = axpy(sc.c[0], ld3(p.ks[cur], cell, n), acc);
+            f3 acc = axpy(sc.c[0], q1, q0);
             acc = axpy(sc.c[0], k, acc);
             next = normalized(acc);
             st3(p.ms[1 - cur], cell, n, next);
@@ -735,9 +787,9 @@ static cudaError_t set_attr_all() {
     cudaError_t e;
     const int mx = 200 * 1024;
     if ((e = cudaFuncSetAttribute(k_xfwd<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
-    if ((e = cudaFuncSetAttribute(k_yconv<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_colconv<L, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_colconv<L, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_yfwd<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
-    if ((e = cudaFuncSetAttribute(k_zconv<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_yinv<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_xinv_local<L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_xinv_local<L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
@@ -760,9 +812,9 @@ static void launch_x(const HotParams& p, const LaunchArgs& a, int pass, cudaStre
 template <int L>
 static void launch_y(const HotParams& p, const LaunchArgs& a, int pass, cudaStream_t s) {
     if (pass == PASS_YCONV) {
-        using S = CS<L, kxb_of(L)>;
-        const dim3 g((p.hx + kxb_of(L) - 1) / kxb_of(L));
-        k_yconv<L><<<g, S::NT, (size_t)S::NL * S::LS * sizeof(float2), s>>>(p, a);
+        using S = CC<L>;
+        const dim3 g((p.hx + S::COLS - 1) / S::COLS);
+        k_colconv<L, 0><<<g, S::NT, (size_t)3 * S::COLS * S::LS * sizeof(float2), s>>>(p, a);
     } else {
         using S = CS<L, tz_of(L)>;
         const dim3 g(p.hx, (p.nz + tz_of(L) - 1) / tz_of(L));
@@ -774,9 +826,9 @@ static void launch_y(const HotParams& p, const LaunchArgs& a, int pass, cudaStre
 
 template <int L>
 static void launch_z(const HotParams& p, const LaunchArgs& a, cudaStream_t s) {
-    using S = CS<L, tky_of(L)>;
-    const dim3 g(p.hx, (p.py + tky_of(L) - 1) / tky_of(L));
-    k_zconv<L><<<g, S::NT, (size_t)S::NL * S::LS * sizeof(float2), s>>>(p, a);
+    using S = CC<L>;
+    const dim3 g(p.hx, (p.py + S::COLS - 1) / S::COLS);
+    k_colconv<L, 1><<<g, S::NT, (size_t)3 * S::COLS * S::LS * sizeof(float2), s>>>(p, a);
 }
 
 #define MM_LOGP_SWITCH(LOGP, CALL)                                          \
