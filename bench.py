@@ -148,7 +148,7 @@ def algorithmic_bytes(nx, ny):
     xf = spec + 3 * m                      # stage 2 input m_n + h a21 k1, written out as m_2
     return {
         "k_xfwd": float(xf),
-        "k_yconv": float(2 * spec + kern),
+        "k_colconv_y": float(2 * spec + kern),
         "k_xinv_local_fused": sum(fused) / 5.0,
         "k_xinv_local": float(final),
         "step": float(xf + 6 * (2 * spec + kern) + sum(fused) + final),

@@ -217,7 +217,7 @@ def mm_run_host(ctx, m_host, method, nsteps, dt_s=0.0, tol=1e-6):
     return _check(ctx, lib().mm_run_host(ctx, _ptr(m_host), int(method), int(nsteps), float(dt_s), float(tol)))
 
 
-PASS_NAMES = ["k_xfwd", "k_yconv", "k_yfwd", "k_zconv", "k_yinv", "k_xinv_local", "k_combine2", "k_local",
+PASS_NAMES = ["k_xfwd", "k_colconv_y", "k_yfwd", "k_colconv_z", "k_yinv", "k_xinv_local", "k_combine2", "k_local",
               "k_xinv_local_fused"]
 NPASS = len(PASS_NAMES)
 
