@@ -33,6 +33,13 @@ WORKLOAD = "film_1024x1024"
 METRIC = "Heff cell-evals/s"
 UNIT = "cell-evals/s"
 EVALS_PER_STEP = 6
+# workload -> time stepping used for it
+METHODS = {
+    "film_1024x1024": {"method": "RKDP", "tol": 1e-6, "evals": 6,
+                       "desc": "RKDP adaptive, tol 1e-6"},
+    "cube_256x256x64": {"method": "HEUN", "dt": 50e-15, "evals": 2,
+                        "desc": "Heun, dt 50 fs, thermal field at 300 K (one Philox draw per step)"},
+}
 
 
 def _peaks():
@@ -155,6 +162,28 @@ def algorithmic_bytes(nx, ny):
     }
 
 
+def algorithmic_bytes_3d(shape, pz, images_axes=(True, True, False)):
+    """Bytes per pass for the 3-D sequence (x fused, y forward, z column, y inverse), Heun stages."""
+    nx, ny, nz = shape
+    N = nx * ny * nz
+    px = nx if images_axes[0] else 2 * nx
+    py = ny if images_axes[1] else 2 * ny
+    hx = px // 2 + 1
+    s1 = 3 * hx * nz * ny * 8
+    s2 = 3 * hx * py * nz * 8
+    kern = 6 * hx * (py // 2 + 1) * (pz // 2 + 1) * 4
+    m = 12 * N
+    heun1 = s1 + m + 2 * m + s1            # k1 and the predictor written, next spectrum written
+    heun2 = s1 + m + 2 * m + m + s1        # m_n and k1 read, m_{n+1} written, next spectrum written
+    return {
+        "k_yfwd": float(s1 + s2),
+        "k_colconv_z": float(2 * s2 + kern),
+        "k_yinv": float(s2 + s1),
+        "k_xinv_local_fused": (heun1 + heun2) / 2.0,
+        "step": float(2 * (2 * (s1 + s2) + 2 * s2 + kern) + heun1 + heun2),
+    }
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -169,9 +198,15 @@ def run_gpu(args):
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     dev = torch.cuda.current_device()
-    w = inputs.workload(WORKLOAD, seed=rank)
+    wname = args.workload
+    spec = METHODS[wname]
+    w = inputs.workload(wname, seed=rank)
     nx, ny, nz = w["shape"]
     N = nx * ny * nz
+    if spec["method"] == "RKDP":
+        method, first_dt, dt_step, tol = B.MM_RKDP, 1e-13, 0.0, spec["tol"]
+    else:
+        method, first_dt, dt_step, tol = B.MM_HEUN, spec["dt"], spec["dt"], 0.0
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         s = B.Solver(w["shape"], w["cell"], pbc=w["pbc"], stream=stream.cuda_stream, **w["material"])
@@ -179,7 +214,7 @@ def run_gpu(args):
         ctx = s.ctx
         B.mm_load(ctx, m)
         # warm-up (also settles the step size)
-        B.mm_advance(ctx, B.MM_RKDP, args.warmup, dt_s=1e-13, tol=1e-6)
+        B.mm_advance(ctx, method, args.warmup, dt_s=first_dt, tol=tol)
         st0 = B.mm_get_stats(ctx)
         flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")    # > 129 MB L2
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -191,7 +226,7 @@ def run_gpu(args):
             for k in range(args.steps):
                 flush.fill_(k & 0xFF)                     # evict the previous step from L2
                 ev[k][0].record(stream)
-                B.mm_advance(ctx, B.MM_RKDP, 1, dt_s=0.0, tol=1e-6)
+                B.mm_advance(ctx, method, 1, dt_s=dt_step, tol=tol)
                 ev[k][1].record(stream)
             torch.cuda.synchronize()
             t_wall = time.perf_counter() - t_wall0
@@ -203,19 +238,19 @@ def run_gpu(args):
         assert st1["status"] == 0, st1
 
         # per-pass durations over a second timed region of the same steps
-        passes = B.pass_times(ctx, lambda: B.mm_advance(ctx, B.MM_RKDP, min(args.steps, 200), dt_s=0.0, tol=1e-6))
+        passes = B.pass_times(ctx, lambda: B.mm_advance(ctx, method, min(args.steps, 200), dt_s=dt_step, tol=tol))
 
         # end to end through the host-buffer entry point: H2D + step + D2H per step
         mh = torch.from_numpy(w["m"]).pin_memory()
         mh_np = mh.numpy()
-        B.mm_run_host(ctx, mh_np, B.MM_RKDP, 1, dt_s=1e-13, tol=1e-6)
+        B.mm_run_host(ctx, mh_np, method, 1, dt_s=first_dt, tol=tol)
         torch.cuda.synchronize()
         e0 = B.mm_get_stats(ctx)["evals"]
-        ke = max(3, args.steps // 2)
+        ke = max(3, min(args.steps // 2, 200))
         te = time.perf_counter()
         ev_total = 0
         for _ in range(ke):
-            B.mm_run_host(ctx, mh_np, B.MM_RKDP, 1, dt_s=0.0, tol=1e-6)
+            B.mm_run_host(ctx, mh_np, method, 1, dt_s=dt_step, tol=tol)
             ev_total += B.mm_get_stats(ctx)["evals"]
         te = time.perf_counter() - te
         del e0
@@ -235,7 +270,7 @@ def run_gpu(args):
         return None
 
     hbm, peak_kind = _peaks()
-    ab = algorithmic_bytes(nx, ny)
+    ab = algorithmic_bytes(nx, ny) if nz == 1 else algorithmic_bytes_3d(w["shape"], 2 * nz, tuple(bool(v) for v in w["pbc"]))
     # dominant pass = largest share of the step time
     dom = max((k for k in passes if k in ab), key=lambda k: passes[k]["ms_total"])
     dms = passes[dom]["ms_per_launch"]
@@ -245,8 +280,8 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": gpu_ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded vortex-plus-noise state, random applied field)",
-        "config": {"workload": WORKLOAD, "grid": [nx, ny, nz], "cell_nm": [4, 4, 2], "fft": [2 * nx, 2 * ny],
-                   "method": "RKDP adaptive, tol 1e-6", "evals_per_step": EVALS_PER_STEP,
+        "config": {"workload": wname, "grid": [nx, ny, nz], "cell_nm": [round(c * 1e9, 3) for c in w["cell"]],
+                   "pbc": list(w["pbc"]), "method": spec["desc"], "evals_per_step": spec["evals"],
                    "l2": "flushed between timed steps (256 MB write, outside the events)",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
@@ -257,10 +292,10 @@ def run_gpu(args):
         "passes": passes,
         "ns_simulated_per_hour": sim_t * 1e9 / (gpu_ms * 1e-3 / 3600.0) if gpu_ms > 0 else None,
         "clocks": clk.summary(),
-        "gpu_launches": int(args.steps * (2 * EVALS_PER_STEP + 1)),
+        "gpu_launches": int(sum(v["launches"] for v in passes.values()) / max(1, min(args.steps, 200)) * args.steps),
         "e2e": {"value": ev_total * N / te if te > 0 else None, "unit": UNIT,
                 "h2d_bytes_per_step": 12 * N, "d2h_bytes_per_step": 12 * N,
-                "note": "mm_run_host: pinned host m in, one RKDP step (7 evaluations: fresh k1 + 6), m out"},
+                "note": "mm_run_host: pinned host m in, one step (RKDP: 7 evaluations, fresh k1 + 6), m out"},
     }
     return line
 
@@ -324,6 +359,69 @@ def cpu_baseline_sample(seconds=20.0):
             "sample": f"{n} full-grid H_eff evaluations (FP64 numpy, one thread) of {WORKLOAD}"}
 
 
+def run_table1(args):
+    """Euler steps (one field evaluation + LL + update each) on the Table-1 grids."""
+    import numpy as np
+    import torch
+
+    from paper_1102_3069_gb300 import binding as B
+    from paper_1102_3069_gb300 import inputs
+
+    rows = []
+    sizes = [("N2", n) for n in (32, 64, 128, 256, 512, 1024, 2048)] + [("N3", n) for n in (8, 16, 32, 64, 128)]
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
+    for kind, n in sizes:
+        w = inputs.workload(f"table1_{kind}_{n}")
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            s = B.Solver(w["shape"], w["cell"], stream=stream.cuda_stream, **w["material"])
+            m = torch.from_numpy(w["m"]).cuda()
+            B.mm_load(s.ctx, m)
+            B.mm_advance(s.ctx, B.MM_EULER, 5, dt_s=1e-14)
+            k = 50
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+            for i in range(k):
+                flush.fill_(i & 0xFF)
+                ev[i][0].record(stream)
+                B.mm_advance(s.ctx, B.MM_EULER, 1, dt_s=1e-14)
+                ev[i][1].record(stream)
+            torch.cuda.synchronize()
+            ms = sorted(a.elapsed_time(b) for a, b in ev)[k // 2]
+        cells = int(np.prod(w["shape"]))
+        rows.append({"grid": f"{n}^{2 if kind == 'N2' else 3}", "cells": cells, "ms_per_euler_step": ms,
+                     "cell_evals_per_s": cells / (ms * 1e-3)})
+        s.close()
+        del s, m
+        torch.cuda.empty_cache()
+    return {"metric": "Euler step time (Table 1 grids)", "unit": "ms", "rows": rows,
+            "config": {"material": "Ms 8e5 A/m, A 1.3e-11 J/m, Ku 5e3 J/m^3 along x, Bz 10 mT, alpha 0.01",
+                       "cell_nm": 4, "timing": "median of 50 steps, CUDA events, L2 flushed between steps"}}
+
+
+def cpu_baseline_cube(seconds=20.0):
+    """Oracle on a 32^3 crop of the cube workload (its full periodic kernel is out of reach in numpy)."""
+    import numpy as np
+
+    from oracle import llg
+    from paper_1102_3069_gb300 import inputs
+
+    w = inputs.workload("cube_256x256x64", seed=0)
+    mat = w["material"]
+    shape = (32, 32, 32)
+    p = llg.Problem(shape, w["cell"], mat["Ms"], mat["Aex"], mat["alpha"], Ku=mat["Ku"], u=mat["easy_axis"],
+                    B=mat["B"], T=mat["temperature"], seed=mat["seed"], pbc=(True, True, False), images=2)
+    m = inputs.random_unit(shape, 0).astype(np.float64)
+    N = int(np.prod(shape))
+    n = 0
+    t = time.perf_counter()
+    while time.perf_counter() - t < seconds or n < 2:
+        p.rhs(m, step=n, dt=w["dt"])
+        n += 1
+    dt = time.perf_counter() - t
+    return {"value": n * N / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} H_eff evaluations of a 32^3 crop of cube_256x256x64 (2 images per periodic side)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -331,6 +429,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(METHODS))
+    ap.add_argument("--table1", action="store_true",
+                    help="Euler-step timing sweep of the paper's Table 1 grids (N^2 and N^3, 4 nm cells)")
     args = ap.parse_args()
     if args.impl == "reference":
         if args.steps > 5:
@@ -345,12 +446,15 @@ def main():
     from paper_1102_3069_gb300 import binding
     if not os.path.exists(binding.LIB_PATH):
         __graft_entry__.build()
+    if args.table1:
+        print(json.dumps(run_table1(args)))
+        return
     line = run_gpu(args)
     if line is None:
         return
     ws, _ = _dist()
     if ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_sample()
+        line["cpu_baseline"] = cpu_baseline_sample() if args.workload == WORKLOAD else cpu_baseline_cube()
     print(json.dumps(line))
 
 

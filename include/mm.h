@@ -100,6 +100,17 @@ int mm_set_material(mm_ctx* ctx, double Ms, double Aex, double Ku, const double 
                     const double B_applied_T[3]);
 
 /*
+ * Cubic magnetocrystalline anisotropy (Sec. 2.1.3, Eq. 5):
+ *   phi = K1 (a1^2 a2^2 + a2^2 a3^2 + a1^2 a3^2) + K2 a1^2 a2^2 a3^2  (J/m^3)
+ * with direction cosines a_i = m . c_i to the cubic axes c1, c2 and
+ * c3 = c1 x c2 (c1 is normalised and c2 made orthogonal to it here).  Adds
+ * H = -(1/(mu0 Ms)) dphi/dm to H_eff and phi to the energy.  K1 = K2 = 0
+ * (the default) switches it off; the axes may then be NULL.
+ * MM_EINVAL for non-finite constants or degenerate axes.
+ */
+int mm_set_cubic_anisotropy(mm_ctx* ctx, double K1, double K2, const double c1[3], const double c2[3]);
+
+/*
  * Enable (1) or disable (0) the magnetostatic term.  Enabled by default; when
  * enabled, mm_demag_kernel must have run before any evaluation.  Disabling it
  * leaves exchange, anisotropy, Zeeman and thermal terms (used for uncoupled

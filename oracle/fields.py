@@ -9,6 +9,11 @@ applied, anisotropy, thermal).
   periodic axes wrap.
 * uniaxial anisotropy (Sec. 2.1.3, Eq. 4, phi = Ku sin^2 theta):
   H_an = 2 Ku/(mu0 Ms) (m . u) u, Ku > 0 an easy axis u (unit vector).
+* cubic anisotropy (Sec. 2.1.3, Eq. 5): phi = K1 (a1^2 a2^2 + a2^2 a3^2 + a1^2 a3^2)
+  + K2 a1^2 a2^2 a3^2 with direction cosines a_i = m . c_i to the orthonormal
+  cubic axes c1, c2, c3 = c1 x c2; H_cub = -(1/(mu0 Ms)) dphi/dm
+  = -(2/(mu0 Ms)) sum_i a_i [K1 (a_j^2 + a_k^2) + K2 a_j^2 a_k^2] c_i.
+  phi is quartic, so its energy is summed directly (not as -mu0 Ms m.H/2).
 * Zeeman: H_z = B / mu0 for an applied flux density B in tesla.
 * thermal (Sec. 2.1.3, Eq. 6): H_th = eta sqrt(2 alpha kB T / (gamma0 mu0 Ms V dt)),
   eta ~ N(0,1) per cell, component and step (drawn by ``philox``).
@@ -59,6 +64,36 @@ def anisotropy_field(m, Ms, Ku, u):
         u = u.reshape(3, 1, 1, 1)
     mu = (m * u).sum(axis=0, keepdims=True)
     return (2.0 * Ku / (MU0 * Ms)) * mu * u
+
+
+def cubic_axes(c1, c2):
+    """Orthonormal cubic axes from two given directions (Gram-Schmidt; c3 = c1 x c2)."""
+    c1 = np.asarray(c1, float) / np.linalg.norm(c1)
+    c2 = np.asarray(c2, float)
+    c2 = c2 - c1 * (c1 @ c2)
+    c2 = c2 / np.linalg.norm(c2)
+    return c1, c2, np.cross(c1, c2)
+
+
+def cubic_energy_density(m, K1, K2, c1, c2):
+    """phi of Eq. 5 per cell (J/m^3); m shape (3, ...)."""
+    a = [np.tensordot(c, m, axes=(0, 0)) for c in cubic_axes(c1, c2)]
+    s = [x * x for x in a]
+    return K1 * (s[0] * s[1] + s[1] * s[2] + s[0] * s[2]) + K2 * s[0] * s[1] * s[2]
+
+
+def cubic_anisotropy_field(m, Ms, K1, K2, c1, c2):
+    """H_cub = -(1/(mu0 Ms)) dphi/dm (A/m)."""
+    m = np.asarray(m, float)
+    cs = cubic_axes(c1, c2)
+    a = [np.tensordot(c, m, axes=(0, 0)) for c in cs]
+    s = [x * x for x in a]
+    H = np.zeros_like(m)
+    for i in range(3):
+        j, k = (i + 1) % 3, (i + 2) % 3
+        dphi = 2.0 * a[i] * (K1 * (s[j] + s[k]) + K2 * s[j] * s[k])
+        H -= dphi[None] * cs[i].reshape((3,) + (1,) * (m.ndim - 1))
+    return H / (MU0 * Ms)
 
 
 def zeeman_field(m, B):

@@ -73,7 +73,8 @@ class Problem:
 
     def __init__(self, shape, cell, Ms, Aex, alpha, Ku=0.0, u=(1.0, 0.0, 0.0),
                  B=(0.0, 0.0, 0.0), T=0.0, seed=0, gamma0=F.GAMMA0,
-                 pbc=(False, False, False), images=10, demag=True, L=None):
+                 pbc=(False, False, False), images=10, demag=True, L=None,
+                 K1=0.0, K2=0.0, c1=(1.0, 0.0, 0.0), c2=(0.0, 1.0, 0.0)):
         self.shape = tuple(int(v) for v in shape)
         self.cell = tuple(float(v) for v in cell)
         self.V = self.cell[0] * self.cell[1] * self.cell[2]
@@ -85,6 +86,8 @@ class Problem:
         self.T, self.seed, self.gamma0 = float(T), int(seed), float(gamma0)
         self.pbc = tuple(bool(p) for p in pbc)
         self.demag = _demag.Demag(self.shape, self.cell, self.pbc, images, L) if demag else None
+        self.K1, self.K2 = float(K1), float(K2)
+        self.c1, self.c2 = np.asarray(c1, float), np.asarray(c2, float)
         self.n_evals = 0
 
     @property
@@ -100,6 +103,8 @@ class Problem:
             "d": self.demag.field(m, self.Ms) if self.demag is not None else zero,
             "ex": F.exchange_field(m, self.Ms, self.Aex, self.cell, self.pbc),
             "an": F.anisotropy_field(m, self.Ms, self.Ku, self.u) if self.Ku != 0.0 else zero,
+            "cub": (F.cubic_anisotropy_field(m, self.Ms, self.K1, self.K2, self.c1, self.c2)
+                    if (self.K1 != 0.0 or self.K2 != 0.0) else zero),
             "z": F.zeeman_field(m, self.B),
             "th": zero,
         }
@@ -113,14 +118,17 @@ class Problem:
     def heff(self, m, step=0, dt=None):
         t = self.terms(m, step, dt)
         self.n_evals += 1
-        return t["d"] + t["ex"] + t["an"] + t["z"] + t["th"]
+        return t["d"] + t["ex"] + t["an"] + t["cub"] + t["z"] + t["th"]
 
     def rhs(self, m, step=0, dt=None):
         return ll_rhs(m, self.heff(m, step, dt), self.alpha, self.gamma0)
 
     def energy(self, m):
         t = self.terms(m)
-        return F.energy(m, self.Ms, self.V, t["d"], t["ex"], t["an"], t["z"])
+        e = F.energy(m, self.Ms, self.V, t["d"], t["ex"], t["an"], t["z"])
+        if self.K1 != 0.0 or self.K2 != 0.0:
+            e += self.V * F.cubic_energy_density(np.asarray(m, float), self.K1, self.K2, self.c1, self.c2).sum()
+        return e
 
     def torque(self, m):
         return F.torque_max(m, self.heff(m), self.Ms)

@@ -49,6 +49,7 @@ _SIGS = {
     "mm_set_workspace": (_i, [_vp, _vp, _sz]),
     "mm_set_material": (_i, [_vp, _d, _d, _d, _dp, _d, _d, _d, _u64, _dp]),
     "mm_set_demag": (_i, [_vp, _i]),
+    "mm_set_cubic_anisotropy": (_i, [_vp, _d, _d, _dp, _dp]),
     "mm_demag_kernel": (_i, [_vp, _dp]),
     "mm_demag_tensor_len": (_sz, [_vp]),
     "mm_eval_heff": (_i, [_vp, _vp, _vp, _vp, _dp]),
@@ -141,6 +142,12 @@ def mm_set_material(ctx, Ms, Aex, Ku=0.0, easy_axis=(1.0, 0.0, 0.0), alpha=0.02,
     b, _keep_b = _d3(B)
     return _check(ctx, lib().mm_set_material(ctx, float(Ms), float(Aex), float(Ku), u, float(alpha), float(gamma0),
                                              float(temperature), int(seed) & 0xFFFFFFFFFFFFFFFF, b))
+
+
+def mm_set_cubic_anisotropy(ctx, K1, K2, c1=(1.0, 0.0, 0.0), c2=(0.0, 1.0, 0.0)):
+    a, _ka = _d3(c1)
+    b, _kb = _d3(c2)
+    return _check(ctx, lib().mm_set_cubic_anisotropy(ctx, float(K1), float(K2), a, b))
 
 
 def mm_set_demag(ctx, enabled):

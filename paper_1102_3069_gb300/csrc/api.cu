@@ -63,6 +63,7 @@ struct mm_ctx {
     double Ms = 0, Aex = 0, Ku = 0, u[3] = {1, 0, 0}, alpha = 0, gamma0 = DEFAULT_GAMMA0, T = 0;
     uint64_t seed = 0;
     double B[3] = {0, 0, 0};
+    double K1 = 0, K2 = 0, cub[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
     bool demag = true;
     bool kernel_ready = false;
     // workspace
@@ -172,6 +173,10 @@ mm::HotParams hot_params(mm_ctx* c, double dt_internal, bool thermal) {
     p.hzx = (float)(c->B[0] / (MU0 * Ms));
     p.hzy = (float)(c->B[1] / (MU0 * Ms));
     p.hzz = (float)(c->B[2] / (MU0 * Ms));
+    p.kc1 = (float)(2.0 * c->K1 / (MU0 * Ms * Ms));
+    p.kc2 = (float)(2.0 * c->K2 / (MU0 * Ms * Ms));
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) p.c[i][j] = (float)c->cub[i][j];
     p.alpha = (float)c->alpha;
     p.llpref = (float)(1.0 / (1.0 + c->alpha * c->alpha));
     p.seed = c->seed;
@@ -411,6 +416,33 @@ int mm_set_material(mm_ctx* ctx, double Ms, double Aex, double Ku, const double 
     for (int i = 0; i < 3; ++i) { ctx->u[i] = u[i]; ctx->B[i] = B[i]; }
     ctx->have_material = true;
     if (ms_changed) ctx->state_loaded = false;     // internal time unit changed
+    ctx->k1_valid = false;
+    ctx->param_version++;
+    return MM_OK;
+}
+
+int mm_set_cubic_anisotropy(mm_ctx* ctx, double K1, double K2, const double c1[3], const double c2[3]) {
+    if (!ctx) return MM_EINVAL;
+    if (!std::isfinite(K1) || !std::isfinite(K2)) return fail(ctx, MM_EINVAL, "K1, K2 must be finite");
+    double a[3] = {1, 0, 0}, b[3] = {0, 1, 0};
+    if (K1 != 0.0 || K2 != 0.0) {
+        if (!c1 || !c2) return fail(ctx, MM_EINVAL, "cubic axes needed when K1 or K2 != 0");
+        for (int i = 0; i < 3; ++i) { a[i] = c1[i]; b[i] = c2[i]; }
+    }
+    // Gram-Schmidt: c1 normalised, c2 made orthogonal to it, c3 = c1 x c2
+    const double na = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    if (!(na > 0) || !std::isfinite(na)) return fail(ctx, MM_EINVAL, "cubic axis c1 must be a non-zero vector");
+    for (int i = 0; i < 3; ++i) a[i] /= na;
+    const double d = a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+    for (int i = 0; i < 3; ++i) b[i] -= d * a[i];
+    const double nb = std::sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+    if (!(nb > 1e-12 * (1.0 + std::fabs(d))) || !std::isfinite(nb))
+        return fail(ctx, MM_EINVAL, "cubic axis c2 must not be parallel to c1");
+    for (int i = 0; i < 3; ++i) b[i] /= nb;
+    const double c3[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+    for (int i = 0; i < 3; ++i) { ctx->cub[0][i] = a[i]; ctx->cub[1][i] = b[i]; ctx->cub[2][i] = c3[i]; }
+    ctx->K1 = K1;
+    ctx->K2 = K2;
     ctx->k1_valid = false;
     ctx->param_version++;
     return MM_OK;

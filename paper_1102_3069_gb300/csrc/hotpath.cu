@@ -551,7 +551,20 @@ __device__ __forceinline__ f3 cell_update(const HotParams& p, const LaunchArgs& 
     if (usey) hex = hex + p.cex[1] * ((myp - m) + (mym - m));
     if (usez) hex = hex + p.cex[2] * ((mzp - m) + (mzm - m));
     const f3 u = mk(p.ux, p.uy, p.uz);
-    const f3 han = (p.kan * dot(m, u)) * u;
+    f3 han = (p.kan * dot(m, u)) * u;
+    float ecub = 0.f;
+    if (p.kc1 != 0.f || p.kc2 != 0.f) {
+        // cubic anisotropy (Eq. 5): h = -sum_i a_i [kc1 (a_j^2 + a_k^2) + kc2 a_j^2 a_k^2] c_i
+        const f3 c1 = mk(p.c[0][0], p.c[0][1], p.c[0][2]);
+        const f3 c2 = mk(p.c[1][0], p.c[1][1], p.c[1][2]);
+        const f3 c3 = mk(p.c[2][0], p.c[2][1], p.c[2][2]);
+        const float a1 = dot(m, c1), a2 = dot(m, c2), a3 = dot(m, c3);
+        const float s1 = a1 * a1, s2 = a2 * a2, s3 = a3 * a3;
+        han = han - ((a1 * (p.kc1 * (s2 + s3) + p.kc2 * s2 * s3)) * c1 +
+                     (a2 * (p.kc1 * (s1 + s3) + p.kc2 * s1 * s3)) * c2 +
+                     (a3 * (p.kc1 * (s1 + s2) + p.kc2 * s1 * s2)) * c3);
+        ecub = 0.5f * (p.kc1 * (s1 * s2 + s2 * s3 + s1 * s3) + p.kc2 * s1 * s2 * s3);   // phi/(mu0 Ms^2)
+    }
     const f3 hz = mk(p.hzx, p.hzy, p.hzz);
     f3 h = hd + hex + han + hz;
     if (p.sigma_th > 0.f) h = h + p.sigma_th * gauss3(cell, tstep, p.seed);
@@ -565,7 +578,11 @@ __device__ __forceinline__ f3 cell_update(const HotParams& p, const LaunchArgs& 
             if (p.h_out) st3(p.h_out, cell, n, p.h_scale * h);
             if (p.tq_out) st3(p.tq_out, cell, n, p.t_scale * k);
             pt.torque = fmaxf(pt.torque, tq);
-            if (p.want_energy) pt.energy -= 0.5 * (double)dot(m, hd + hex + han) + (double)dot(m, hz);
+            if (p.want_energy) {
+                // quadratic terms as -m.H/2; the quartic cubic term by its density
+                const f3 hquad = hd + hex + (p.kan * dot(m, u)) * u;
+                pt.energy += -0.5 * (double)dot(m, hquad) - (double)dot(m, hz) + (double)ecub;
+            }
             pt.bad |= !finite3(h);
             break;
         }

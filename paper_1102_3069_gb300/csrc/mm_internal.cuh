@@ -77,6 +77,8 @@ struct HotParams {
     float kan;               // 2Ku/(mu0 Ms^2)
     float ux, uy, uz;        // easy axis
     float hzx, hzy, hzz;     // B/(mu0 Ms)
+    float kc1, kc2;          // cubic anisotropy 2K1/(mu0 Ms^2), 2K2/(mu0 Ms^2) (0: off)
+    float c[3][3];           // orthonormal cubic axes c1, c2, c3
     float alpha;
     float llpref;            // 1/(1+alpha^2)
     float sigma_th;          // thermal sigma / Ms for the current dt (0: off)

@@ -105,3 +105,23 @@ def test_nonfinite_input_is_reported():
     # the context stays usable
     m[0, 0, 2, 3] = 1.0
     s.heff(to_dev(m), energy=True)
+
+
+@pytest.mark.parametrize("shape", [(33, 7, 1), (16, 12, 3)])
+def test_cubic_anisotropy_matches_oracle(shape):
+    from paper_1102_3069_gb300 import binding as B
+    cell = (4e-9, 3e-9, 2e-9)
+    K1, K2, c1, c2 = 4.8e4, -1.5e4, (1.0, 1.0, 0.0), (-1.0, 1.0, 0.5)
+    m = inputs.random_unit(shape, 4)
+    s = solver(shape, cell, **MAT)
+    B.mm_set_cubic_anisotropy(s.ctx, K1, K2, c1, c2)
+    h, tq, e = s.heff(to_dev(m), torque=True, energy=True)
+    p = llg.Problem(shape, cell, MAT["Ms"], MAT["Aex"], MAT["alpha"], Ku=MAT["Ku"], u=MAT["easy_axis"], B=MAT["B"],
+                    K1=K1, K2=K2, c1=c1, c2=c2)
+    m64 = m.astype(np.float64)
+    H = p.heff(m64)
+    assert rel_l2(to_np(h), H) <= HEFF_REL_L2
+    assert rel_l2(to_np(tq), llg.ll_rhs(m64, H, p.alpha)) <= 2 * HEFF_REL_L2
+    assert e == pytest.approx(p.energy(m64), rel=1e-6)
+    with pytest.raises(B.MMError):
+        B.mm_set_cubic_anisotropy(s.ctx, K1, K2, c1, c1)      # parallel axes

@@ -155,3 +155,51 @@ def test_thermal_sigma_units():
     # sigma^2 * gamma0 mu0 Ms V dt = 2 alpha kB T  (Eq. 6)
     s = F.thermal_sigma(0.05, 300.0, 1.1e6, 27e-27, 50e-15)
     assert s * s * F.GAMMA0 * F.MU0 * 1.1e6 * 27e-27 * 50e-15 == pytest.approx(2 * 0.05 * F.KB * 300.0, rel=1e-12)
+
+
+def test_cubic_anisotropy_is_minus_energy_gradient():
+    rng = np.random.default_rng(9)
+    m = rng.standard_normal((3, 1, 2, 3))
+    K1, K2 = 4.5e4, -2.1e4
+    c1, c2 = (1.0, 1.0, 0.0), (0.0, 0.3, 1.0)
+    H = F.cubic_anisotropy_field(m, MS, K1, K2, c1, c2)
+    eps = 1e-6
+    for comp in range(3):
+        d = np.zeros_like(m)
+        d[comp] = eps
+        g = (F.cubic_energy_density(m + d, K1, K2, c1, c2) - F.cubic_energy_density(m - d, K1, K2, c1, c2)) / (2 * eps)
+        np.testing.assert_allclose(H[comp], -g / (F.MU0 * MS), rtol=1e-7, atol=1e-3)
+
+
+def test_cubic_anisotropy_special_directions():
+    K1, K2 = 4.8e4, 1.2e4
+    c1, c2, c3 = F.cubic_axes((1.0, 0.0, 0.0), (0.0, 1.0, 0.0))
+    m_axis = np.array([1.0, 0, 0]).reshape(3, 1, 1, 1)
+    m_111 = (np.ones(3) / np.sqrt(3)).reshape(3, 1, 1, 1)
+    m_110 = (np.array([1.0, 1.0, 0.0]) / np.sqrt(2)).reshape(3, 1, 1, 1)
+    assert F.cubic_energy_density(m_axis, K1, K2, c1, c2).item() == pytest.approx(0.0, abs=1e-9)
+    assert F.cubic_energy_density(m_111, K1, K2, c1, c2).item() == pytest.approx(K1 / 3 + K2 / 27, rel=1e-12)
+    assert F.cubic_energy_density(m_110, K1, K2, c1, c2).item() == pytest.approx(K1 / 4, rel=1e-12)
+    # along a cube axis, [110] and [111] the field is parallel to m (no torque)
+    for mm in (m_axis, m_111, m_110):
+        H = F.cubic_anisotropy_field(mm, MS, K1, K2, c1, c2)
+        assert np.allclose(np.cross(mm, H, axis=0), 0.0, atol=1e-9)
+    # the axes are orthonormal and right-handed
+    assert np.allclose(np.array([c1, c2, c3]) @ np.array([c1, c2, c3]).T, np.eye(3))
+    assert np.allclose(np.cross(c1, c2), c3)
+
+
+def test_cubic_energy_decreases_under_damping():
+    from oracle import llg
+    shape = (6, 4, 1)
+    rng = np.random.default_rng(3)
+    m = rng.standard_normal((3, 1, 4, 6))
+    m /= np.linalg.norm(m, axis=0)
+    p = llg.Problem(shape, (4e-9, 4e-9, 4e-9), 8e5, 1.3e-11, 0.5, K1=5e4, K2=1e4, c1=(1, 1, 0), c2=(-1, 1, 0))
+    st = llg.Stepper(p, m, h0=1e-14, tol=1e-7)
+    E = [p.energy(st.m)]
+    for _ in range(30):
+        if st.step():
+            E.append(p.energy(st.m))
+    assert np.all(np.diff(E) <= 1e-7 * abs(E[0]))
+    assert E[-1] < E[0]
