@@ -47,8 +47,10 @@ typedef enum {
     MM_ESTATE = -7           /* operation needs state that is not there yet         */
 } mm_status;
 
-/* Time integrators of Sec. 2.2 (values are the Runge-Kutta order names). */
-enum { MM_EULER = 1, MM_HEUN = 2, MM_RKDP = 5 };
+/* Time integrators of Sec. 2.2: RK1 Euler, RK2 Heun, RK3 Kutta, RK4 classical
+ * (fixed dt); RK12 Heun-Euler, RK23 Bogacki-Shampine, RKCK Cash-Karp and RKDP
+ * Dormand-Prince (adaptive step, error bound tol per step). */
+enum { MM_EULER = 1, MM_HEUN = 2, MM_RK3 = 3, MM_RK4 = 4, MM_RKDP = 5, MM_RKCK = 6, MM_RK12 = 12, MM_RK23 = 23 };
 
 typedef struct mm_stats {
     long long evals;        /* H_eff evaluations issued since the last mm_load      */
@@ -165,12 +167,14 @@ int mm_store(mm_ctx* ctx, float* m);
 
 /*
  * Enqueue nsteps time steps on the stream without waiting (device-side step
- * control, Sec. 2.2).  method = MM_EULER or MM_HEUN with the fixed step
- * dt_s > 0; or MM_RKDP (Dormand-Prince 5(4), adaptive, first same as last)
- * with per-step error bound tol (max over cells of |dm|) and the proposed
- * step dt_s (> 0 sets it; <= 0 keeps the current one, 100 fs after mm_load).
- * tol < 0 selects fixed Dormand-Prince steps of dt_s (no step control; the
- * error estimate is still computed and reported).  t_end_s > 0 stops the
+ * control, Sec. 2.2).  Fixed-step methods (MM_EULER, MM_HEUN, MM_RK3, MM_RK4)
+ * take dt_s > 0.  Adaptive methods (MM_RK12, MM_RK23, MM_RKCK, MM_RKDP) take
+ * the per-step error bound tol (max over cells of |dm|) and the proposed step
+ * dt_s (> 0 sets it; <= 0 keeps the current one, 100 fs after mm_load); the
+ * step factor is 0.9 (tol/err)^(1/q), q = 2, 3, 5, 5 respectively, clamped to
+ * [0.2, 5].  tol < 0 selects fixed steps of dt_s for an adaptive method (the
+ * error estimate is still computed and reported).  The thermal field (T > 0)
+ * needs a fixed-step method.  t_end_s > 0 stops the
  * run exactly at t_end_s (the last step is shortened); torque_tol > 0 stops
  * it once max |m x H|/Ms < torque_tol (relaxation).  Once stopped, queued
  * steps do no work.  The thermal field (T > 0) needs MM_EULER or MM_HEUN.

@@ -255,3 +255,123 @@ def relax(p, m, torque_tol=1e-4, h0=1e-13, tol=1e-6, max_steps=100000):
 def ll_heff_from_k1(p, m):
     """H_eff at m (the FSAL evaluation re-done explicitly, for the torque)."""
     return p.heff(m)
+
+
+# ---------------------------------------------------------------------------
+# The rest of the Runge-Kutta family of Sec. 2.2, as explicit tableaus.
+# Coefficients from the published schemes: Kutta's third-order method, the
+# classical fourth-order method, Heun-Euler (2nd order with an embedded Euler
+# step), Bogacki & Shampine (1989) 3(2) with first-same-as-last, Cash & Karp
+# (1990) 5(4).  For an embedded pair the step-size factor uses the exponent
+# 1/q, q = order of the error estimate's leading term in h.
+
+class Tableau:
+    def __init__(self, name, a, b, bstar=None, fsal=False, q=None):
+        self.name, self.a, self.b, self.bstar, self.fsal, self.q = name, a, b, bstar, fsal, q
+
+    @property
+    def stages(self):
+        return len(self.b)
+
+    @property
+    def adaptive(self):
+        return self.bstar is not None
+
+
+TABLEAUS = {
+    "rk3": Tableau("rk3", ((), (1 / 2,), (-1.0, 2.0)), (1 / 6, 2 / 3, 1 / 6)),
+    "rk4": Tableau("rk4", ((), (1 / 2,), (0.0, 1 / 2), (0.0, 0.0, 1.0)), (1 / 6, 1 / 3, 1 / 3, 1 / 6)),
+    "rk12": Tableau("rk12", ((), (1.0,)), (1 / 2, 1 / 2), bstar=(1.0, 0.0), q=2),
+    "rk23": Tableau("rk23", ((), (1 / 2,), (0.0, 3 / 4), (2 / 9, 1 / 3, 4 / 9)), (2 / 9, 1 / 3, 4 / 9, 0.0),
+                    bstar=(7 / 24, 1 / 4, 1 / 3, 1 / 8), fsal=True, q=3),
+    "rkck": Tableau("rkck", ((), (1 / 5,), (3 / 40, 9 / 40), (3 / 10, -9 / 10, 6 / 5),
+                             (-11 / 54, 5 / 2, -70 / 27, 35 / 27),
+                             (1631 / 55296, 175 / 512, 575 / 13824, 44275 / 110592, 253 / 4096)),
+                    (37 / 378, 0.0, 250 / 621, 125 / 594, 0.0, 512 / 1771),
+                    bstar=(2825 / 27648, 0.0, 18575 / 48384, 13525 / 55296, 277 / 14336, 1 / 4), q=5),
+    "rkdp": Tableau("rkdp", DP_A, DP_B, bstar=DP_BSTAR, fsal=True, q=5),
+}
+
+
+def rk_attempt(p, m, h, tab, k1=None, step=0, dt=None):
+    """One attempt of an explicit tableau.
+
+    Stage s input: m + h sum_j a_sj k_j (not renormalised); the result
+    m + h sum_j b_j k_j is renormalised.  With first-same-as-last the last
+    stage is evaluated at that renormalised result.  Returns (m_next, k, err),
+    err = max_i |h sum_j (b_j - b*_j) k_j,i| (0 without an embedded pair).
+    One thermal draw per step is shared by all stages (dt = the step).
+    """
+    if p.T > 0.0 and tab.adaptive:
+        raise ValueError("thermal field with an adaptive method is not supported")
+    k = [p.rhs(m, step, dt) if k1 is None else k1]
+    S = tab.stages
+    for s in range(1, S):
+        ms = m.copy()
+        for j, a in enumerate(tab.a[s]):
+            if a != 0.0:
+                ms = ms + h * a * k[j]
+        if tab.fsal and s == S - 1:
+            ms = normalize(ms)
+        k.append(p.rhs(ms, step, dt))
+    if tab.fsal:
+        mn = ms
+    else:
+        mn = m.copy()
+        for j in range(S):
+            if tab.b[j] != 0.0:
+                mn = mn + h * tab.b[j] * k[j]
+        mn = normalize(mn)
+    err = 0.0
+    if tab.adaptive:
+        e = np.zeros_like(m)
+        for j in range(S):
+            d = tab.b[j] - tab.bstar[j]
+            if d != 0.0:
+                e = e + h * d * k[j]
+        err = float(np.sqrt((e * e).sum(axis=0)).max())
+    return mn, k, err
+
+
+def rk_fixed(p, m, h, nsteps, tab):
+    """nsteps fixed steps of a tableau (first-same-as-last reuse when it has it)."""
+    k1 = None
+    for n in range(nsteps):
+        m, k, _ = rk_attempt(p, m, h, tab, k1, step=n, dt=h)
+        k1 = k[-1] if tab.fsal else None
+    return m
+
+
+class TableauStepper(Stepper):
+    """Adaptive stepping of an embedded tableau with the same controller as
+    Stepper but the step-size exponent 1/q of that tableau."""
+
+    def __init__(self, p, m, tab, h0=1e-13, tol=1e-6, t=0.0):
+        super().__init__(p, m, h0, tol, t)
+        self.tab = tab
+
+    def _factor(self, err, after_reject):
+        f = 5.0 if err == 0.0 else 0.9 * (self.tol / err) ** (1.0 / self.tab.q)
+        f = min(max(f, 0.2), 5.0)
+        return min(f, 1.0) if after_reject else f
+
+    def step(self):
+        mn, k, err = rk_attempt(self.p, self.m, self.h, self.tab, self.k1 if self.tab.fsal else None)
+        if err <= self.tol:
+            self.t += self.h
+            self.m = mn
+            self.k1 = k[-1] if self.tab.fsal else None
+            self.accepted += 1
+            self.h *= self._factor(err, self.after_reject)
+            self.after_reject = False
+            ok = True
+        else:
+            if self.tab.fsal and self.k1 is None:
+                self.k1 = k[0]
+            self.rejected += 1
+            self.after_reject = True
+            self.h *= self._factor(err, True)
+            ok = False
+        if self.h < H_MIN:
+            raise NotConverged("step size underflow")
+        return ok

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libmm.so")
 
 MM_OK, MM_EINVAL, MM_ENOMEM, MM_ECUDA = 0, -1, -2, -3
 MM_ENOTCONVERGED, MM_ENONFINITE, MM_ETIMEOUT, MM_ESTATE = -4, -5, -6, -7
-MM_EULER, MM_HEUN, MM_RKDP = 1, 2, 5
+MM_EULER, MM_HEUN, MM_RK3, MM_RK4, MM_RKDP, MM_RKCK, MM_RK12, MM_RK23 = 1, 2, 3, 4, 5, 6, 12, 23
 
 STATUS_NAMES = {0: "MM_OK", -1: "MM_EINVAL", -2: "MM_ENOMEM", -3: "MM_ECUDA", -4: "MM_ENOTCONVERGED",
                 -5: "MM_ENONFINITE", -6: "MM_ETIMEOUT", -7: "MM_ESTATE"}

@@ -19,6 +19,20 @@ constexpr double KB = 1.380649e-23;
 constexpr double DEFAULT_GAMMA0 = 2.211e5;
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+// Runge-Kutta methods of the C ABI -> tableau index, stages, first-same-as-last, adaptive
+struct RkInfo { int index, stages, fsal, adaptive; };
+bool rk_info(int method, RkInfo* r) {
+    switch (method) {
+        case MM_RKDP: *r = {0, 7, 1, 1}; return true;
+        case MM_RK23: *r = {1, 4, 1, 1}; return true;
+        case MM_RKCK: *r = {2, 6, 0, 1}; return true;
+        case MM_RK4:  *r = {3, 4, 0, 0}; return true;
+        case MM_RK3:  *r = {4, 3, 0, 0}; return true;
+        case MM_RK12: *r = {5, 2, 0, 1}; return true;
+        default: return false;
+    }
+}
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 int ilog2(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
 int next_pow2(int v) { int p = 1; while (p < v) p <<= 1; return p; }
@@ -248,13 +262,23 @@ namespace {
 // right after a load nothing is (Euler/Heun).
 int enqueue_step(mm_ctx* ctx, const mm::HotParams& p, int method, bool first) {
     int rc;
-    if (method == MM_RKDP) {
-        if ((rc = eval(ctx, p, mm::SRC_COMBINE2, mm::LM_RK, 2, true, first))) return rc;
-        if ((rc = eval(ctx, p, mm::SRC_STAGE1, mm::LM_RK, 3, true, true))) return rc;
-        if ((rc = eval(ctx, p, mm::SRC_STAGE0, mm::LM_RK, 4, true, true))) return rc;
-        if ((rc = eval(ctx, p, mm::SRC_STAGE1, mm::LM_RK, 5, true, true))) return rc;
-        if ((rc = eval(ctx, p, mm::SRC_STAGE0, mm::LM_RK, 6, true, true))) return rc;
-        return eval(ctx, p, mm::SRC_NEXT, mm::LM_RKFINAL, 7, false, true);
+    RkInfo r;
+    if (rk_info(method, &r)) {
+        const int S = r.stages;
+        // stage s reads its input from mstage[s & 1]; with first same as last
+        // the last stage reads the candidate m_{n+1} (slot ms[1-cur])
+        auto src_of = [&](int st) { return (st & 1) ? mm::SRC_STAGE1 : mm::SRC_STAGE0; };
+        if (r.fsal) {
+            if ((rc = eval(ctx, p, mm::SRC_COMBINE2, mm::LM_RK, 2, true, first))) return rc;
+            for (int st = 3; st < S; ++st)
+                if ((rc = eval(ctx, p, src_of(st), mm::LM_RK, st, true, true))) return rc;
+            return eval(ctx, p, mm::SRC_NEXT, mm::LM_RKFINAL, S, false, true);
+        }
+        // without first same as last: k1 = f(m_n) each step (the pass also forms m_2)
+        if ((rc = eval(ctx, p, mm::SRC_CUR, mm::LM_K1, 1, true, first))) return rc;
+        for (int st = 2; st < S; ++st)
+            if ((rc = eval(ctx, p, src_of(st), mm::LM_RK, st, true, true))) return rc;
+        return eval(ctx, p, src_of(S), mm::LM_RKFINAL, S, false, true);
     }
     if (method == MM_EULER) return eval(ctx, p, mm::SRC_CUR, mm::LM_EULER, 0, true, !first);
     if ((rc = eval(ctx, p, mm::SRC_CUR, mm::LM_HEUN1, 0, true, !first))) return rc;
@@ -581,28 +605,33 @@ int mm_advance(mm_ctx* ctx, int method, long nsteps, double dt_s, double tol, do
     if (!std::isfinite(dt_s) || !std::isfinite(tol) || !std::isfinite(t_end_s) || !std::isfinite(torque_tol))
         return fail(ctx, MM_EINVAL, "non-finite argument");
     const double tu = ctx->gamma0 * ctx->Ms;
-    if (method == MM_EULER || method == MM_HEUN) {
+    RkInfo rk = {0, 7, 1, 1};
+    const bool is_rk = rk_info(method, &rk);
+    if (method == MM_EULER || method == MM_HEUN || (is_rk && !rk.adaptive)) {
         if (!(dt_s > 0)) return fail(ctx, MM_EINVAL, "fixed-step methods need dt > 0");
-    } else if (method == MM_RKDP) {
-        if (ctx->T > 0.0) return fail(ctx, MM_EINVAL, "thermal field needs MM_EULER or MM_HEUN (fixed dt)");
-        if (tol == 0.0) return fail(ctx, MM_EINVAL, "RKDP needs tol > 0 (or < 0 for fixed steps)");
-        if (tol < 0.0 && !(dt_s > 0)) return fail(ctx, MM_EINVAL, "fixed-step RKDP (tol < 0) needs dt > 0");
+    } else if (is_rk) {
+        if (ctx->T > 0.0) return fail(ctx, MM_EINVAL, "thermal field needs a fixed-step method (fixed dt)");
+        if (tol == 0.0) return fail(ctx, MM_EINVAL, "adaptive methods need tol > 0 (or < 0 for fixed steps)");
+        if (tol < 0.0 && !(dt_s > 0)) return fail(ctx, MM_EINVAL, "fixed steps (tol < 0) need dt > 0");
     } else {
         return fail(ctx, MM_EINVAL, "unknown method");
     }
     double dt = dt_s * tu;
-    if (method == MM_RKDP) {
+    if (is_rk && rk.adaptive) {
         if (dt > 0) ctx->rk_h_set = true;
         else if (!ctx->rk_h_set) { dt = 1e-13 * tu; ctx->rk_h_set = true; }   // default first step 100 fs
     }
     ctx->last_method = method;
     mm::HotParams p = hot_params(ctx, dt, true);
-    k_set_run<<<1, 1, 0, ctx->stream>>>(dstate(ctx), tol, t_end_s > 0 ? t_end_s * tu : 0.0,
+    p.rk = rk.index;
+    p.rk_stages = rk.stages;
+    p.rk_fsal = rk.fsal;
+    const bool fixed_steps = is_rk && (!rk.adaptive || tol < 0.0);
+    k_set_run<<<1, 1, 0, ctx->stream>>>(dstate(ctx), fixed_steps ? 1.0 : tol, t_end_s > 0 ? t_end_s * tu : 0.0,
                                         torque_tol > 0 ? torque_tol : 0.0,
-                                        method == MM_RKDP ? (dt > 0 ? dt : 0.0) : 0.0, 1e-20 * tu, 1,
-                                        method == MM_RKDP && tol < 0.0 ? 1 : 0);
+                                        is_rk ? (dt > 0 ? dt : 0.0) : 0.0, 1e-20 * tu, 1, fixed_steps ? 1 : 0);
     CK(cudaGetLastError());
-    if (method == MM_RKDP) {
+    if (is_rk && rk.fsal) {
         if (dt > 0 && ctx->spec == mm_ctx::SPEC_M2) ctx->spec = mm_ctx::SPEC_NONE;   // m_2 depends on h
         if (!ctx->k1_valid) {
             // k1 = f(m_n); the same pass forms m_2 and its x spectrum
@@ -617,7 +646,13 @@ int mm_advance(mm_ctx* ctx, int method, long nsteps, double dt_s, double tol, do
     long s = 0;
     // a first step that can reuse a spectrum already in place differs from
     // the standard step: launch it directly
-    const bool first_special = method == MM_RKDP ? ctx->spec == mm_ctx::SPEC_M2 : ctx->spec != mm_ctx::SPEC_MCUR;
+    // FSAL tableaus: right after k1 the stage-2 input and its spectrum are in place;
+    // others: the first step finds the spectrum of m_n in place only if a previous
+    // Euler/Heun run left it (their standard step needs it, the tableaus' does not)
+    bool first_special;
+    if (is_rk && rk.fsal) first_special = ctx->spec == mm_ctx::SPEC_M2;
+    else if (is_rk) first_special = ctx->spec == mm_ctx::SPEC_MCUR;
+    else first_special = ctx->spec != mm_ctx::SPEC_MCUR;
     if (nsteps > 0 && first_special) {
         if ((rc = enqueue_step(ctx, p, method, true))) return rc;
         ++s;
@@ -627,7 +662,7 @@ int mm_advance(mm_ctx* ctx, int method, long nsteps, double dt_s, double tol, do
         bool graphed = false;
         if (ctx->stream != nullptr && !ctx->profiling) {
             if (!ctx->step_graph || ctx->graph_method != method || ctx->graph_version != ctx->param_version ||
-                (method != MM_RKDP && ctx->graph_dt != dt)) {
+                ctx->graph_dt != dt) {
                 if (ctx->step_graph) { cudaGraphExecDestroy(ctx->step_graph); ctx->step_graph = nullptr; }
                 cudaGraph_t g = nullptr;
                 if (cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
@@ -655,7 +690,8 @@ int mm_advance(mm_ctx* ctx, int method, long nsteps, double dt_s, double tol, do
             }
         }
     }
-    if (nsteps > 0) ctx->spec = method == MM_RKDP ? mm_ctx::SPEC_NONE : mm_ctx::SPEC_MCUR;
+    if (nsteps > 0) ctx->spec = is_rk ? mm_ctx::SPEC_NONE : mm_ctx::SPEC_MCUR;
+    if (is_rk && !rk.fsal) ctx->k1_valid = false;
     return MM_OK;
 }
 
@@ -673,7 +709,8 @@ int mm_get_stats(mm_ctx* ctx, mm_stats* stats) {
         stats->rejected = h.rejected;
         stats->step_index = h.step_index;
         stats->t = h.t / tu;
-        stats->dt = (ctx->last_method == MM_RKDP ? h.h : ctx->last_fixed_dt) / tu;
+        RkInfo ri;
+        stats->dt = ((rk_info(ctx->last_method, &ri) && ri.adaptive) ? h.h : ctx->last_fixed_dt) / tu;
         stats->last_err = h.last_err;
         stats->max_torque = h.max_torque;
         const double V = ctx->dx * ctx->dy * ctx->dz;

@@ -31,28 +31,47 @@ namespace mm {
 using namespace mmfft;
 namespace r8 = mmfft::r8;
 
-// Dormand-Prince 5(4) tableau (Dormand & Prince 1980), double precision.
-// c_dpa[s][j]: weight of k_j in the input of stage s (s = 2..7, j = 1..6);
-// row 7 is the 5th-order solution b.  c_dpe[j] = b_j - b*_j.
-__constant__ double c_dpa[8][8] = {
+// Explicit Runge-Kutta tableaus of Sec. 2.2, double precision, by method
+// index: 0 Dormand-Prince 5(4) (Dormand & Prince 1980, first same as last),
+// 1 Bogacki-Shampine 3(2) (1989, first same as last), 2 Cash-Karp 5(4) (1990),
+// 3 classical RK4, 4 Kutta's RK3, 5 Heun-Euler 2(1).
+// c_rka[r][s][j]: weight of k_j in the input of stage s (1-based); with first
+// same as last the last stage's row is b.  c_rke[r][j] = b_j - b*_j.
+constexpr int NRK = 6;
+__constant__ double c_rka[NRK][8][8] = {
+    {{0}, {0}, {0, 1.0 / 5}, {0, 3.0 / 40, 9.0 / 40}, {0, 44.0 / 45, -56.0 / 15, 32.0 / 9},
+     {0, 19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729},
+     {0, 9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656},
+     {0, 35.0 / 384, 0.0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84}},
+    {{0}, {0}, {0, 1.0 / 2}, {0, 0.0, 3.0 / 4}, {0, 2.0 / 9, 1.0 / 3, 4.0 / 9}},
+    {{0}, {0}, {0, 1.0 / 5}, {0, 3.0 / 40, 9.0 / 40}, {0, 3.0 / 10, -9.0 / 10, 6.0 / 5},
+     {0, -11.0 / 54, 5.0 / 2, -70.0 / 27, 35.0 / 27},
+     {0, 1631.0 / 55296, 175.0 / 512, 575.0 / 13824, 44275.0 / 110592, 253.0 / 4096}},
+    {{0}, {0}, {0, 1.0 / 2}, {0, 0.0, 1.0 / 2}, {0, 0.0, 0.0, 1.0}},
+    {{0}, {0}, {0, 1.0 / 2}, {0, -1.0, 2.0}},
+    {{0}, {0}, {0, 1.0}},
+};
+__constant__ double c_rkb[NRK][8] = {
+    {0, 35.0 / 384, 0.0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84, 0.0},
+    {0, 2.0 / 9, 1.0 / 3, 4.0 / 9, 0.0},
+    {0, 37.0 / 378, 0.0, 250.0 / 621, 125.0 / 594, 0.0, 512.0 / 1771},
+    {0, 1.0 / 6, 1.0 / 3, 1.0 / 3, 1.0 / 6},
+    {0, 1.0 / 6, 2.0 / 3, 1.0 / 6},
+    {0, 1.0 / 2, 1.0 / 2},
+};
+__constant__ double c_rke[NRK][8] = {
+    {0, 35.0 / 384 - 5179.0 / 57600, 0.0, 500.0 / 1113 - 7571.0 / 16695, 125.0 / 192 - 393.0 / 640,
+     -2187.0 / 6784 + 92097.0 / 339200, 11.0 / 84 - 187.0 / 2100, -1.0 / 40},
+    {0, 2.0 / 9 - 7.0 / 24, 1.0 / 3 - 1.0 / 4, 4.0 / 9 - 1.0 / 3, -1.0 / 8},
+    {0, 37.0 / 378 - 2825.0 / 27648, 0.0, 250.0 / 621 - 18575.0 / 48384, 125.0 / 594 - 13525.0 / 55296,
+     -277.0 / 14336, 512.0 / 1771 - 1.0 / 4},
     {0}, {0},
-    {0, 1.0 / 5},
-    {0, 3.0 / 40, 9.0 / 40},
-    {0, 44.0 / 45, -56.0 / 15, 32.0 / 9},
-    {0, 19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729},
-    {0, 9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656},
-    {0, 35.0 / 384, 0.0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84},
+    {0, 1.0 / 2 - 1.0, 1.0 / 2},
 };
-__constant__ double c_dpe[8] = {
-    0,
-    35.0 / 384 - 5179.0 / 57600,
-    0.0,
-    500.0 / 1113 - 7571.0 / 16695,
-    125.0 / 192 - 393.0 / 640,
-    -2187.0 / 6784 + 92097.0 / 339200,
-    11.0 / 84 - 187.0 / 2100,
-    -1.0 / 40,
-};
+// stages, first-same-as-last, exponent denominator q of the step-size factor (0: fixed step)
+__constant__ int c_rks[NRK] = {7, 4, 6, 4, 3, 2};
+__constant__ int c_rkfsal[NRK] = {1, 1, 0, 0, 0, 0};
+__constant__ double c_rkq[NRK] = {5.0, 3.0, 5.0, 0.0, 0.0, 2.0};
 
 // ---------------------------------------------------------------------------
 // small helpers
@@ -183,7 +202,7 @@ __global__ void __launch_bounds__(XS<LOGP>::NT, XS<LOGP>::MINB) k_xfwd(HotParams
     const float* src = comb ? p.ms[cur] : src_ptr(p, a.src, cur);
     const float* k1 = p.ks[cur];
     float* wout = p.mstage[0];
-    const Coef c21 = comb ? split(st->h * c_dpa[2][1]) : Coef{0.f, 0.f};
+    const Coef c21 = comb ? split(st->h * c_rka[p.rk][2][1]) : Coef{0.f, 0.f};
     const int NX = p.nx, NY = p.ny;
     for (int idx = threadIdx.x; idx < S::NL * S::P; idx += S::NT) {
         const int l = idx >> LOGP, x = idx & (S::P - 1);
@@ -398,15 +417,18 @@ __device__ void finalize(const HotParams& p, const LaunchArgs& a) {
         case LM_RKFINAL: {
             st->last_err = err;
             if (bad || !isfinite(err)) { st->status = -5; st->done = 1; break; }
-            const bool accept = st->fixed_h || (double)err <= st->tol;
-            double f = (err == 0.0f) ? 5.0 : 0.9 * pow(st->tol / (double)err, 0.2);
+            const double q = c_rkq[p.rk];
+            const bool fixed = st->fixed_h || q == 0.0;
+            const bool accept = fixed || (double)err <= st->tol;
+            double f = (err == 0.0f) ? 5.0 : 0.9 * pow(st->tol / (double)err, 1.0 / (q > 0.0 ? q : 5.0));
             f = fmin(fmax(f, 0.2), 5.0);
-            if (st->fixed_h) f = 1.0;
+            if (fixed) f = 1.0;
             if (accept) {
                 if (st->after_reject) f = fmin(f, 1.0);
                 st->t += st->h;
                 st->cur ^= 1;
                 st->accepted += 1;
+                st->step_index += 1;
                 st->max_torque = tq;
                 st->after_reject = 0;
             } else {
@@ -482,6 +504,7 @@ __device__ void reduce_and_finish(const HotParams& p, const LaunchArgs& a, Parti
 // Everything that happens to one cell once its demag field is known.
 struct StageCoefs {
     Coef c[8];          // per mode: stage combination weights (see stage_coefs)
+    Coef e[8];          // final stage: error weights h (b_j - b*_j)
 };
 
 // Returns the magnetisation the next evaluation of this step reads at this
@@ -521,28 +544,31 @@ __device__ __forceinline__ f3 cell_update(const HotParams& p, const LaunchArgs& 
     f3 myp = m, mym = m, mzp = m, mzm = m;
     if (usey) { myp = ld3(min, iyp, n); mym = ld3(min, iym, n); }
     if (usez) { mzp = ld3(min, izp, n); mzm = ld3(min, izm, n); }
-    // stage inputs: q[0] = m_n, q[1] = k1, q[j] = k_j
-    f3 q0 = mk(0.f, 0.f, 0.f), q1 = q0, q2 = q0, q3 = q0, q4 = q0, q5 = q0, q6 = q0;
+    // stage inputs: q0 = m_n, qk[0] = k1, qk[j-1] = k_j
+    f3 q0 = mk(0.f, 0.f, 0.f);
+    f3 qk[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) qk[j] = q0;
     const int s = a.stage;
+    const bool fsal = p.rk_fsal != 0;
     switch (a.mode) {
-        case LM_RK:
+        case LM_RK:                                  // stage s: input of s+1 = m_n + sum_{j<=s} a k_j
             q0 = ld3(p.ms[cur], cell, n);
-            q1 = ld3(p.ks[cur], cell, n);
-            if (s >= 3 && sc.c[2].hi != 0.f) q2 = ld3(p.kb[2], cell, n);
-            if (s >= 4) q3 = ld3(p.kb[3], cell, n);
-            if (s >= 5) q4 = ld3(p.kb[4], cell, n);
-            if (s >= 6) q5 = ld3(p.kb[5], cell, n);
+            qk[0] = ld3(p.ks[cur], cell, n);
+#pragma unroll
+            for (int j = 2; j <= 6; ++j)
+                if (j < s && sc.c[j].hi != 0.f) qk[j - 1] = ld3(p.kb[j], cell, n);
             break;
-        case LM_RKFINAL:
-            q1 = ld3(p.ks[cur], cell, n);
-            q3 = ld3(p.kb[3], cell, n);
-            q4 = ld3(p.kb[4], cell, n);
-            q5 = ld3(p.kb[5], cell, n);
-            q6 = ld3(p.kb[6], cell, n);
+        case LM_RKFINAL:                             // stage S: error (and m_{n+1} without FSAL)
+            if (!fsal) q0 = ld3(p.ms[cur], cell, n);
+            qk[0] = ld3(p.ks[cur], cell, n);
+#pragma unroll
+            for (int j = 2; j <= 6; ++j)
+                if (j < s && (sc.e[j].hi != 0.f || (!fsal && sc.c[j].hi != 0.f))) qk[j - 1] = ld3(p.kb[j], cell, n);
             break;
         case LM_HEUN2:
             q0 = ld3(p.ms[cur], cell, n);
-            q1 = ld3(p.ks[cur], cell, n);
+            qk[0] = ld3(p.ks[cur], cell, n);
             break;
         default: break;
     }
@@ -593,33 +619,42 @@ __device__ __forceinline__ f3 cell_update(const HotParams& p, const LaunchArgs& 
             next = axpy(sc.c[1], k, m);                 // m_2 = m_n + h a21 k1
             st3(p.mstage[0], cell, n, next);
             break;
-        case LM_RK: {                                    // stages 2..6
+        case LM_RK: {                                    // stages 2..S-1
             st3(p.kb[s], cell, n, k);
-            f3 acc = axpy(sc.c[1], q1, q0);
-            if (s >= 3 && sc.c[2].hi != 0.f) acc = axpy(sc.c[2], q2, acc);
-            if (s >= 4) acc = axpy(sc.c[3], q3, acc);
-            if (s >= 5) acc = axpy(sc.c[4], q4, acc);
-            if (s >= 6) acc = axpy(sc.c[5], q5, acc);
+            f3 acc = axpy(sc.c[1], qk[0], q0);
+#pragma unroll
+            for (int j = 2; j <= 6; ++j)
+                if (j < s && sc.c[j].hi != 0.f) acc = axpy(sc.c[j], qk[j - 1], acc);
             acc = axpy(sc.c[s], k, acc);
-            if (s < 6) {
-                st3(p.mstage[(s + 1) & 1], cell, n, acc);
-                next = acc;
-            } else {
+            if (fsal && s + 1 == p.rk_stages) {          // the last stage evaluates the candidate
                 next = normalized(acc);
                 st3(p.ms[1 - cur], cell, n, next);
+            } else {
+                st3(p.mstage[(s + 1) & 1], cell, n, acc);
+                next = acc;
             }
             pt.bad |= !finite3(k);
             break;
         }
-        case LM_RKFINAL: {
-            st3(p.ks[1 - cur], cell, n, k);
+        case LM_RKFINAL: {                               // stage S
             f3 e = mk(0.f, 0.f, 0.f);
-            e = axpy(sc.c[1], q1, e);
-            e = axpy(sc.c[3], q3, e);
-            e = axpy(sc.c[4], q4, e);
-            e = axpy(sc.c[5], q5, e);
-            e = axpy(sc.c[6], q6, e);
-            e = axpy(sc.c[7], k, e);
+            e = axpy(sc.e[1], qk[0], e);
+#pragma unroll
+            for (int j = 2; j <= 6; ++j)
+                if (j < s && sc.e[j].hi != 0.f) e = axpy(sc.e[j], qk[j - 1], e);
+            e = axpy(sc.e[s], k, e);
+            if (fsal) {
+                st3(p.ks[1 - cur], cell, n, k);          // k_S = f(m_{n+1}) is the next step's k1
+            } else {
+                f3 acc = axpy(sc.c[1], qk[0], q0);
+#pragma unroll
+                for (int j = 2; j <= 6; ++j)
+                    if (j < s && sc.c[j].hi != 0.f) acc = axpy(sc.c[j], qk[j - 1], acc);
+                acc = axpy(sc.c[s], k, acc);
+                const f3 mn = normalized(acc);
+                st3(p.ms[1 - cur], cell, n, mn);
+                pt.bad |= !finite3(mn);
+            }
             pt.err = fmaxf(pt.err, sqrtf(dot(e, e)));
             pt.torque = fmaxf(pt.torque, tq);
             pt.bad |= !finite3(k) || !finite3(e);
@@ -639,7 +674,7 @@ __device__ __forceinline__ f3 cell_update(const HotParams& p, const LaunchArgs& 
             break;
         }
         case LM_HEUN2: {
-            f3 acc = axpy(sc.c[0], q1, q0);
+            f3 acc = axpy(sc.c[0], qk[0], q0);
             acc = axpy(sc.c[0], k, acc);
             next = normalized(acc);
             st3(p.ms[1 - cur], cell, n, next);
@@ -652,17 +687,21 @@ __device__ __forceinline__ f3 cell_update(const HotParams& p, const LaunchArgs& 
 }
 
 __device__ void stage_coefs(const HotParams& p, const LaunchArgs& a, const DevState* st, StageCoefs& sc) {
-    for (int j = 0; j < 8; ++j) sc.c[j] = {0.f, 0.f};
+    for (int j = 0; j < 8; ++j) { sc.c[j] = {0.f, 0.f}; sc.e[j] = {0.f, 0.f}; }
     const double h = st->h;
+    const int r = p.rk;
     switch (a.mode) {
         case LM_K1:
-            sc.c[1] = split(h * c_dpa[2][1]);
+            sc.c[1] = split(h * c_rka[r][2][1]);
             break;
         case LM_RK:
-            for (int j = 1; j <= a.stage; ++j) sc.c[j] = split(h * c_dpa[a.stage + 1][j]);
+            for (int j = 1; j <= a.stage; ++j) sc.c[j] = split(h * c_rka[r][a.stage + 1][j]);
             break;
         case LM_RKFINAL:
-            for (int j = 1; j <= 7; ++j) sc.c[j] = split(h * c_dpe[j]);
+            for (int j = 1; j <= 7; ++j) {
+                sc.e[j] = split(h * c_rke[r][j]);
+                sc.c[j] = split(h * c_rkb[r][j]);
+            }
             break;
         case LM_EULER:
         case LM_HEUN1:
@@ -785,7 +824,7 @@ __global__ void k_combine2(HotParams p) {
     if (st->done) return;
     const long long n = p.ncell;
     const int cur = st->cur;
-    const Coef c = split(st->h * c_dpa[2][1]);
+    const Coef c = split(st->h * c_rka[p.rk][2][1]);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         st3(p.mstage[0], i, n, axpy(c, ld3(p.ks[cur], i, n), ld3(p.ms[cur], i, n)));
 }

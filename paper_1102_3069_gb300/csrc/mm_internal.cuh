@@ -39,8 +39,8 @@ struct DevState {
 enum LocalMode : int {
     LM_EVAL = 0,      // write H (A/m) and dm/dt (1/s); optional energy
     LM_K1 = 1,        // k1 = f(m_n) into the current k slot; torque check
-    LM_RK = 2,        // Dormand-Prince stage s = 2..6: k_s and m_{s+1}
-    LM_RKFINAL = 3,   // stage 7 (FSAL): k7, error, torque, step control
+    LM_RK = 2,        // Runge-Kutta stage s = 2..S-1: k_s and the input of stage s+1
+    LM_RKFINAL = 3,   // last stage S: error, torque, (m_{n+1} without FSAL), step control
     LM_EULER = 4,
     LM_HEUN1 = 5,
     LM_HEUN2 = 6,
@@ -87,6 +87,9 @@ struct HotParams {
     int demag;
     // step (internal units)
     double dt_d;             // Euler/Heun fixed step
+    int rk;                  // Runge-Kutta tableau index (hotpath.cu c_rka)
+    int rk_stages;           // its number of stages
+    int rk_fsal;             // its last stage evaluates the new solution
     // output scales
     float h_scale;           // Ms (A/m)
     float t_scale;           // gamma0 Ms (1/s)

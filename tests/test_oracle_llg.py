@@ -195,3 +195,54 @@ def test_langevin_statistics_of_thermal_macrospins():
             cnt += 1
     expect = 1.0 / np.tanh(x) - 1.0 / x
     assert acc / cnt == pytest.approx(expect, abs=0.01)
+
+
+@pytest.mark.parametrize("name,order,hs", [("rk3", 3, [4e-12, 2e-12]), ("rk4", 4, [8e-12, 4e-12]),
+                                          ("rk12", 2, [2e-12, 1e-12]), ("rk23", 3, [4e-12, 2e-12]),
+                                          ("rkck", 5, [1e-11, 5e-12]), ("rkdp", 5, [1e-11, 5e-12])])
+def test_tableau_convergence_orders(name, order, hs):
+    tab = llg.TABLEAUS[name]
+
+    def st(p, m, h, k):
+        return llg.rk_attempt(p, m, h, tab)[0]
+
+    assert _order(st, hs, 1e-10) == pytest.approx(order, abs=0.3)
+
+
+@pytest.mark.parametrize("name,q", [("rk12", 2), ("rk23", 3), ("rkck", 5)])
+def test_embedded_error_orders(name, q):
+    p = _macrospin(0.1, 0.05)
+    m = _m0(1.0, 0.0)
+    tab = llg.TABLEAUS[name]
+    e1 = llg.rk_attempt(p, m, 4e-12, tab)[2]
+    e2 = llg.rk_attempt(p, m, 2e-12, tab)[2]
+    assert np.log2(e1 / e2) == pytest.approx(q, abs=0.3)
+
+
+def test_tableau_rows_are_consistent():
+    # sum_j a_sj = c_s is implied; each row of a first-same-as-last tableau ends in b
+    for tab in llg.TABLEAUS.values():
+        assert sum(tab.b) == pytest.approx(1.0, abs=1e-15)
+        if tab.bstar is not None:
+            assert sum(tab.bstar) == pytest.approx(1.0, abs=1e-15)
+        if tab.fsal:
+            assert tuple(tab.a[-1]) == pytest.approx(tuple(tab.b[:-1]), abs=1e-15)
+            assert tab.b[-1] == 0.0
+
+
+def test_generic_dormand_prince_equals_the_dedicated_one():
+    p, m = _random_film(0.05, seed=2, shape=(8, 4, 1))
+    a = llg.rk_attempt(p, m, 3e-14, llg.TABLEAUS["rkdp"])
+    b = llg.rkdp_stages(p, m, 3e-14)
+    assert np.max(np.abs(a[0] - b[0])) < 1e-15
+    assert a[2] == pytest.approx(b[2], rel=1e-12)
+
+
+@pytest.mark.parametrize("name", ["rk12", "rk23", "rkck"])
+def test_adaptive_tableaus_hit_the_closed_form(name):
+    alpha, B, th0 = 0.05, 0.05, 1.2
+    p = _macrospin(alpha, B)
+    st = llg.TableauStepper(p, _m0(th0, 0.0), llg.TABLEAUS[name], h0=1e-13, tol=1e-8)
+    st.run_until(1e-10)
+    assert st.t == pytest.approx(1e-10, rel=1e-12)
+    np.testing.assert_allclose(st.m, _exact(alpha, B, th0, 0.0, st.t), atol=2e-5)
