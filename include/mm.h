@@ -113,6 +113,18 @@ int mm_set_material(mm_ctx* ctx, double Ms, double Aex, double Ku, const double 
 int mm_set_cubic_anisotropy(mm_ctx* ctx, double K1, double K2, const double c1[3], const double c2[3]);
 
 /*
+ * Spin-transfer torque of Zhang and Li (Sec. 2.1.4, Eq. 7), a torque added to
+ * dm/dt (not a field):
+ *   dm/dt += -b_j/(1+alpha^2) [ m x (m x (j.grad)m) + (xi - alpha) m x (j.grad)m ],
+ *   b_j = P mu_B / (e Ms (1 + xi^2)),
+ * with polarisation P, non-adiabaticity xi and the uniform current density
+ * j_A_per_m2[3] (A/m^2; NULL = no current).  (j.grad)m uses central
+ * differences; at a free boundary the missing neighbour is the cell itself.
+ * P = 0 or j = 0 (the default) switches it off.  MM_EINVAL for non-finite input.
+ */
+int mm_set_stt(mm_ctx* ctx, double P, double xi, const double j_A_per_m2[3]);
+
+/*
  * Enable (1) or disable (0) the magnetostatic term.  Enabled by default; when
  * enabled, mm_demag_kernel must have run before any evaluation.  Disabling it
  * leaves exchange, anisotropy, Zeeman and thermal terms (used for uncoupled

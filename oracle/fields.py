@@ -15,6 +15,10 @@ applied, anisotropy, thermal).
   = -(2/(mu0 Ms)) sum_i a_i [K1 (a_j^2 + a_k^2) + K2 a_j^2 a_k^2] c_i.
   phi is quartic, so its energy is summed directly (not as -mu0 Ms m.H/2).
 * Zeeman: H_z = B / mu0 for an applied flux density B in tesla.
+* spin-transfer torque (Sec. 2.1.4, Eq. 7, Zhang & Li): a torque, not a field:
+  dm/dt += -b_j/(1+alpha^2) [m x (m x (j.grad)m) + (xi - alpha) m x (j.grad)m],
+  b_j = P mu_B / (e Ms (1 + xi^2)); (j.grad)m by central differences with the
+  free-boundary rule of the exchange stencil (a missing neighbour = the cell).
 * thermal (Sec. 2.1.3, Eq. 6): H_th = eta sqrt(2 alpha kB T / (gamma0 mu0 Ms V dt)),
   eta ~ N(0,1) per cell, component and step (drawn by ``philox``).
 
@@ -31,6 +35,8 @@ import numpy as np
 
 MU0 = 4.0e-7 * np.pi          # H/m
 KB = 1.380649e-23             # J/K
+MU_B = 9.2740100783e-24       # J/T, Bohr magneton
+E_CHARGE = 1.602176634e-19    # C
 GAMMA0 = 2.211e5              # m/(A s): gamma acting on H in A/m (a reading)
 
 
@@ -117,6 +123,41 @@ def energy(m, Ms, V, Hd, Hex, Han, Hz):
     m = np.asarray(m, float)
     e = 0.5 * (m * (Hd + Hex + Han)).sum() + (m * Hz).sum()
     return -MU0 * Ms * V * e
+
+
+def stt_bj(P, xi, Ms):
+    """b_j = P mu_B / (e Ms (1 + xi^2)) of Sec. 2.1.4 (m^3/C: b_j j is a velocity)."""
+    return P * MU_B / (E_CHARGE * Ms * (1.0 + xi * xi))
+
+
+def current_derivative(m, j, cell, pbc=(False, False, False)):
+    """(j . grad) m by central differences; at a free boundary the missing
+    neighbour is replaced by the cell itself (zero normal derivative)."""
+    m = np.asarray(m, float)
+    u = np.zeros_like(m)
+    for axis, jc, d, per in ((3, j[0], cell[0], pbc[0]), (2, j[1], cell[1], pbc[1]), (1, j[2], cell[2], pbc[2])):
+        if jc == 0.0:
+            continue
+        n = m.shape[axis]
+        up = np.roll(m, -1, axis=axis)          # neighbour at +1
+        dn = np.roll(m, 1, axis=axis)           # neighbour at -1
+        if not per:
+            last = [slice(None)] * 4
+            first = [slice(None)] * 4
+            last[axis] = n - 1
+            first[axis] = 0
+            up[tuple(last)] = m[tuple(last)]
+            dn[tuple(first)] = m[tuple(first)]
+        u += jc * (up - dn) / (2.0 * d)
+    return u
+
+
+def stt_torque(m, alpha, P, xi, j, cell, Ms, pbc=(False, False, False)):
+    """Zhang-Li spin-transfer torque of Eq. 7 divided by Ms (1/s):
+    -b_j/(1+alpha^2) [ m x (m x (j.grad)m) + (xi - alpha) m x (j.grad)m ]."""
+    u = current_derivative(m, j, cell, pbc)
+    mxu = np.cross(m, u, axis=0)
+    return -stt_bj(P, xi, Ms) / (1.0 + alpha * alpha) * (np.cross(m, mxu, axis=0) + (xi - alpha) * mxu)
 
 
 def torque_max(m, H, Ms):

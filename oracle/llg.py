@@ -74,7 +74,8 @@ class Problem:
     def __init__(self, shape, cell, Ms, Aex, alpha, Ku=0.0, u=(1.0, 0.0, 0.0),
                  B=(0.0, 0.0, 0.0), T=0.0, seed=0, gamma0=F.GAMMA0,
                  pbc=(False, False, False), images=10, demag=True, L=None,
-                 K1=0.0, K2=0.0, c1=(1.0, 0.0, 0.0), c2=(0.0, 1.0, 0.0)):
+                 K1=0.0, K2=0.0, c1=(1.0, 0.0, 0.0), c2=(0.0, 1.0, 0.0),
+                 stt_P=0.0, stt_xi=0.0, stt_j=(0.0, 0.0, 0.0)):
         self.shape = tuple(int(v) for v in shape)
         self.cell = tuple(float(v) for v in cell)
         self.V = self.cell[0] * self.cell[1] * self.cell[2]
@@ -88,6 +89,7 @@ class Problem:
         self.demag = _demag.Demag(self.shape, self.cell, self.pbc, images, L) if demag else None
         self.K1, self.K2 = float(K1), float(K2)
         self.c1, self.c2 = np.asarray(c1, float), np.asarray(c2, float)
+        self.stt_P, self.stt_xi, self.stt_j = float(stt_P), float(stt_xi), tuple(float(v) for v in stt_j)
         self.n_evals = 0
 
     @property
@@ -121,7 +123,10 @@ class Problem:
         return t["d"] + t["ex"] + t["an"] + t["cub"] + t["z"] + t["th"]
 
     def rhs(self, m, step=0, dt=None):
-        return ll_rhs(m, self.heff(m, step, dt), self.alpha, self.gamma0)
+        d = ll_rhs(m, self.heff(m, step, dt), self.alpha, self.gamma0)
+        if self.stt_P != 0.0 and any(v != 0.0 for v in self.stt_j):
+            d = d + F.stt_torque(m, self.alpha, self.stt_P, self.stt_xi, self.stt_j, self.cell, self.Ms, self.pbc)
+        return d
 
     def energy(self, m):
         t = self.terms(m)

@@ -50,6 +50,7 @@ _SIGS = {
     "mm_set_material": (_i, [_vp, _d, _d, _d, _dp, _d, _d, _d, _u64, _dp]),
     "mm_set_demag": (_i, [_vp, _i]),
     "mm_set_cubic_anisotropy": (_i, [_vp, _d, _d, _dp, _dp]),
+    "mm_set_stt": (_i, [_vp, _d, _d, _dp]),
     "mm_demag_kernel": (_i, [_vp, _dp]),
     "mm_demag_tensor_len": (_sz, [_vp]),
     "mm_eval_heff": (_i, [_vp, _vp, _vp, _vp, _dp]),
@@ -148,6 +149,11 @@ def mm_set_cubic_anisotropy(ctx, K1, K2, c1=(1.0, 0.0, 0.0), c2=(0.0, 1.0, 0.0))
     a, _ka = _d3(c1)
     b, _kb = _d3(c2)
     return _check(ctx, lib().mm_set_cubic_anisotropy(ctx, float(K1), float(K2), a, b))
+
+
+def mm_set_stt(ctx, P, xi, j=(0.0, 0.0, 0.0)):
+    jj, _kj = _d3(j)
+    return _check(ctx, lib().mm_set_stt(ctx, float(P), float(xi), jj))
 
 
 def mm_set_demag(ctx, enabled):

@@ -78,6 +78,7 @@ struct mm_ctx {
     uint64_t seed = 0;
     double B[3] = {0, 0, 0};
     double K1 = 0, K2 = 0, cub[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    double stt_P = 0, stt_xi = 0, stt_j[3] = {0, 0, 0};
     bool demag = true;
     bool kernel_ready = false;
     // workspace
@@ -191,6 +192,14 @@ mm::HotParams hot_params(mm_ctx* c, double dt_internal, bool thermal) {
     p.kc2 = (float)(2.0 * c->K2 / (MU0 * Ms * Ms));
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) p.c[i][j] = (float)c->cub[i][j];
+    if (c->stt_P != 0.0 && (c->stt_j[0] != 0.0 || c->stt_j[1] != 0.0 || c->stt_j[2] != 0.0)) {
+        constexpr double MU_B = 9.2740100783e-24, E_CHARGE = 1.602176634e-19;
+        const double bj = c->stt_P * MU_B / (E_CHARGE * Ms * (1.0 + c->stt_xi * c->stt_xi));
+        const double d[3] = {c->dx, c->dy, c->dz};
+        for (int a = 0; a < 3; ++a) p.stt_s[a] = (float)(bj * c->stt_j[a] / (2.0 * d[a] * c->gamma0 * Ms));
+        p.stt_beta = (float)(c->stt_xi - c->alpha);
+        p.stt = 1;
+    }
     p.alpha = (float)c->alpha;
     p.llpref = (float)(1.0 / (1.0 + c->alpha * c->alpha));
     p.seed = c->seed;
@@ -467,6 +476,23 @@ int mm_set_cubic_anisotropy(mm_ctx* ctx, double K1, double K2, const double c1[3
     for (int i = 0; i < 3; ++i) { ctx->cub[0][i] = a[i]; ctx->cub[1][i] = b[i]; ctx->cub[2][i] = c3[i]; }
     ctx->K1 = K1;
     ctx->K2 = K2;
+    ctx->k1_valid = false;
+    ctx->param_version++;
+    return MM_OK;
+}
+
+int mm_set_stt(mm_ctx* ctx, double P, double xi, const double j_A_per_m2[3]) {
+    if (!ctx) return MM_EINVAL;
+    if (!std::isfinite(P) || !std::isfinite(xi)) return fail(ctx, MM_EINVAL, "P and xi must be finite");
+    double j[3] = {0, 0, 0};
+    if (j_A_per_m2)
+        for (int a = 0; a < 3; ++a) {
+            if (!std::isfinite(j_A_per_m2[a])) return fail(ctx, MM_EINVAL, "current density must be finite");
+            j[a] = j_A_per_m2[a];
+        }
+    ctx->stt_P = P;
+    ctx->stt_xi = xi;
+    for (int a = 0; a < 3; ++a) ctx->stt_j[a] = j[a];
     ctx->k1_valid = false;
     ctx->param_version++;
     return MM_OK;

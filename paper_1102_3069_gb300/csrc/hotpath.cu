@@ -595,7 +595,14 @@ __device__ __forceinline__ f3 cell_update(const HotParams& p, const LaunchArgs& 
     f3 h = hd + hex + han + hz;
     if (p.sigma_th > 0.f) h = h + p.sigma_th * gauss3(cell, tstep, p.seed);
     const f3 mxh = cross(m, h);
-    const f3 k = (-p.llpref) * (mxh + p.alpha * cross(m, mxh));
+    f3 k = (-p.llpref) * (mxh + p.alpha * cross(m, mxh));
+    if (p.stt) {
+        // Zhang-Li spin-transfer torque (Eq. 7 / Ms): (j.grad)m from the same
+        // neighbours (a missing one is the cell itself), b_j folded into stt_s
+        const f3 us = (p.stt_s[0] * (mxp - mxm) + p.stt_s[1] * (myp - mym)) + p.stt_s[2] * (mzp - mzm);
+        const f3 mxu = cross(m, us);
+        k = k - p.llpref * (cross(m, mxu) + p.stt_beta * mxu);
+    }
     const float tq = sqrtf(dot(mxh, mxh));
     f3 next = mk(0.f, 0.f, 0.f);
 

@@ -79,6 +79,9 @@ struct HotParams {
     float hzx, hzy, hzz;     // B/(mu0 Ms)
     float kc1, kc2;          // cubic anisotropy 2K1/(mu0 Ms^2), 2K2/(mu0 Ms^2) (0: off)
     float c[3][3];           // orthonormal cubic axes c1, c2, c3
+    float stt_s[3];          // spin-transfer torque: b_j j_a / (2 d_a gamma0 Ms) per axis (0: off)
+    float stt_beta;          // xi - alpha
+    int stt;                 // spin-transfer torque on
     float alpha;
     float llpref;            // 1/(1+alpha^2)
     float sigma_th;          // thermal sigma / Ms for the current dt (0: off)

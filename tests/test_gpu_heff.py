@@ -125,3 +125,20 @@ def test_cubic_anisotropy_matches_oracle(shape):
     assert e == pytest.approx(p.energy(m64), rel=1e-6)
     with pytest.raises(B.MMError):
         B.mm_set_cubic_anisotropy(s.ctx, K1, K2, c1, c1)      # parallel axes
+
+
+@pytest.mark.parametrize("shape,pbc", [((33, 7, 1), (0, 0, 0)), ((16, 12, 3), (1, 0, 0)), ((32, 8, 1), (1, 1, 0))])
+def test_spin_transfer_torque_matches_oracle(shape, pbc):
+    from paper_1102_3069_gb300 import binding as B
+    cell = (4e-9, 3e-9, 2e-9)
+    P, xi, j = 0.56, 0.05, (1e12, -4e11, 2e11)
+    m = inputs.random_unit(shape, 6)
+    s = solver(shape, cell, pbc=pbc, images=2, **MAT)
+    B.mm_set_stt(s.ctx, P, xi, j)
+    h, tq, _ = s.heff(to_dev(m), torque=True)
+    p = llg.Problem(shape, cell, MAT["Ms"], MAT["Aex"], MAT["alpha"], Ku=MAT["Ku"], u=MAT["easy_axis"], B=MAT["B"],
+                    pbc=tuple(bool(v) for v in pbc), images=2, stt_P=P, stt_xi=xi, stt_j=j)
+    m64 = m.astype(np.float64)
+    assert rel_l2(to_np(h), p.heff(m64)) <= HEFF_REL_L2          # a torque, not a field
+    ref = p.rhs(m64)
+    assert rel_l2(to_np(tq), ref) <= 2 * HEFF_REL_L2

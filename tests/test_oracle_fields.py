@@ -203,3 +203,57 @@ def test_cubic_energy_decreases_under_damping():
             E.append(p.energy(st.m))
     assert np.all(np.diff(E) <= 1e-7 * abs(E[0]))
     assert E[-1] < E[0]
+
+
+def _spiral(n, k, d):
+    x = np.arange(n) * d
+    m = np.zeros((3, 1, 1, n))
+    m[0, 0, 0] = np.cos(k * x)
+    m[1, 0, 0] = np.sin(k * x)
+    return m, x
+
+
+def test_stt_vanishes_for_uniform_state_and_is_perpendicular():
+    m = np.zeros((3, 2, 3, 4))
+    m[2] = 1.0
+    tq = F.stt_torque(m, 0.1, 0.5, 0.05, (1e12, -3e11, 2e11), (4e-9, 3e-9, 2e-9), MS)
+    assert np.max(np.abs(tq)) == 0.0
+    rng = np.random.default_rng(11)
+    m = rng.standard_normal((3, 3, 4, 5))
+    m /= np.linalg.norm(m, axis=0)
+    tq = F.stt_torque(m, 0.1, 0.5, 0.05, (1e12, -3e11, 2e11), (4e-9, 3e-9, 2e-9), MS, pbc=(True, False, True))
+    assert np.max(np.abs((m * tq).sum(axis=0))) <= 1e-9 * np.max(np.abs(tq))
+
+
+def test_stt_on_a_spiral_has_the_closed_form():
+    # m = (cos kx, sin kx, 0), periodic in x: (j.grad)m = j sin(kd)/d (-sin kx, cos kx, 0)
+    n, d, q = 32, 2e-9, 3
+    k = 2 * np.pi * q / (n * d)
+    m, x = _spiral(n, k, d)
+    P, xi, alpha, jx = 0.6, 0.05, 0.02, 1e12
+    tq = F.stt_torque(m, alpha, P, xi, (jx, 0.0, 0.0), (d, 1e-9, 1e-9), MS, pbc=(True, False, False))
+    c = jx * np.sin(k * d) / d
+    u = c * np.stack([-np.sin(k * x), np.cos(k * x), np.zeros(n)])
+    zhat = np.stack([np.zeros(n), np.zeros(n), c * np.ones(n)])
+    bj = F.stt_bj(P, xi, MS)
+    expect = -bj / (1 + alpha ** 2) * (-u + (xi - alpha) * zhat)
+    np.testing.assert_allclose(tq[:, 0, 0, :], expect, rtol=1e-12, atol=1e-12 * np.abs(expect).max())
+    assert bj == pytest.approx(P * F.MU_B / (F.E_CHARGE * MS * (1 + xi * xi)), rel=1e-15)
+
+
+def test_adiabatic_stt_advects_a_spiral():
+    # xi = alpha and no field: dm/dt = b_j/(1+alpha^2) (j.grad)m, a rigid rotation of the
+    # spiral about z at rate b_j j sin(kd)/d/(1+alpha^2) - a translation of the texture
+    from oracle import llg
+    n, d, q = 32, 2e-9, 2
+    k = 2 * np.pi * q / (n * d)
+    m, x = _spiral(n, k, d)
+    P, alpha, jx = 0.7, 0.1, 2e12
+    p = llg.Problem((n, 1, 1), (d, 1e-9, 1e-9), MS, 0.0, alpha, pbc=(True, False, False), demag=False,
+                    stt_P=P, stt_xi=alpha, stt_j=(jx, 0.0, 0.0))
+    w = F.stt_bj(P, alpha, MS) * jx * np.sin(k * d) / d / (1 + alpha ** 2)
+    T = 0.4 / w
+    mT = llg.rkdp_fixed(p, m, T / 200, 200)
+    exact, _ = _spiral(n, k, d)
+    exact = np.stack([np.cos(k * x + w * T), np.sin(k * x + w * T), np.zeros(n)])
+    np.testing.assert_allclose(mT[:, 0, 0, :], exact, atol=1e-9)
