@@ -153,11 +153,18 @@ def algorithmic_bytes(nx, ny):
     fused = [spec + m + m * (reads[s] + 2) + spec for s in range(2, 7)]
     final = spec + m + m * 5 + m
     xf = spec + 3 * m                      # stage 2 input m_n + h a21 k1, written out as m_2
+    # split passes (padded x length >= 64): the inverse x pass writes H_demag
+    # (m bytes) and the cell pass reads it back; that round trip is not part
+    # of the method's bytes, so "step" leaves it out
+    cell = [m + m + m * (reads[s] + 2) for s in range(2, 7)] + [m + m + 5 * m + m]
     return {
         "k_xfwd": float(xf),
         "k_colconv_y": float(2 * spec + kern),
         "k_xinv_local_fused": sum(fused) / 5.0,
         "k_xinv_local": float(final),
+        "k_xinv_h": float(spec + m),
+        "k_local_h": sum(cell) / 6.0,
+        "k_xfwd_next": float(m + spec),
         "step": float(xf + 6 * (2 * spec + kern) + sum(fused) + final),
     }
 
@@ -180,6 +187,9 @@ def algorithmic_bytes_3d(shape, pz, images_axes=(True, True, False)):
         "k_colconv_z": float(2 * s2 + kern),
         "k_yinv": float(s2 + s1),
         "k_xinv_local_fused": (heun1 + heun2) / 2.0,
+        "k_xinv_h": float(s1 + m),
+        "k_local_h": (4 * m + 5 * m) / 2.0,    # H_demag read back + the Heun stage's reads and writes
+        "k_xfwd_next": float(m + s1),
         "step": float(2 * (2 * (s1 + s2) + 2 * s2 + kern) + heun1 + heun2),
     }
 

@@ -230,9 +230,12 @@ int mm_run_host(mm_ctx* ctx, float* m_host, int method, long nsteps, double dt_s
  * mm_profile(ctx, 1); arrays of MM_NPASS entries in the order
  * x forward, y conv (2-D), y forward, z conv, y inverse (3-D), x inverse +
  * local terms, stage-2 combine, local terms without demag, x inverse + local
- * terms + forward x transform of the next stage's input.
+ * terms + forward x transform of the next stage's input, x inverse alone
+ * (demag field to a buffer), cell pass reading that buffer, forward x
+ * transform of the next stage's input.  Time steps on grids whose padded x
+ * length is at least 64 use the last three; the rest use the fused passes.
  */
-enum { MM_NPASS = 9 };
+enum { MM_NPASS = 12 };
 int mm_profile(mm_ctx* ctx, int enable);
 int mm_pass_times(mm_ctx* ctx, double* ms_out, long long* count_out);
 

@@ -137,8 +137,8 @@ void layout(mm_ctx* c) {
     c->sz_kt = (size_t)c->ncomp * c->hx * c->hyk * c->hzk * sizeof(float);
     c->sz_s1 = (size_t)3 * c->hx * c->nz * c->nyp * sizeof(float2);
     c->sz_s2 = c->nz > 1 ? (size_t)3 * c->hx * c->py * c->nzp * sizeof(float2) : 0;
-    // ms[2], ks[2], k2..k6, mstage[2]: 11 arrays of 3*ncell floats
-    c->sz_rk = 11 * align256((size_t)n3 * sizeof(float));
+    // ms[2], ks[2], k2..k6, mstage[2], hbuf: 12 arrays of 3*ncell floats
+    c->sz_rk = 12 * align256((size_t)n3 * sizeof(float));
     c->sz_setup = align256((size_t)6 * c->ox * c->oy * c->oz * sizeof(double)) +
                   align256((size_t)c->px * c->py * c->pz * sizeof(double2));
     size_t off = 0;
@@ -222,6 +222,7 @@ mm::HotParams hot_params(mm_ctx* c, double dt_internal, bool thermal) {
     p.ks[0] = rk_array(c, 2); p.ks[1] = rk_array(c, 3);
     for (int j = 2; j <= 6; ++j) p.kb[j] = rk_array(c, 2 + j);    // 4..8
     p.mstage[0] = rk_array(c, 9); p.mstage[1] = rk_array(c, 10);
+    p.hbuf = rk_array(c, 11);
     return p;
 }
 
@@ -241,6 +242,19 @@ __global__ void k_set_run(mm::DevState* st, double tol, double t_end, double tor
 int eval(mm_ctx* ctx, const mm::HotParams& p, int src, int mode, int stage, bool fuse = false,
          bool have_spectrum = false) {
     mm::LaunchArgs a{src, mode, stage, fuse ? 1 : 0, have_spectrum ? 1 : 0};
+    // where the cell pass leaves the next evaluation's input (what a fused
+    // forward x transform reads): after Euler and Heun's second stage the
+    // last block has already flipped the slots, so m_{n+1} is ms[cur]
+    switch (mode) {
+        case mm::LM_K1: case mm::LM_HEUN1: a.next_src = mm::SRC_STAGE0; break;
+        case mm::LM_RK:
+            a.next_src = (p.rk_fsal && stage + 1 == p.rk_stages) ? mm::SRC_NEXT
+                       : (((stage + 1) & 1) ? mm::SRC_STAGE1 : mm::SRC_STAGE0);
+            break;
+        case mm::LM_EULER: case mm::LM_HEUN2: a.next_src = mm::SRC_CUR; a.keep = 1; break;
+        default: a.next_src = mm::SRC_CUR; break;
+    }
+    a.need = mm::stage_need_mask(p.rk, mode, stage);
     int ids[8];
     const int n = mm::eval_passes(p, a, ids);
     for (int i = 0; i < n; ++i) {
@@ -882,6 +896,7 @@ int mm_eval_heff_static(mm_ctx* ctx, const float* m, float* h_out, float* torque
     p.kt = ctx->demag ? reinterpret_cast<const float*>(ctx->ws + ctx->off_kt) : nullptr;
     for (int i = 0; i < 2; ++i) { p.ms[i] = nullptr; p.ks[i] = nullptr; p.mstage[i] = nullptr; }
     for (int j = 0; j < 8; ++j) p.kb[j] = nullptr;
+    p.hbuf = nullptr;
     p.m_eval = m;
     p.h_out = h_out;
     p.tq_out = torque_out;

@@ -349,16 +349,41 @@ __device__ __forceinline__ int out_pos(int j, int i) {
 template <int LOGP>
 __host__ __device__ constexpr int nval() { return LOGP >= 3 ? 8 : (1 << LOGP); }
 
-template <int LOGP, bool REV, bool INV, int PI>
-__device__ __forceinline__ void compute(float2* v, int j, const float2* __restrict__ tw) {
+// w[r] = tw[t1]^r for r = 1..R-1 (conjugated for INV), formed as in
+// apply_twiddles: the loads w, w^2, w^4 and products of them
+template <int R, bool INV>
+__device__ __forceinline__ void twiddle_powers(float2* w, const float2* __restrict__ tw, int t1) {
+    if constexpr (R >= 2) w[1] = ldtw<INV>(tw, t1);
+    if constexpr (R >= 4) {
+        w[2] = ldtw<INV>(tw, 2 * t1);
+        w[3] = cmul(w[1], w[2]);
+    }
+    if constexpr (R >= 8) {
+        w[4] = ldtw<INV>(tw, 4 * t1);
+        w[5] = cmul(w[1], w[4]);
+        w[6] = cmul(w[2], w[4]);
+        w[7] = cmul(w[3], w[4]);
+    }
+}
+
+// pass PI on the same butterflies of NC lines: the twiddle factors are formed
+// once per butterfly and applied to every line
+template <int LOGP, bool REV, bool INV, int PI, int NC>
+__device__ __forceinline__ void compute_nc(float2 (*v)[8], int j, const float2* __restrict__ tw) {
     constexpr int R = radix_at<LOGP, REV>(PI), NS = ns_at<LOGP, REV>(PI), BPT = bpt_of<LOGP>(R);
 #pragma unroll
     for (int b = 0; b < BPT; ++b) {
         if constexpr (NS > 1) {
             const int jj = j + b * Plan8<LOGP>::NB, k = jj & (NS - 1);
-            apply_twiddles<R, INV>(v + b * R, tw, k * (TWN / (NS * R)));
+            float2 w[R > 1 ? R : 2];
+            twiddle_powers<R, INV>(w, tw, k * (TWN / (NS * R)));
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[c][b * R + r] = cmul(v[c][b * R + r], w[r]);
         }
-        dft<R, INV>(v + b * R);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) dft<R, INV>(v[c] + b * R);
     }
 }
 template <int LOGP, bool REV, int PI>
@@ -388,10 +413,7 @@ __device__ __forceinline__ void run(float2* const* a, float2 (*v)[8], int j, boo
                 for (int c = 0; c < NC; ++c) load<LOGP, REV, PI>(a[c], v[c], j);
             }
         }
-        if (active) {
-#pragma unroll
-            for (int c = 0; c < NC; ++c) compute<LOGP, REV, INV, PI>(v[c], j, tw);
-        }
+        if (active) compute_nc<LOGP, REV, INV, PI, NC>(v, j, tw);
         if constexpr (PI + 1 < PL::NPASS) {
             __syncthreads();
             if (active) {

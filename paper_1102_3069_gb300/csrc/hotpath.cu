@@ -38,36 +38,43 @@ namespace r8 = mmfft::r8;
 // c_rka[r][s][j]: weight of k_j in the input of stage s (1-based); with first
 // same as last the last stage's row is b.  c_rke[r][j] = b_j - b*_j.
 constexpr int NRK = 6;
-__constant__ double c_rka[NRK][8][8] = {
-    {{0}, {0}, {0, 1.0 / 5}, {0, 3.0 / 40, 9.0 / 40}, {0, 44.0 / 45, -56.0 / 15, 32.0 / 9},
-     {0, 19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729},
-     {0, 9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656},
-     {0, 35.0 / 384, 0.0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84}},
-    {{0}, {0}, {0, 1.0 / 2}, {0, 0.0, 3.0 / 4}, {0, 2.0 / 9, 1.0 / 3, 4.0 / 9}},
-    {{0}, {0}, {0, 1.0 / 5}, {0, 3.0 / 40, 9.0 / 40}, {0, 3.0 / 10, -9.0 / 10, 6.0 / 5},
-     {0, -11.0 / 54, 5.0 / 2, -70.0 / 27, 35.0 / 27},
-     {0, 1631.0 / 55296, 175.0 / 512, 575.0 / 13824, 44275.0 / 110592, 253.0 / 4096}},
-    {{0}, {0}, {0, 1.0 / 2}, {0, 0.0, 1.0 / 2}, {0, 0.0, 0.0, 1.0}},
-    {{0}, {0}, {0, 1.0 / 2}, {0, -1.0, 2.0}},
-    {{0}, {0}, {0, 1.0}},
-};
-__constant__ double c_rkb[NRK][8] = {
-    {0, 35.0 / 384, 0.0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84, 0.0},
-    {0, 2.0 / 9, 1.0 / 3, 4.0 / 9, 0.0},
-    {0, 37.0 / 378, 0.0, 250.0 / 621, 125.0 / 594, 0.0, 512.0 / 1771},
-    {0, 1.0 / 6, 1.0 / 3, 1.0 / 3, 1.0 / 6},
-    {0, 1.0 / 6, 2.0 / 3, 1.0 / 6},
-    {0, 1.0 / 2, 1.0 / 2},
-};
-__constant__ double c_rke[NRK][8] = {
-    {0, 35.0 / 384 - 5179.0 / 57600, 0.0, 500.0 / 1113 - 7571.0 / 16695, 125.0 / 192 - 393.0 / 640,
-     -2187.0 / 6784 + 92097.0 / 339200, 11.0 / 84 - 187.0 / 2100, -1.0 / 40},
-    {0, 2.0 / 9 - 7.0 / 24, 1.0 / 3 - 1.0 / 4, 4.0 / 9 - 1.0 / 3, -1.0 / 8},
-    {0, 37.0 / 378 - 2825.0 / 27648, 0.0, 250.0 / 621 - 18575.0 / 48384, 125.0 / 594 - 13525.0 / 55296,
-     -277.0 / 14336, 512.0 / 1771 - 1.0 / 4},
-    {0}, {0},
-    {0, 1.0 / 2 - 1.0, 1.0 / 2},
-};
+#define MM_RKA_INIT { \
+    {{0}, {0}, {0, 1.0 / 5}, {0, 3.0 / 40, 9.0 / 40}, {0, 44.0 / 45, -56.0 / 15, 32.0 / 9}, \
+     {0, 19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729}, \
+     {0, 9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656}, \
+     {0, 35.0 / 384, 0.0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84}}, \
+    {{0}, {0}, {0, 1.0 / 2}, {0, 0.0, 3.0 / 4}, {0, 2.0 / 9, 1.0 / 3, 4.0 / 9}}, \
+    {{0}, {0}, {0, 1.0 / 5}, {0, 3.0 / 40, 9.0 / 40}, {0, 3.0 / 10, -9.0 / 10, 6.0 / 5}, \
+     {0, -11.0 / 54, 5.0 / 2, -70.0 / 27, 35.0 / 27}, \
+     {0, 1631.0 / 55296, 175.0 / 512, 575.0 / 13824, 44275.0 / 110592, 253.0 / 4096}}, \
+    {{0}, {0}, {0, 1.0 / 2}, {0, 0.0, 1.0 / 2}, {0, 0.0, 0.0, 1.0}}, \
+    {{0}, {0}, {0, 1.0 / 2}, {0, -1.0, 2.0}}, \
+    {{0}, {0}, {0, 1.0}}, \
+}
+#define MM_RKB_INIT { \
+    {0, 35.0 / 384, 0.0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84, 0.0}, \
+    {0, 2.0 / 9, 1.0 / 3, 4.0 / 9, 0.0}, \
+    {0, 37.0 / 378, 0.0, 250.0 / 621, 125.0 / 594, 0.0, 512.0 / 1771}, \
+    {0, 1.0 / 6, 1.0 / 3, 1.0 / 3, 1.0 / 6}, \
+    {0, 1.0 / 6, 2.0 / 3, 1.0 / 6}, \
+    {0, 1.0 / 2, 1.0 / 2}, \
+}
+#define MM_RKE_INIT { \
+    {0, 35.0 / 384 - 5179.0 / 57600, 0.0, 500.0 / 1113 - 7571.0 / 16695, 125.0 / 192 - 393.0 / 640, \
+     -2187.0 / 6784 + 92097.0 / 339200, 11.0 / 84 - 187.0 / 2100, -1.0 / 40}, \
+    {0, 2.0 / 9 - 7.0 / 24, 1.0 / 3 - 1.0 / 4, 4.0 / 9 - 1.0 / 3, -1.0 / 8}, \
+    {0, 37.0 / 378 - 2825.0 / 27648, 0.0, 250.0 / 621 - 18575.0 / 48384, 125.0 / 594 - 13525.0 / 55296, \
+     -277.0 / 14336, 512.0 / 1771 - 1.0 / 4}, \
+    {0}, {0}, \
+    {0, 1.0 / 2 - 1.0, 1.0 / 2}, \
+}
+__constant__ double c_rka[NRK][8][8] = MM_RKA_INIT;
+__constant__ double c_rkb[NRK][8] = MM_RKB_INIT;
+__constant__ double c_rke[NRK][8] = MM_RKE_INIT;
+// host copies: which stage derivatives a pass must load (stage_need_mask)
+static constexpr double h_rka[NRK][8][8] = MM_RKA_INIT;
+static constexpr double h_rkb[NRK][8] = MM_RKB_INIT;
+static constexpr double h_rke[NRK][8] = MM_RKE_INIT;
 // stages, first-same-as-last, exponent denominator q of the step-size factor (0: fixed step)
 __constant__ int c_rks[NRK] = {7, 4, 6, 4, 3, 2};
 __constant__ int c_rkfsal[NRK] = {1, 1, 0, 0, 0, 0};
@@ -403,7 +410,9 @@ __device__ void finalize(const HotParams& p, const LaunchArgs& a) {
     const float tq = __uint_as_float(atomicExch(&st->torque_bits, 0u));
     const unsigned bad = atomicExch(&st->bad, 0u);
     st->blocks_done = 0u;
-    st->evals += 1;
+    // the stage passes before the last one have no last block (reduce_and_finish):
+    // the last pass counts their evaluations too
+    st->evals += (a.mode == LM_RKFINAL) ? p.rk_stages - 1 : (a.mode == LM_HEUN2) ? 2 : 1;
     switch (a.mode) {
         case LM_EVAL:
             st->max_torque = tq;
@@ -462,6 +471,12 @@ __device__ void finalize(const HotParams& p, const LaunchArgs& a) {
 }
 
 __device__ void reduce_and_finish(const HotParams& p, const LaunchArgs& a, Partials pt) {
+    if (a.mode == LM_RK || a.mode == LM_HEUN1) {
+        // intermediate stages reduce nothing but the non-finite flag, which the
+        // step's last pass reads: one vote per warp, an atomic only when set
+        if (__any_sync(0xffffffffu, pt.bad) && (threadIdx.x & 31) == 0) atomicOr(&p.st->bad, 1u);
+        return;
+    }
     __shared__ float r_err[32], r_tq[32];
     __shared__ double r_e[32];
     __shared__ unsigned r_bad[32];
@@ -507,13 +522,19 @@ struct StageCoefs {
     Coef e[8];          // final stage: error weights h (b_j - b*_j)
 };
 
-// Returns the magnetisation the next evaluation of this step reads at this
-// cell (m_{s+1}, m_2, the predictor or m_{n+1}); zero when there is none.
-// All loads the cell needs - m, its neighbours and the stage inputs - are
-// issued before any arithmetic, so their latencies overlap.
-__device__ __forceinline__ f3 cell_update(const HotParams& p, const LaunchArgs& a, int cur, const StageCoefs& sc,
+// What one cell reads: m at the cell and its neighbours (a missing neighbour
+// is the cell itself) and the stage inputs q0 = m_n, qk[j-1] = k_j.
+struct CellIn {
+    f3 m, mxp, mxm, myp, mym, mzp, mzm;
+    f3 q0;
+    f3 qk[6];
+};
+
+// Issues every load a cell needs, before any arithmetic, so their latencies
+// overlap.  Which k_j are read is fixed by the tableau (a.need), not by h.
+__device__ __forceinline__ void load_cell(const HotParams& p, const LaunchArgs& a, int cur,
                                           const float* __restrict__ min, long long cell, int x, int y, int z,
-                                          f3 hd, long long tstep, Partials& pt) {
+                                          CellIn& in) {
     const long long n = p.ncell;
     // neighbour indices; a missing neighbour (free boundary) points at the cell
     // itself, so its difference is zero
@@ -539,39 +560,52 @@ __device__ __forceinline__ f3 cell_update(const HotParams& p, const LaunchArgs& 
         if (z > 0) izm = cell - sz;
         else if (p.pbc[2]) izm = cell + (long long)(p.nz - 1) * sz;
     }
-    const f3 m = ld3(min, cell, n);
-    const f3 mxp = ld3(min, ixp, n), mxm = ld3(min, ixm, n);
-    f3 myp = m, mym = m, mzp = m, mzm = m;
-    if (usey) { myp = ld3(min, iyp, n); mym = ld3(min, iym, n); }
-    if (usez) { mzp = ld3(min, izp, n); mzm = ld3(min, izm, n); }
-    // stage inputs: q0 = m_n, qk[0] = k1, qk[j-1] = k_j
-    f3 q0 = mk(0.f, 0.f, 0.f);
-    f3 qk[6];
+    in.m = ld3(min, cell, n);
+    in.mxp = ld3(min, ixp, n);
+    in.mxm = ld3(min, ixm, n);
+    in.myp = in.mym = in.mzp = in.mzm = in.m;
+    if (usey) { in.myp = ld3(min, iyp, n); in.mym = ld3(min, iym, n); }
+    if (usez) { in.mzp = ld3(min, izp, n); in.mzm = ld3(min, izm, n); }
+    in.q0 = mk(0.f, 0.f, 0.f);
 #pragma unroll
-    for (int j = 0; j < 6; ++j) qk[j] = q0;
+    for (int j = 0; j < 6; ++j) in.qk[j] = in.q0;
     const int s = a.stage;
-    const bool fsal = p.rk_fsal != 0;
     switch (a.mode) {
         case LM_RK:                                  // stage s: input of s+1 = m_n + sum_{j<=s} a k_j
-            q0 = ld3(p.ms[cur], cell, n);
-            qk[0] = ld3(p.ks[cur], cell, n);
+            in.q0 = ld3(p.ms[cur], cell, n);
+            in.qk[0] = ld3(p.ks[cur], cell, n);
 #pragma unroll
             for (int j = 2; j <= 6; ++j)
-                if (j < s && sc.c[j].hi != 0.f) qk[j - 1] = ld3(p.kb[j], cell, n);
+                if (j < s && ((a.need >> j) & 1)) in.qk[j - 1] = ld3(p.kb[j], cell, n);
             break;
         case LM_RKFINAL:                             // stage S: error (and m_{n+1} without FSAL)
-            if (!fsal) q0 = ld3(p.ms[cur], cell, n);
-            qk[0] = ld3(p.ks[cur], cell, n);
+            if (!p.rk_fsal) in.q0 = ld3(p.ms[cur], cell, n);
+            in.qk[0] = ld3(p.ks[cur], cell, n);
 #pragma unroll
             for (int j = 2; j <= 6; ++j)
-                if (j < s && (sc.e[j].hi != 0.f || (!fsal && sc.c[j].hi != 0.f))) qk[j - 1] = ld3(p.kb[j], cell, n);
+                if (j < s && ((a.need >> j) & 1)) in.qk[j - 1] = ld3(p.kb[j], cell, n);
             break;
         case LM_HEUN2:
-            q0 = ld3(p.ms[cur], cell, n);
-            qk[0] = ld3(p.ks[cur], cell, n);
+            in.q0 = ld3(p.ms[cur], cell, n);
+            in.qk[0] = ld3(p.ks[cur], cell, n);
             break;
         default: break;
     }
+}
+
+// Everything that happens to one cell once its inputs and demag field are
+// known.  Returns the magnetisation the next evaluation of this step reads at
+// this cell (m_{s+1}, m_2, the predictor or m_{n+1}); zero when there is none.
+__device__ __forceinline__ f3 update_cell(const HotParams& p, const LaunchArgs& a, int cur, const StageCoefs& sc,
+                                          long long cell, const CellIn& in, f3 hd, long long tstep, Partials& pt) {
+    const long long n = p.ncell;
+    const f3 m = in.m, mxp = in.mxp, mxm = in.mxm, myp = in.myp, mym = in.mym, mzp = in.mzp, mzm = in.mzm;
+    const f3 q0 = in.q0;
+    const f3* qk = in.qk;
+    const bool usey = p.ny > 1 || p.pbc[1];
+    const bool usez = p.nz > 1 || p.pbc[2];
+    const int s = a.stage;
+    const bool fsal = p.rk_fsal != 0;
     // exchange, 6-neighbour (4 in 2-D) Laplacian (Eq. 3)
     f3 hex = p.cex[0] * ((mxp - m) + (mxm - m));
     if (usey) hex = hex + p.cex[1] * ((myp - m) + (mym - m));
@@ -693,32 +727,59 @@ __device__ __forceinline__ f3 cell_update(const HotParams& p, const LaunchArgs& 
     return next;
 }
 
+__device__ __forceinline__ f3 cell_update(const HotParams& p, const LaunchArgs& a, int cur, const StageCoefs& sc,
+                                          const float* __restrict__ min, long long cell, int x, int y, int z,
+                                          f3 hd, long long tstep, Partials& pt) {
+    CellIn in;
+    load_cell(p, a, cur, min, cell, x, y, z, in);
+    return update_cell(p, a, cur, sc, cell, in, hd, tstep, pt);
+}
+
+// The stage weights of this pass times h, split into float pairs.  Called by
+// the first warp of a block: lane l < 8 forms c[l], lane 8 + l forms e[l].
 __device__ void stage_coefs(const HotParams& p, const LaunchArgs& a, const DevState* st, StageCoefs& sc) {
-    for (int j = 0; j < 8; ++j) { sc.c[j] = {0.f, 0.f}; sc.e[j] = {0.f, 0.f}; }
+    const int lane = threadIdx.x & 31;
+    if (lane >= 16) return;
+    const int j = lane & 7;
+    const bool err = lane >= 8;
     const double h = st->h;
     const int r = p.rk;
+    double v = 0.0;
     switch (a.mode) {
         case LM_K1:
-            sc.c[1] = split(h * c_rka[r][2][1]);
+            if (!err && j == 1) v = h * c_rka[r][2][1];
             break;
         case LM_RK:
-            for (int j = 1; j <= a.stage; ++j) sc.c[j] = split(h * c_rka[r][a.stage + 1][j]);
+            if (!err && j >= 1 && j <= a.stage) v = h * c_rka[r][a.stage + 1][j];
             break;
         case LM_RKFINAL:
-            for (int j = 1; j <= 7; ++j) {
-                sc.e[j] = split(h * c_rke[r][j]);
-                sc.c[j] = split(h * c_rkb[r][j]);
-            }
+            if (j >= 1) v = h * (err ? c_rke[r][j] : c_rkb[r][j]);
             break;
         case LM_EULER:
         case LM_HEUN1:
-            sc.c[0] = split(p.dt_d);
+            if (!err && j == 0) v = p.dt_d;
             break;
         case LM_HEUN2:
-            sc.c[0] = split(0.5 * p.dt_d);
+            if (!err && j == 0) v = 0.5 * p.dt_d;
             break;
         default: break;
     }
+    const Coef c = v == 0.0 ? Coef{0.f, 0.f} : split(v);
+    if (err) sc.e[j] = c;
+    else sc.c[j] = c;
+}
+
+// Bit j set: pass (mode, stage) of tableau rk reads k_j (j >= 2).
+unsigned stage_need_mask(int rk, int mode, int stage) {
+    unsigned m = 0;
+    if (rk < 0 || rk >= NRK) return 0;
+    for (int j = 2; j <= 6 && j < stage; ++j) {
+        bool need = false;
+        if (mode == LM_RK) need = stage + 1 < 8 && h_rka[rk][stage + 1][j] != 0.0;
+        else if (mode == LM_RKFINAL) need = h_rke[rk][j] != 0.0 || h_rkb[rk][j] != 0.0;
+        if (need) m |= 1u << j;
+    }
+    return m;
 }
 
 // Inverse x pass (C2R) + crop + cell-local epilogue.  With FUSE the block
@@ -736,8 +797,8 @@ __global__ void __launch_bounds__(XS<LOGP>::NT, XS<LOGP>::MINB) k_xinv_local(Hot
     const int y0 = blockIdx.x * S::TY, z = blockIdx.y;
     DevState* st = p.st;
     if (a.mode != LM_EVAL && st->done) return;
+    if (threadIdx.x < 32) stage_coefs(p, a, st, s_sc);
     if (threadIdx.x == 0) {
-        stage_coefs(p, a, st, s_sc);
         s_cur = st->cur;
         s_tstep = (a.mode == LM_EVAL) ? p.thermal_step : st->step_index;
     }
@@ -790,31 +851,212 @@ __global__ void __launch_bounds__(XS<LOGP>::NT, XS<LOGP>::MINB) k_xinv_local(Hot
     reduce_and_finish(p, a, pt);
 }
 
-// Local terms without the magnetostatic field (demag disabled).
-__global__ void __launch_bounds__(256) k_local(HotParams p, LaunchArgs a) {
+// ---------------------------------------------------------------------------
+// x passes in the register style of the column pass (P >= 64).  A block holds
+// PAIRS row pairs; each thread owns the same radix-8 butterflies of the three
+// component lines of one pair (a complex line packs rows y and y+1), so the
+// twiddles are shared and every pass has three independent butterflies in
+// flight.  The inverse transform's first pass reads the half spectrum from
+// global memory directly (unpacking each row pair's two real spectra into one
+// complex line), and the forward transform of the next evaluation's input
+// starts from the epilogue's output.
+constexpr int XREG_MIN_LOGP = 6;
+#ifndef XR_MINB256
+#define XR_MINB256 3
+#endif
+
+template <int LOGP>
+struct XR {
+    using PL = r8::Plan8<LOGP>;
+    static constexpr int P = PL::P, NB = PL::NB, LS = PL::LS;
+    static constexpr int PAIRS = NB >= 256 ? 1 : (256 / NB > 8 ? 8 : 256 / NB);
+    static constexpr int TY = 2 * PAIRS;
+    static constexpr int NT = (PAIRS * NB + 31) / 32 * 32 < 64 ? 64 : (PAIRS * NB + 31) / 32 * 32;
+    static constexpr int HX = P / 2 + 1;
+    static constexpr int NL = 3 * PAIRS;
+    static constexpr int LASTF = PL::NPASS - 1;
+    static constexpr int MINB = NT >= 256 ? XR_MINB256 : 1024 / NT;
+    static constexpr size_t SMEM = (size_t)NL * LS * sizeof(float2);
+};
+
+// Unpack of the paired rows (A = (Z_k + conj Z_-k)/2, B = (Z_k - conj Z_-k)/(2i))
+// and transposed store to s1 [c][kx][z][y] for lines laid out as
+// line (c, q) = sm + (c*PAIRS + q)*LS, q the row pair.
+template <int LOGP>
+__device__ __forceinline__ void store_x_spectrum_r(const HotParams& p, const float2* sm, int y0, int z) {
+    using S = XR<LOGP>;
+    for (int idx = threadIdx.x; idx < S::NL * S::HX; idx += S::NT) {
+        const int l = idx / S::HX, k = idx - l * S::HX;
+        const float2 A = sm[l * S::LS + pad(k)];
+        const float2 B = cconj(sm[l * S::LS + pad((S::P - k) & (S::P - 1))]);
+        const float2 D = csub(A, B);
+        const float4 out = make_float4(0.5f * (A.x + B.x), 0.5f * (A.y + B.y), 0.5f * D.y, -0.5f * D.x);
+        const int c = l / S::PAIRS, q = l - c * S::PAIRS;
+        float2* dst = p.s1 + ((long long)(c * S::HX + k) * p.nz + z) * p.nyp + y0 + 2 * q;
+        *reinterpret_cast<float4*>(dst) = out;
+    }
+}
+
+// forward transform of the lines whose pass-0 inputs are in v (REV = false
+// order) and transposed store of the half spectrum
+template <int LOGP>
+__device__ __forceinline__ void xr_forward_store(const HotParams& p, float2* const* lines, float2 (*v)[8], int j,
+                                                 bool act, bool from_smem, int y0, int z, float2* sm) {
+    using S = XR<LOGP>;
+    r8::run<LOGP, false, false, 0, 3>(lines, v, j, act, p.tw, from_smem);
+    __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) lines[c][pad(r8::out_pos<LOGP, false, S::LASTF>(j, i))] = v[c][i];
+    }
+    __syncthreads();
+    store_x_spectrum_r<LOGP>(p, sm, y0, z);
+}
+
+template <int LOGP>
+__global__ void __launch_bounds__(XR<LOGP>::NT, XR<LOGP>::MINB) k_xfwd_r(HotParams p, LaunchArgs a) {
+    using S = XR<LOGP>;
+    extern __shared__ float2 sm[];
+    const int y0 = blockIdx.x * S::TY, z = blockIdx.y;
+    DevState* st = p.st;
+    if (!a.keep && a.mode != LM_EVAL && st->done) return;
+    const int cur = st->cur;
+    const long long n = p.ncell;
+    const bool comb = a.src == SRC_COMBINE2;
+    const float* src = comb ? p.ms[cur] : src_ptr(p, a.src, cur);
+    const float* k1 = p.ks[cur];
+    float* wout = p.mstage[0];
+    const Coef c21 = comb ? split(st->h * c_rka[p.rk][2][1]) : Coef{0.f, 0.f};
+    const int NX = p.nx, NY = p.ny;
+    const int tid = threadIdx.x;
+    int q = tid / S::NB;
+    const int j = tid - q * S::NB;
+    const bool act = q < S::PAIRS;
+    if (!act) q = 0;
+    float2* lines[3] = {sm + (0 * S::PAIRS + q) * S::LS, sm + (1 * S::PAIRS + q) * S::LS,
+                        sm + (2 * S::PAIRS + q) * S::LS};
+    const int y = y0 + 2 * q;
+    float2 v[3][8];
+    if (act) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int x = r8::in_pos<LOGP, false, 0>(j, i);
+                float2 w = make_float2(0.f, 0.f);
+                if (x < NX) {
+                    const long long i0 = (long long)c * n + ((long long)z * NY + y) * NX + x;
+                    if (y < NY) {
+                        float u = src[i0];
+                        if (comb) { u = fmaf(c21.lo, k1[i0], fmaf(c21.hi, k1[i0], u)); wout[i0] = u; }
+                        w.x = u;
+                    }
+                    if (y + 1 < NY) {
+                        float u = src[i0 + NX];
+                        if (comb) { u = fmaf(c21.lo, k1[i0 + NX], fmaf(c21.hi, k1[i0 + NX], u)); wout[i0 + NX] = u; }
+                        w.y = u;
+                    }
+                }
+                v[c][i] = w;
+            }
+    }
+    xr_forward_store<LOGP>(p, lines, v, j, act, false, y0, z, sm);
+}
+
+// Inverse x pass alone (C2R + crop): H_demag into hbuf [3][ncell], stored
+// straight from the registers of the last pass (thread j holds positions
+// j + r*P/8, so a warp stores consecutive x).
+template <int LOGP>
+__global__ void __launch_bounds__(XR<LOGP>::NT, XR<LOGP>::MINB) k_xinv_h(HotParams p, LaunchArgs a) {
+    using S = XR<LOGP>;
+    extern __shared__ float2 sm[];
+    const int y0 = blockIdx.x * S::TY, z = blockIdx.y;
+    if (a.mode != LM_EVAL && p.st->done) return;
+    const int tid = threadIdx.x;
+    int q = tid / S::NB;
+    const int j = tid - q * S::NB;
+    const bool act = q < S::PAIRS;
+    if (!act) q = 0;
+    float2* lines[3] = {sm + (0 * S::PAIRS + q) * S::LS, sm + (1 * S::PAIRS + q) * S::LS,
+                        sm + (2 * S::PAIRS + q) * S::LS};
+    float2 v[3][8];
+    if (act) {
+        const long long cs = (long long)S::HX * p.nz * p.nyp;
+        const float2* base = p.s1 + (long long)z * p.nyp + y0 + 2 * q;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int pos = r8::in_pos<LOGP, true, 0>(j, i);
+            const bool mir = pos > (S::P >> 1);
+            const int k = mir ? S::P - pos : pos;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                // (A, B) = the two rows' spectra at k; Z = A + iB, Z[-k] = conj A + i conj B
+                const float4 w = __ldg(reinterpret_cast<const float4*>(base + c * cs + (long long)k * p.nz * p.nyp));
+                v[c][i] = mir ? make_float2(w.x + w.w, w.z - w.y) : make_float2(w.x - w.w, w.y + w.z);
+            }
+        }
+    }
+    r8::run<LOGP, true, true, 0, 3>(lines, v, j, act, p.tw, false);
+    if (act) {
+        const int NX = p.nx, NY = p.ny, y = y0 + 2 * q;
+        const long long n = p.ncell;
+        const long long row = ((long long)z * NY + y) * NX;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int x = r8::out_pos<LOGP, true, S::LASTF>(j, i);
+            if (x < NX) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    if (y < NY) p.hbuf[c * n + row + x] = v[c][i].x;
+                    if (y + 1 < NY) p.hbuf[c * n + row + NX + x] = v[c][i].y;
+                }
+            }
+        }
+    }
+}
+
+// Cell pass: local terms, torque and stage update for every cell, with the
+// magnetostatic field from hbuf when demag is on (the inverse x pass wrote
+// it) and without it otherwise.
+__global__ void __launch_bounds__(256, 4) k_local(HotParams p, LaunchArgs a) {
     __shared__ StageCoefs s_sc;
-    __shared__ int s_cur;
     __shared__ long long s_tstep;
     DevState* st = p.st;
     if (a.mode != LM_EVAL && st->done) return;
-    if (threadIdx.x == 0) {
-        stage_coefs(p, a, st, s_sc);
-        s_cur = st->cur;
-        s_tstep = (a.mode == LM_EVAL) ? p.thermal_step : st->step_index;
+    // the first warp forms the stage weights while every thread issues its loads
+    if (threadIdx.x < 32) stage_coefs(p, a, st, s_sc);
+    if (threadIdx.x == 0) s_tstep = (a.mode == LM_EVAL) ? p.thermal_step : st->step_index;
+    const int cur = st->cur;
+    const float* min = src_ptr(p, a.src, cur);
+    const long long n = p.ncell;
+    const long long cell = blockIdx.x * 256ll + threadIdx.x;
+    const bool valid = cell < n;
+    const int NX = p.nx, NY = p.ny;
+    int x = 0, y = 0, z = 0;
+    if (valid) {
+        if (n <= 0xffffffffll) {                   // 32-bit division where it suffices
+            const unsigned c32 = (unsigned)cell, r = c32 / (unsigned)NX;
+            x = (int)(c32 - r * (unsigned)NX);
+            y = (int)(r % (unsigned)NY);
+            z = (int)(r / (unsigned)NY);
+        } else {
+            const long long r = cell / NX;
+            x = (int)(cell - r * NX);
+            y = (int)(r % NY);
+            z = (int)(r / NY);
+        }
+    }
+    CellIn in;
+    f3 hd = mk(0.f, 0.f, 0.f);
+    if (valid) {
+        load_cell(p, a, cur, min, cell, x, y, z, in);
+        if (p.demag) hd = ld3(p.hbuf, cell, n);
     }
     __syncthreads();
-    const int cur = s_cur;
-    const float* min = src_ptr(p, a.src, cur);
     Partials pt = {0.f, 0.f, 0.0, 0u};
-    const StageCoefs& sc = s_sc;
-    const int NX = p.nx, NY = p.ny;
-    const long long n = p.ncell;
-    for (long long cell = blockIdx.x * 256ll + threadIdx.x; cell < n; cell += (long long)gridDim.x * 256) {
-        const int x = (int)(cell % NX);
-        const long long r = cell / NX;
-        const int y = (int)(r % NY), z = (int)(r / NY);
-        cell_update(p, a, cur, sc, min, cell, x, y, z, mk(0.f, 0.f, 0.f), s_tstep, pt);
-    }
+    if (valid) update_cell(p, a, cur, s_sc, cell, in, hd, s_tstep, pt);
     reduce_and_finish(p, a, pt);
 }
 
@@ -856,6 +1098,10 @@ static cudaError_t set_attr_all() {
     if ((e = cudaFuncSetAttribute(k_yinv<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_xinv_local<L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_xinv_local<L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if constexpr (L >= XREG_MIN_LOGP) {
+        if ((e = cudaFuncSetAttribute(k_xfwd_r<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+        if ((e = cudaFuncSetAttribute(k_xinv_h<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    }
     if constexpr (L > 0) return set_attr_all<L - 1>();
     return cudaSuccess;
 }
@@ -864,6 +1110,18 @@ cudaError_t configure_hot_kernels() { return set_attr_all<12>(); }
 
 template <int L>
 static void launch_x(const HotParams& p, const LaunchArgs& a, int pass, cudaStream_t s) {
+    if constexpr (L >= XREG_MIN_LOGP) {
+        using R = XR<L>;
+        const dim3 g((p.ny + R::TY - 1) / R::TY, p.nz);
+        if (pass == PASS_XFWD) { k_xfwd_r<L><<<g, R::NT, R::SMEM, s>>>(p, a); return; }
+        if (pass == PASS_XFWD_NEXT) {
+            LaunchArgs b = a;
+            b.src = a.next_src;
+            k_xfwd_r<L><<<g, R::NT, R::SMEM, s>>>(p, b);
+            return;
+        }
+        if (pass == PASS_XINV_H) { k_xinv_h<L><<<g, R::NT, R::SMEM, s>>>(p, a); return; }
+    }
     using S = XS<L>;
     const dim3 g((p.ny + S::TY - 1) / S::TY, p.nz);
     const size_t sm = (size_t)S::NL * S::LS * sizeof(float2);
@@ -917,7 +1175,14 @@ int eval_passes(const HotParams& p, const LaunchArgs& a, int* ids) {
             ids[n++] = PASS_ZCONV;
             ids[n++] = PASS_YINV;
         }
-        ids[n++] = a.fuse ? PASS_XINV_FUSED : PASS_XINV_LOCAL;
+        if (p.logpx >= XREG_MIN_LOGP && a.mode != LM_EVAL && p.hbuf) {
+            // a step: inverse x transform, cell pass, forward x transform of the next input
+            ids[n++] = PASS_XINV_H;
+            ids[n++] = PASS_LOCAL_H;
+            if (a.fuse) ids[n++] = PASS_XFWD_NEXT;
+        } else {
+            ids[n++] = a.fuse ? PASS_XINV_FUSED : PASS_XINV_LOCAL;
+        }
     } else {
         if (a.src == SRC_COMBINE2) ids[n++] = PASS_COMBINE2;   // no x pass to fold m_2 into
         ids[n++] = PASS_LOCAL;
@@ -930,6 +1195,8 @@ cudaError_t launch_pass(const HotParams& p, const LaunchArgs& a, int pass, cudaS
         case PASS_XFWD:
         case PASS_XINV_LOCAL:
         case PASS_XINV_FUSED:
+        case PASS_XINV_H:
+        case PASS_XFWD_NEXT:
 #define MM_CALL_X(L) launch_x<L>(p, a, pass, s)
             MM_LOGP_SWITCH(p.logpx, MM_CALL_X)
 #undef MM_CALL_X
@@ -950,7 +1217,8 @@ cudaError_t launch_pass(const HotParams& p, const LaunchArgs& a, int pass, cudaS
             k_combine2<<<4 * 152, 256, 0, s>>>(p);
             break;
         case PASS_LOCAL:
-            k_local<<<(unsigned)((p.ncell + 255) / 256 < 4 * 152 ? (p.ncell + 255) / 256 : 4 * 152), 256, 0, s>>>(p, a);
+        case PASS_LOCAL_H:          // one cell per thread: every load in flight at once
+            k_local<<<(unsigned)((p.ncell + 255) / 256), 256, 0, s>>>(p, a);
             break;
         default:
             return cudaErrorInvalidValue;

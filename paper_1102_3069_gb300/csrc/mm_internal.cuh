@@ -106,6 +106,7 @@ struct HotParams {
     float* ks[2];
     float* kb[8];            // k2..k6 at kb[2..6]
     float* mstage[2];
+    float* hbuf;             // H_demag [3][ncell] between the inverse x pass and the cell pass
     const float* m_eval;
     float* h_out;
     float* tq_out;
@@ -118,20 +119,29 @@ struct LaunchArgs {
     int stage;               // RK stage (2..7)
     int fuse = 0;            // inverse-x pass also transforms the next evaluation's input
     int have_spectrum = 0;   // s1 already holds the x spectrum of this evaluation's input
+    int next_src = 0;        // Source of the next evaluation's input (transformed when fuse)
+    int keep = 0;            // that transform runs even when the run has finished (Euler/Heun
+                             // keep the spectrum of m_n in place between calls)
+    unsigned need = 0;       // bit j: the cell pass reads k_j (stage_need_mask)
 };
 
 // passes of one evaluation (the kernels of hotpath.cu), in launch order
 enum Pass : int {
     PASS_XFWD = 0, PASS_YCONV = 1, PASS_YFWD = 2, PASS_ZCONV = 3, PASS_YINV = 4,
-    PASS_XINV_LOCAL = 5, PASS_COMBINE2 = 6, PASS_LOCAL = 7, PASS_XINV_FUSED = 8, NPASS = 9
+    PASS_XINV_LOCAL = 5, PASS_COMBINE2 = 6, PASS_LOCAL = 7, PASS_XINV_FUSED = 8,
+    PASS_XINV_H = 9,        // inverse x transform alone: H_demag into hbuf
+    PASS_LOCAL_H = 10,      // cell pass with H_demag from hbuf
+    PASS_XFWD_NEXT = 11,    // forward x transform of the next evaluation's input
+    NPASS = 12
 };
 
 // hot path (hotpath.cu)
 cudaError_t launch_normalize_load(const HotParams& p, const float* m_user, cudaStream_t s);
 cudaError_t launch_copy_out(const HotParams& p, float* m_user, cudaStream_t s);
-int eval_passes(const HotParams& p, const LaunchArgs& a, int* ids);     // fills <= 5 pass ids
+int eval_passes(const HotParams& p, const LaunchArgs& a, int* ids);     // fills <= 7 pass ids
 cudaError_t launch_pass(const HotParams& p, const LaunchArgs& a, int pass, cudaStream_t s);
 cudaError_t configure_hot_kernels();
+unsigned stage_need_mask(int rk, int mode, int stage);   // host: which k_j a pass reads
 
 // kernel setup (setup.cu)
 struct SetupParams {
