@@ -277,6 +277,57 @@ const char* mm_last_error(const mm_ctx* ctx);
 /* Free the context (not the caller's workspace).  NULL is accepted. */
 void mm_destroy(mm_ctx* ctx);
 
+/*
+ * Batched ensembles (Sec. 3.1 taken to many problems: independent samples stay
+ * on the GPU and are stepped together).  The paper runs one problem at a time;
+ * the batch runs many independent ones, each with its own context, through
+ * the same passes.
+ *
+ * mm_batch_create takes n ready contexts (workspace set, material set, demag
+ * kernel built with mm_demag_kernel, demag enabled; padded FFT lengths 64 to
+ * 1024 along x and y, i.e. 32 <= n <= 512 on an open axis and n a power of
+ * two from 64 to 1024 on a periodic one; padded length at most 1024 along z)
+ * and the CUDA stream all their work then goes on (each context's stream
+ * is replaced by it).  The contexts stay owned by the caller and must outlive
+ * the batch; while in a batch they should not be stepped on their own.
+ * MM_EINVAL if a context does not qualify.
+ *
+ * Every pass of an evaluation is launched once per FFT length over all
+ * samples of that length, with the block bodies of the single-context
+ * kernels on the same block decomposition (the batched kernels read each
+ * sample's parameters from device memory, so results agree with stepping the
+ * sample alone up to float32 rounding).  A standard step is replayed from a
+ * CUDA graph.
+ *
+ * mm_batch_workspace_bytes / mm_batch_set_workspace: a small device buffer
+ * (sample descriptors, work lists, a state gather area) the caller allocates;
+ * 256-byte aligned; valid until mm_batch_destroy.
+ * mm_batch_load(m): m[i] = device SoA magnetisation of sample i (as mm_load,
+ * normalised on load).  mm_batch_store(m): copies each sample's state out.
+ * mm_batch_advance: nsteps steps of a Runge-Kutta method (MM_RK3 ... MM_RKDP)
+ * for every sample; dt_s > 0 sets every sample's step (s); tol as in
+ * mm_advance.  Asynchronous after its set-up.  The thermal field is refused.
+ * mm_batch_get_stats: out[i] = sample i's statistics (synchronises).
+ * mm_batch_relax: loads m, runs Dormand-Prince steps until every sample's
+ * max |m x H|/Ms < torque_tol (polled every 64 steps; finished samples leave
+ * the launches) or max_steps, stores m back.  steps_out[i], torque_out[i]
+ * (may be NULL): per-sample steps taken and final torque; n_converged (may
+ * be NULL): how many samples reached the bound.  MM_ENOTCONVERGED if some did
+ * not; a sample's device failure is returned as its status.
+ */
+typedef struct mm_batch mm_batch;
+int mm_batch_create(mm_batch** out, mm_ctx* const* ctxs, int n, void* cuda_stream);
+size_t mm_batch_workspace_bytes(const mm_batch* b);
+int mm_batch_set_workspace(mm_batch* b, void* dev_ptr, size_t bytes);
+int mm_batch_load(mm_batch* b, const float* const* m);
+int mm_batch_store(mm_batch* b, float* const* m);
+int mm_batch_advance(mm_batch* b, int method, long nsteps, double dt_s, double tol);
+int mm_batch_get_stats(mm_batch* b, mm_stats* out);
+int mm_batch_relax(mm_batch* b, float* const* m, double torque_tol, double err_tol, long max_steps,
+                   long* steps_out, double* torque_out, int* n_converged);
+const char* mm_batch_last_error(const mm_batch* b);
+void mm_batch_destroy(mm_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -67,6 +67,17 @@ _SIGS = {
     "mm_pass_times": (_i, [_vp, _dp, ctypes.POINTER(ctypes.c_longlong)]),
     "mm_last_error": (ctypes.c_char_p, [_vp]),
     "mm_destroy": (None, [_vp]),
+    "mm_batch_create": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _vp]),
+    "mm_batch_workspace_bytes": (_sz, [_vp]),
+    "mm_batch_set_workspace": (_i, [_vp, _vp, _sz]),
+    "mm_batch_load": (_i, [_vp, ctypes.POINTER(_vp)]),
+    "mm_batch_store": (_i, [_vp, ctypes.POINTER(_vp)]),
+    "mm_batch_advance": (_i, [_vp, _i, _l, _d, _d]),
+    "mm_batch_get_stats": (_i, [_vp, ctypes.POINTER(mm_stats)]),
+    "mm_batch_relax": (_i, [_vp, ctypes.POINTER(_vp), _d, _d, _l, ctypes.POINTER(_l), _dp,
+                            ctypes.POINTER(_i)]),
+    "mm_batch_last_error": (ctypes.c_char_p, [_vp]),
+    "mm_batch_destroy": (None, [_vp]),
 }
 
 
@@ -266,6 +277,97 @@ def mm_destroy(ctx):
     lib().mm_destroy(ctx)
 
 
+# ---- batched ensembles -------------------------------------------------------
+
+def _bcheck(b, rc):
+    if rc != MM_OK:
+        msg = lib().mm_batch_last_error(b)
+        raise MMError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _ptr_array(xs):
+    return (_vp * len(xs))(*[_ptr(x) for x in xs])
+
+
+def mm_batch_create(ctxs, stream=None):
+    b = _vp()
+    arr = (_vp * len(ctxs))(*[c.value if isinstance(c, _vp) else c for c in ctxs])
+    rc = lib().mm_batch_create(ctypes.byref(b), arr, len(ctxs), _vp(stream) if stream else None)
+    if rc != MM_OK:
+        raise MMError(rc, "mm_batch_create rejected a context")
+    return b
+
+
+def mm_batch_workspace_bytes(b):
+    return int(lib().mm_batch_workspace_bytes(b))
+
+
+def mm_batch_set_workspace(b, dev_ptr, nbytes):
+    return _bcheck(b, lib().mm_batch_set_workspace(b, _ptr(dev_ptr), int(nbytes)))
+
+
+def mm_batch_load(b, ms):
+    return _bcheck(b, lib().mm_batch_load(b, _ptr_array(ms)))
+
+
+def mm_batch_store(b, ms):
+    return _bcheck(b, lib().mm_batch_store(b, _ptr_array(ms)))
+
+
+def mm_batch_advance(b, method, nsteps, dt_s=0.0, tol=1e-6):
+    return _bcheck(b, lib().mm_batch_advance(b, int(method), int(nsteps), float(dt_s), float(tol)))
+
+
+def mm_batch_get_stats(b, n):
+    arr = (mm_stats * n)()
+    _bcheck(b, lib().mm_batch_get_stats(b, arr))
+    return [{f: getattr(s, f) for f, _ in mm_stats._fields_} for s in arr]
+
+
+def mm_batch_relax(b, ms, torque_tol=1e-4, err_tol=1e-5, max_steps=100000, check=True):
+    """Returns (rc, steps per sample, torque per sample, number converged)."""
+    n = len(ms)
+    steps = (_l * n)()
+    tq = (ctypes.c_double * n)()
+    conv = _i(0)
+    rc = lib().mm_batch_relax(b, _ptr_array(ms), float(torque_tol), float(err_tol), int(max_steps), steps,
+                              ctypes.cast(tq, _dp), ctypes.byref(conv))
+    if check and rc not in (MM_OK, MM_ENOTCONVERGED):
+        _bcheck(b, rc)
+    return rc, list(steps), list(tq), conv.value
+
+
+def mm_batch_last_error(b):
+    msg = lib().mm_batch_last_error(b)
+    return msg.decode() if msg else ""
+
+
+def mm_batch_destroy(b):
+    lib().mm_batch_destroy(b)
+
+
+class Batch:
+    """An ensemble of Solvers stepped together (all on one stream)."""
+
+    def __init__(self, solvers, stream):
+        import torch
+        self.solvers = list(solvers)
+        self.b = mm_batch_create([s.ctx for s in self.solvers], stream)
+        nbytes = mm_batch_workspace_bytes(self.b)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        base = self.workspace.data_ptr()
+        mm_batch_set_workspace(self.b, (base + 255) // 256 * 256, nbytes)
+
+    def __del__(self):
+        try:
+            if getattr(self, "b", None) is not None:
+                mm_batch_destroy(self.b)
+                self.b = None
+        except Exception:
+            pass
+
+
 # ---- convenience owner ------------------------------------------------------
 
 class Solver:
@@ -275,7 +377,7 @@ class Solver:
     mm_set_material.  ``demag=False`` disables the magnetostatic term.
     """
 
-    def __init__(self, shape, cell, pbc=(0, 0, 0), images=10, demag=True, stream=None, **material):
+    def __init__(self, shape, cell, pbc=(0, 0, 0), images=10, demag=True, stream=None, tensor=True, **material):
         import torch
         self.torch = torch
         self.shape = tuple(int(v) for v in shape)
@@ -293,7 +395,7 @@ class Solver:
         mm_set_demag(self.ctx, demag)
         self.tensor = None
         if demag:
-            self.tensor = mm_demag_kernel(self.ctx, dump=True)
+            self.tensor = mm_demag_kernel(self.ctx, dump=tensor)
 
     @property
     def mshape(self):

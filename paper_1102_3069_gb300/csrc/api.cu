@@ -152,6 +152,7 @@ void layout(mm_ctx* c) {
 }
 
 mm::DevState* dstate(mm_ctx* c) { return reinterpret_cast<mm::DevState*>(c->ws + c->off_st); }
+
 float* rk_array(mm_ctx* c, int i) {
     const size_t each = align256((size_t)3 * c->ncell * sizeof(float));
     return reinterpret_cast<float*>(c->ws + c->off_union + i * each);
@@ -239,8 +240,7 @@ __global__ void k_set_run(mm::DevState* st, double tol, double t_end, double tor
     if (st->t_end > 0.0 && st->h > st->t_end - st->t) st->h = st->t_end - st->t;
 }
 
-int eval(mm_ctx* ctx, const mm::HotParams& p, int src, int mode, int stage, bool fuse = false,
-         bool have_spectrum = false) {
+mm::LaunchArgs make_args(const mm::HotParams& p, int src, int mode, int stage, bool fuse, bool have_spectrum) {
     mm::LaunchArgs a{src, mode, stage, fuse ? 1 : 0, have_spectrum ? 1 : 0};
     // where the cell pass leaves the next evaluation's input (what a fused
     // forward x transform reads): after Euler and Heun's second stage the
@@ -255,6 +255,12 @@ int eval(mm_ctx* ctx, const mm::HotParams& p, int src, int mode, int stage, bool
         default: a.next_src = mm::SRC_CUR; break;
     }
     a.need = mm::stage_need_mask(p.rk, mode, stage);
+    return a;
+}
+
+int eval(mm_ctx* ctx, const mm::HotParams& p, int src, int mode, int stage, bool fuse = false,
+         bool have_spectrum = false) {
+    const mm::LaunchArgs a = make_args(p, src, mode, stage, fuse, have_spectrum);
     int ids[8];
     const int n = mm::eval_passes(p, a, ids);
     for (int i = 0; i < n; ++i) {
@@ -909,6 +915,389 @@ int mm_eval_heff_static(mm_ctx* ctx, const float* m, float* h_out, float* torque
     const int n = mm::eval_passes(p, a, ids);
     for (int i = 0; i < n; ++i) CK(mm::launch_pass(p, a, ids[i], ctx->stream));
     return MM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched ensembles of independent samples (mm_batch_*).  Each sample keeps
+// its own context (geometry, material, workspace slice, demag kernel, device
+// state); a batch launches every pass once per FFT length over all samples
+// of that length and replays one batched step from a CUDA graph.  Samples
+// that reach their torque bound drop out of the launches (the work lists are
+// rebuilt for the rest).
+struct mm_batch {
+    std::vector<mm_ctx*> ctx;                 // not owned
+    cudaStream_t stream = nullptr;
+    char* ws = nullptr;
+    size_t ws_size = 0;
+    size_t off_ps = 0, off_work = 0, off_states = 0, total = 0;
+    size_t max_work = 0;                      // int4 entries for all samples
+    std::vector<mm::HotParams> hp;            // host copies of the device descriptors
+    std::vector<int> active;                  // samples in the current work lists
+    struct Group { int pass, logp, nb; size_t off; };
+    std::vector<Group> groups;
+    bool groups_ready = false;
+    bool loaded = false;
+    bool k1_valid = false;
+    bool spec_m2 = false;                     // x spectrum of every sample holds m_2
+    bool h_set = false;
+    cudaGraphExec_t graph = nullptr;
+    int graph_method = 0;
+    std::string err;
+};
+
+namespace {
+
+constexpr int kBatchPasses[] = {mm::PASS_XFWD, mm::PASS_YCONV, mm::PASS_YFWD, mm::PASS_ZCONV, mm::PASS_YINV,
+                                mm::PASS_XINV_H, mm::PASS_LOCAL_H, mm::PASS_XFWD_NEXT};
+
+int bfail(mm_batch* b, int code, const std::string& msg) {
+    if (b) b->err = msg;
+    return code;
+}
+
+#define BCK(call)                                                                                  \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) return bfail(b, MM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+// blocks of every pass for the samples in `which` (work entries appended to out)
+int batch_work(mm_batch* b, const std::vector<int>& which, std::vector<int4>* out,
+               std::vector<mm_batch::Group>* groups) {
+    for (int pass : kBatchPasses) {
+        std::vector<std::vector<int4>> by_logp(16);
+        for (int i : which) {
+            int gx = 0, gy = 0;
+            BCK(mm::batch_pass_grid(b->hp[i], pass, &gx, &gy));
+            const int nblk = gx * gy;
+            if (nblk == 0) continue;
+            const int lp = mm::batch_pass_logp(b->hp[i], pass);
+            for (int by = 0; by < gy; ++by)
+                for (int bx = 0; bx < gx; ++bx) by_logp[lp].push_back(make_int4(i, bx, by, nblk));
+        }
+        for (int lp = 0; lp < 16; ++lp) {
+            if (by_logp[lp].empty()) continue;
+            if (groups) groups->push_back({pass, lp, (int)by_logp[lp].size(), out->size()});
+            out->insert(out->end(), by_logp[lp].begin(), by_logp[lp].end());
+        }
+    }
+    return MM_OK;
+}
+
+// work lists for the active samples, uploaded to the batch workspace
+int batch_build_groups(mm_batch* b) {
+    std::vector<int4> work;
+    std::vector<mm_batch::Group> groups;
+    int rc = batch_work(b, b->active, &work, &groups);
+    if (rc) return rc;
+    if (work.size() > b->max_work) return bfail(b, MM_ENOMEM, "batch work list larger than its reservation");
+    if (!work.empty())
+        BCK(cudaMemcpyAsync(b->ws + b->off_work, work.data(), work.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                            b->stream));
+    BCK(cudaStreamSynchronize(b->stream));    // the host vector goes out of scope
+    b->groups = groups;
+    b->groups_ready = true;
+    if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+    return MM_OK;
+}
+
+int batch_eval(mm_batch* b, int src, int mode, int stage, bool fuse, bool have_spectrum) {
+    const mm::LaunchArgs a = make_args(b->hp[b->active[0]], src, mode, stage, fuse, have_spectrum);
+    const mm::HotParams* ps = reinterpret_cast<const mm::HotParams*>(b->ws + b->off_ps);
+    const int4* work = reinterpret_cast<const int4*>(b->ws + b->off_work);
+    for (const auto& g : b->groups) {
+        if (g.pass == mm::PASS_XFWD && have_spectrum) continue;
+        if (g.pass == mm::PASS_XFWD_NEXT && !fuse) continue;
+        BCK(mm::launch_pass_batched(ps, work + g.off, g.nb, a, g.pass, g.logp, b->stream));
+    }
+    return MM_OK;
+}
+
+// the launches of one batched Runge-Kutta step (as enqueue_step)
+int batch_step(mm_batch* b, const RkInfo& r, bool first) {
+    int rc;
+    const int S = r.stages;
+    auto src_of = [&](int st) { return (st & 1) ? mm::SRC_STAGE1 : mm::SRC_STAGE0; };
+    if (r.fsal) {
+        if ((rc = batch_eval(b, mm::SRC_COMBINE2, mm::LM_RK, 2, true, first))) return rc;
+        for (int st = 3; st < S; ++st)
+            if ((rc = batch_eval(b, src_of(st), mm::LM_RK, st, true, true))) return rc;
+        return batch_eval(b, mm::SRC_NEXT, mm::LM_RKFINAL, S, false, true);
+    }
+    if ((rc = batch_eval(b, mm::SRC_CUR, mm::LM_K1, 1, true, false))) return rc;
+    for (int st = 2; st < S; ++st)
+        if ((rc = batch_eval(b, src_of(st), mm::LM_RK, st, true, true))) return rc;
+    return batch_eval(b, src_of(S), mm::LM_RKFINAL, S, false, true);
+}
+
+// nsteps Runge-Kutta steps of the active samples.  dt_s > 0 sets every
+// sample's step size (s); tol < 0 keeps it fixed.
+int batch_advance(mm_batch* b, int method, long nsteps, double dt_s, double tol, double torque_tol) {
+    RkInfo r;
+    if (!rk_info(method, &r)) return bfail(b, MM_EINVAL, "batches run the Runge-Kutta methods (RK3 ... RKDP)");
+    if (!b->loaded) return bfail(b, MM_ESTATE, "no state loaded (mm_batch_load)");
+    if (b->active.empty() || nsteps <= 0) return MM_OK;
+    const bool fixed_steps = !r.adaptive || tol < 0.0;
+    if (r.adaptive && !fixed_steps && tol == 0.0) return bfail(b, MM_EINVAL, "adaptive methods need tol > 0");
+    if (fixed_steps && !(dt_s > 0) && !b->h_set) return bfail(b, MM_EINVAL, "fixed steps need dt > 0");
+    if (method != b->graph_method && b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+    if (!b->groups_ready) {
+        int rc = batch_build_groups(b);
+        if (rc) return rc;
+    }
+    double dt0 = dt_s;
+    if (!(dt0 > 0) && !b->h_set) dt0 = 1e-13;        // default first step 100 fs
+    for (int i : b->active) {
+        mm_ctx* c = b->ctx[i];
+        const double tu = c->gamma0 * c->Ms;
+        if (c->T > 0.0) return bfail(b, MM_EINVAL, "batches run without the thermal field (temperature 0)");
+        mm::HotParams& p = b->hp[i];
+        p = hot_params(c, dt0 > 0 ? dt0 * tu : 0.0, true);
+        p.rk = r.index;
+        p.rk_stages = r.stages;
+        p.rk_fsal = r.fsal;
+        k_set_run<<<1, 1, 0, b->stream>>>(dstate(c), fixed_steps ? 1.0 : tol, 0.0, torque_tol > 0 ? torque_tol : 0.0,
+                                          dt0 > 0 ? dt0 * tu : 0.0, 1e-20 * tu, 1, fixed_steps ? 1 : 0);
+        BCK(cudaGetLastError());
+        c->spec = mm_ctx::SPEC_NONE;               // single-context calls start afresh after a batch
+        c->k1_valid = false;
+    }
+    if (dt0 > 0) b->h_set = true;
+    BCK(cudaMemcpyAsync(b->ws + b->off_ps, b->hp.data(), b->hp.size() * sizeof(mm::HotParams),
+                        cudaMemcpyHostToDevice, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    int rc;
+    if (r.fsal) {
+        if (dt_s > 0) b->spec_m2 = false;          // m_2 depends on h
+        if (!b->k1_valid) {
+            // k1 = f(m_n) for every sample; the same passes form m_2 and its spectrum
+            if ((rc = batch_eval(b, mm::SRC_CUR, mm::LM_K1, 1, true, false))) return rc;
+            b->k1_valid = true;
+            b->spec_m2 = true;
+        }
+    }
+    long s = 0;
+    if (r.fsal && b->spec_m2) {
+        if ((rc = batch_step(b, r, true))) return rc;
+        b->spec_m2 = false;
+        ++s;
+    }
+    if (s < nsteps) {
+        if (!b->graph) {
+            cudaGraph_t g = nullptr;
+            if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                const int erc = batch_step(b, r, false);
+                const cudaError_t ee = cudaStreamEndCapture(b->stream, &g);
+                if (erc == MM_OK && ee == cudaSuccess && g && cudaGraphInstantiate(&b->graph, g, 0) == cudaSuccess)
+                    b->graph_method = method;
+                else
+                    b->graph = nullptr;
+                if (g) cudaGraphDestroy(g);
+            }
+            cudaGetLastError();
+        }
+        for (; s < nsteps; ++s) {
+            if (b->graph) BCK(cudaGraphLaunch(b->graph, b->stream));
+            else if ((rc = batch_step(b, r, false))) return rc;
+        }
+    }
+    if (!r.fsal) b->k1_valid = false;
+    return MM_OK;
+}
+
+int batch_states(mm_batch* b, std::vector<mm::DevState>* out) {
+    const int n = (int)b->ctx.size();
+    out->resize(n);
+    mm::DevState* d = reinterpret_cast<mm::DevState*>(b->ws + b->off_states);
+    BCK(mm::launch_gather_states(reinterpret_cast<const mm::HotParams*>(b->ws + b->off_ps), d, n, b->stream));
+    BCK(cudaMemcpyAsync(out->data(), d, n * sizeof(mm::DevState), cudaMemcpyDeviceToHost, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    return MM_OK;
+}
+
+void fill_stats(mm_ctx* c, const mm::DevState& h, int method, mm_stats* s) {
+    const double tu = c->gamma0 * c->Ms;
+    s->evals = h.evals;
+    s->accepted = h.accepted;
+    s->rejected = h.rejected;
+    s->step_index = h.step_index;
+    s->t = h.t / tu;
+    s->dt = h.h / tu;
+    (void)method;
+    s->last_err = h.last_err;
+    s->max_torque = h.max_torque;
+    const double V = c->dx * c->dy * c->dz;
+    s->energy = MU0 * c->Ms * c->Ms * V * h.energy_acc;
+    s->status = h.status;
+    s->done = h.done;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mm_batch_create(mm_batch** out, mm_ctx* const* ctxs, int n, void* cuda_stream) {
+    if (!out) return MM_EINVAL;
+    *out = nullptr;
+    if (!ctxs || n < 1) return MM_EINVAL;
+    mm_batch* b = new (std::nothrow) mm_batch();
+    if (!b) return MM_ENOMEM;
+    b->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    b->ctx.assign(ctxs, ctxs + n);
+    b->hp.resize(n);
+    for (int i = 0; i < n; ++i) {
+        mm_ctx* c = ctxs[i];
+        if (!c || check_ready(c, true) != MM_OK || !c->demag) {
+            delete b;
+            return MM_EINVAL;
+        }
+        c->stream = b->stream;                     // every sample's work goes on the batch stream
+        b->hp[i] = hot_params(c, 0.0, false);
+        b->hp[i].rk_stages = 7;
+        if (!mm::batch_supported(b->hp[i])) {
+            delete b;
+            return MM_EINVAL;
+        }
+    }
+    std::vector<int> all(n);
+    for (int i = 0; i < n; ++i) all[i] = i;
+    std::vector<int4> work;
+    if (batch_work(b, all, &work, nullptr) != MM_OK) {
+        delete b;
+        return MM_EINVAL;
+    }
+    b->max_work = work.size();
+    size_t off = 0;
+    b->off_ps = off; off += align256((size_t)n * sizeof(mm::HotParams));
+    b->off_work = off; off += align256(b->max_work * sizeof(int4));
+    b->off_states = off; off += align256((size_t)n * sizeof(mm::DevState));
+    b->total = off;
+    b->active = all;
+    *out = b;
+    return MM_OK;
+}
+
+size_t mm_batch_workspace_bytes(const mm_batch* b) { return b ? b->total : 0; }
+
+int mm_batch_set_workspace(mm_batch* b, void* dev_ptr, size_t bytes) {
+    if (!b || !dev_ptr) return bfail(b, MM_EINVAL, "null workspace");
+    if (reinterpret_cast<uintptr_t>(dev_ptr) & 255) return bfail(b, MM_EINVAL, "workspace must be 256-byte aligned");
+    if (bytes < b->total) return bfail(b, MM_ENOMEM, "workspace smaller than mm_batch_workspace_bytes()");
+    b->ws = static_cast<char*>(dev_ptr);
+    b->ws_size = bytes;
+    b->groups_ready = false;
+    if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+    BCK(cudaMemcpyAsync(b->ws + b->off_ps, b->hp.data(), b->hp.size() * sizeof(mm::HotParams),
+                        cudaMemcpyHostToDevice, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    return MM_OK;
+}
+
+int mm_batch_load(mm_batch* b, const float* const* m) {
+    if (!b || !m) return MM_EINVAL;
+    if (!b->ws) return bfail(b, MM_ENOMEM, "workspace not set (mm_batch_set_workspace)");
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        const int rc = mm_load(b->ctx[i], m[i], 0.0, 0);
+        if (rc) return bfail(b, rc, "sample " + std::to_string(i) + ": " + b->ctx[i]->err);
+    }
+    std::vector<int> all(b->ctx.size());
+    for (size_t i = 0; i < all.size(); ++i) all[i] = (int)i;
+    if (b->active != all || !b->groups_ready) {
+        b->active = all;
+        b->groups_ready = false;
+    }
+    b->loaded = true;
+    b->k1_valid = false;
+    b->spec_m2 = false;
+    b->h_set = false;
+    return MM_OK;
+}
+
+int mm_batch_store(mm_batch* b, float* const* m) {
+    if (!b || !m) return MM_EINVAL;
+    for (size_t i = 0; i < b->ctx.size(); ++i) {
+        const int rc = mm_store(b->ctx[i], m[i]);
+        if (rc) return bfail(b, rc, "sample " + std::to_string(i) + ": " + b->ctx[i]->err);
+    }
+    return MM_OK;
+}
+
+int mm_batch_advance(mm_batch* b, int method, long nsteps, double dt_s, double tol) {
+    if (!b) return MM_EINVAL;
+    if (!b->ws) return bfail(b, MM_ENOMEM, "workspace not set (mm_batch_set_workspace)");
+    if (nsteps < 0 || !std::isfinite(dt_s) || !std::isfinite(tol)) return bfail(b, MM_EINVAL, "bad arguments");
+    return batch_advance(b, method, nsteps, dt_s, tol, 0.0);
+}
+
+int mm_batch_get_stats(mm_batch* b, mm_stats* out) {
+    if (!b || !out) return MM_EINVAL;
+    if (!b->ws) return bfail(b, MM_ENOMEM, "workspace not set");
+    std::vector<mm::DevState> h;
+    int rc = batch_states(b, &h);
+    if (rc) return rc;
+    for (size_t i = 0; i < b->ctx.size(); ++i) fill_stats(b->ctx[i], h[i], b->graph_method, &out[i]);
+    return MM_OK;
+}
+
+int mm_batch_relax(mm_batch* b, float* const* m, double torque_tol, double err_tol, long max_steps,
+                   long* steps_out, double* torque_out, int* n_converged) {
+    if (!b || !m) return MM_EINVAL;
+    if (!(torque_tol > 0) || !(err_tol > 0) || max_steps < 0) return bfail(b, MM_EINVAL, "bad relax arguments");
+    int rc = mm_batch_load(b, m);
+    if (rc) return rc;
+    const int n = (int)b->ctx.size();
+    std::vector<mm::DevState> h;
+    std::vector<char> finished(n, 0);
+    long done_steps = 0;
+    bool first = true;
+    while (true) {
+        const long chunk = (max_steps - done_steps) < 64 ? (max_steps - done_steps) : 64;
+        if ((rc = batch_advance(b, MM_RKDP, chunk, first ? 1e-13 : 0.0, err_tol, torque_tol))) return rc;
+        first = false;
+        done_steps += chunk;
+        if ((rc = batch_states(b, &h))) return rc;
+        std::vector<int> still;
+        for (int i : b->active) {
+            if (h[i].status) return bfail(b, h[i].status, "sample " + std::to_string(i) + " failed on the device");
+            if (h[i].done) finished[i] = 1;
+            else still.push_back(i);
+        }
+        if (still.empty() || done_steps >= max_steps) break;
+        if (still.size() != b->active.size()) {
+            b->active = still;                       // finished samples leave the launches
+            if ((rc = batch_build_groups(b))) return rc;
+        }
+    }
+    if ((rc = mm_batch_store(b, m))) return rc;
+    BCK(cudaStreamSynchronize(b->stream));
+    int conv = 0;
+    for (int i = 0; i < n; ++i) {
+        const bool ok = finished[i] && h[i].max_torque < torque_tol;
+        conv += ok;
+        if (steps_out) steps_out[i] = (long)(h[i].accepted + h[i].rejected);
+        if (torque_out) torque_out[i] = h[i].max_torque;
+    }
+    if (n_converged) *n_converged = conv;
+    // the next call starts from every sample again
+    std::vector<int> all(n);
+    for (int i = 0; i < n; ++i) all[i] = i;
+    b->active = all;
+    b->groups_ready = false;
+    if (conv < n) return bfail(b, MM_ENOTCONVERGED, std::to_string(n - conv) + " samples did not reach the torque bound");
+    return MM_OK;
+}
+
+const char* mm_batch_last_error(const mm_batch* b) {
+    if (!b) return "null batch";
+    return b->err.c_str();
+}
+
+void mm_batch_destroy(mm_batch* b) {
+    if (!b) return;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    delete b;
 }
 
 }  // extern "C"

@@ -154,6 +154,17 @@ __device__ __forceinline__ const float* src_ptr(const HotParams& p, int src, int
     }
 }
 
+// A block's launch parameters, copied once into shared memory: every field
+// the block reads afterwards is a shared-memory load, whether the launch
+// covers one sample (ps[0]) or many (ps[sample]).
+__device__ __forceinline__ void load_params(const HotParams* __restrict__ src, HotParams* dst) {
+    static_assert(sizeof(HotParams) % 4 == 0, "parameter block copied in 32-bit words");
+    const int* s = reinterpret_cast<const int*>(src);
+    int* d = reinterpret_cast<int*>(dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(HotParams) / 4); i += blockDim.x) d[i] = __ldg(s + i);
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // compile-time shapes of the passes (shared with the host through fft32.cuh)
 template <int LOGP>
@@ -261,7 +272,7 @@ __device__ __forceinline__ int last_out_pos(int j, int i) {
 }
 
 template <int LOGP, int MODE>
-__global__ void __launch_bounds__(CC<LOGP>::NT, CC<LOGP>::NT <= 256 ? 3 : 1) k_colconv(HotParams p, LaunchArgs a) {
+__device__ __forceinline__ void colconv_body(const HotParams& p, const LaunchArgs& a, int bx, int by) {
     using S = CC<LOGP>;
     constexpr int NV = r8::nval<LOGP>();
     extern __shared__ float2 sm[];
@@ -277,15 +288,15 @@ __global__ void __launch_bounds__(CC<LOGP>::NT, CC<LOGP>::NT <= 256 ? 3 : 1) k_c
     long long base, cstride;
     float2* buf;
     if constexpr (MODE == 0) {
-        kx = blockIdx.x * S::COLS + cl;
+        kx = bx * S::COLS + cl;
         valid = kx < HX;
         base = (long long)kx * p.nyp;
         cstride = (long long)HX * p.nyp;
         nvalid = p.ny;
         buf = p.s1;
     } else {
-        kx = blockIdx.x;
-        ky = blockIdx.y * S::COLS + cl;
+        kx = bx;
+        ky = by * S::COLS + cl;
         valid = ky < PY;
         base = ((long long)kx * PY + ky) * p.nzp;
         cstride = (long long)HX * PY * p.nzp;
@@ -347,15 +358,27 @@ __global__ void __launch_bounds__(CC<LOGP>::NT, CC<LOGP>::NT <= 256 ? 3 : 1) k_c
     }
 }
 
+template <int LOGP, int MODE>
+__global__ void __launch_bounds__(CC<LOGP>::NT, CC<LOGP>::NT <= 256 ? 3 : 1) k_colconv(HotParams p, LaunchArgs a) {
+    colconv_body<LOGP, MODE>(p, a, blockIdx.x, blockIdx.y);
+}
+template <int LOGP, int MODE>
+__global__ void __launch_bounds__(CC<LOGP>::NT, CC<LOGP>::NT <= 256 ? 3 : 1)
+kb_colconv(const HotParams* __restrict__ ps, const int4* __restrict__ work, LaunchArgs a) {
+    const int4 w = work[blockIdx.x];
+    __shared__ HotParams s_hp;
+    load_params(ps + w.x, &s_hp);
+    colconv_body<LOGP, MODE>(s_hp, a, w.y, w.z);
+}
+
 // ---------------------------------------------------------------------------
 // 3-D: y forward pass.  s1 [c][kx][z][y]  ->  s2 [c][kx][ky][z]
 template <int LOGP>
-__global__ void __launch_bounds__(CS<LOGP, tz_of(LOGP)>::NT, CS<LOGP, tz_of(LOGP)>::MINB)
-k_yfwd(HotParams p, LaunchArgs a) {
+__device__ __forceinline__ void yfwd_body(const HotParams& p, const LaunchArgs& a, int bx, int by) {
     constexpr int TZ = tz_of(LOGP);
     using S = CS<LOGP, TZ>;
     extern __shared__ float2 sm[];
-    const int kx = blockIdx.x, z0 = blockIdx.y * TZ;
+    const int kx = bx, z0 = by * TZ;
     if (a.mode != LM_EVAL && p.st->done) return;
     const int HX = p.hx, NY = p.ny, NZ = p.nz;
     for (int idx = threadIdx.x; idx < S::NL * S::P; idx += S::NT) {
@@ -373,14 +396,27 @@ k_yfwd(HotParams p, LaunchArgs a) {
     }
 }
 
-// 3-D: y inverse pass.  s2 [c][kx][ky][z]  ->  s1 [c][kx][z][y]
 template <int LOGP>
 __global__ void __launch_bounds__(CS<LOGP, tz_of(LOGP)>::NT, CS<LOGP, tz_of(LOGP)>::MINB)
-k_yinv(HotParams p, LaunchArgs a) {
+k_yfwd(HotParams p, LaunchArgs a) {
+    yfwd_body<LOGP>(p, a, blockIdx.x, blockIdx.y);
+}
+template <int LOGP>
+__global__ void __launch_bounds__(CS<LOGP, tz_of(LOGP)>::NT, CS<LOGP, tz_of(LOGP)>::MINB)
+kb_yfwd(const HotParams* __restrict__ ps, const int4* __restrict__ work, LaunchArgs a) {
+    const int4 w = work[blockIdx.x];
+    __shared__ HotParams s_hp;
+    load_params(ps + w.x, &s_hp);
+    yfwd_body<LOGP>(s_hp, a, w.y, w.z);
+}
+
+// 3-D: y inverse pass.  s2 [c][kx][ky][z]  ->  s1 [c][kx][z][y]
+template <int LOGP>
+__device__ __forceinline__ void yinv_body(const HotParams& p, const LaunchArgs& a, int bx, int by) {
     constexpr int TZ = tz_of(LOGP);
     using S = CS<LOGP, TZ>;
     extern __shared__ float2 sm[];
-    const int kx = blockIdx.x, z0 = blockIdx.y * TZ;
+    const int kx = bx, z0 = by * TZ;
     if (a.mode != LM_EVAL && p.st->done) return;
     const int HX = p.hx, NY = p.ny, NZ = p.nz;
     for (int idx = threadIdx.x; idx < S::NL * S::P; idx += S::NT) {
@@ -394,6 +430,20 @@ k_yinv(HotParams p, LaunchArgs a) {
         const int c = l / TZ, zt = l - c * TZ, z = z0 + zt;
         if (y < NY && z < NZ) p.s1[((long long)(c * HX + kx) * NZ + z) * p.nyp + y] = sm[l * S::LS + pad(y)];
     }
+}
+
+template <int LOGP>
+__global__ void __launch_bounds__(CS<LOGP, tz_of(LOGP)>::NT, CS<LOGP, tz_of(LOGP)>::MINB)
+k_yinv(HotParams p, LaunchArgs a) {
+    yinv_body<LOGP>(p, a, blockIdx.x, blockIdx.y);
+}
+template <int LOGP>
+__global__ void __launch_bounds__(CS<LOGP, tz_of(LOGP)>::NT, CS<LOGP, tz_of(LOGP)>::MINB)
+kb_yinv(const HotParams* __restrict__ ps, const int4* __restrict__ work, LaunchArgs a) {
+    const int4 w = work[blockIdx.x];
+    __shared__ HotParams s_hp;
+    load_params(ps + w.x, &s_hp);
+    yinv_body<LOGP>(s_hp, a, w.y, w.z);
 }
 
 // ---------------------------------------------------------------------------
@@ -470,7 +520,8 @@ __device__ void finalize(const HotParams& p, const LaunchArgs& a) {
     }
 }
 
-__device__ void reduce_and_finish(const HotParams& p, const LaunchArgs& a, Partials pt) {
+// nblk: the blocks of this evaluation that report (the last of them runs finalize)
+__device__ void reduce_and_finish(const HotParams& p, const LaunchArgs& a, Partials pt, int nblk) {
     if (a.mode == LM_RK || a.mode == LM_HEUN1) {
         // intermediate stages reduce nothing but the non-finite flag, which the
         // step's last pass reads: one vote per warp, an atomic only when set
@@ -506,7 +557,7 @@ __device__ void reduce_and_finish(const HotParams& p, const LaunchArgs& a, Parti
         if (pt.bad) atomicOr(&st->bad, 1u);
         __threadfence();
         const unsigned prev = atomicAdd(&st->blocks_done, 1u);
-        s_last = (prev == gridDim.x * gridDim.y - 1);
+        s_last = (prev == (unsigned)nblk - 1u);
     }
     __syncthreads();
     if (s_last && threadIdx.x == 0) {
@@ -848,7 +899,7 @@ __global__ void __launch_bounds__(XS<LOGP>::NT, XS<LOGP>::MINB) k_xinv_local(Hot
         fft_lines<LOGP, S::NL, false>(sm, p.tw);
         store_x_spectrum<LOGP>(p, sm, y0, z);
     }
-    reduce_and_finish(p, a, pt);
+    reduce_and_finish(p, a, pt, gridDim.x * gridDim.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -861,6 +912,9 @@ __global__ void __launch_bounds__(XS<LOGP>::NT, XS<LOGP>::MINB) k_xinv_local(Hot
 // complex line), and the forward transform of the next evaluation's input
 // starts from the epilogue's output.
 constexpr int XREG_MIN_LOGP = 6;
+// FFT lengths the batched passes are compiled for: 2^6..2^10 along x and y,
+// 2^1..2^10 along z
+constexpr int BATCH_MIN_LOGP = 6, BATCH_MAX_LOGP = 10;
 #ifndef XR_MINB256
 #define XR_MINB256 3
 #endif
@@ -916,10 +970,10 @@ __device__ __forceinline__ void xr_forward_store(const HotParams& p, float2* con
 }
 
 template <int LOGP>
-__global__ void __launch_bounds__(XR<LOGP>::NT, XR<LOGP>::MINB) k_xfwd_r(HotParams p, LaunchArgs a) {
+__device__ __forceinline__ void xfwd_r_body(const HotParams& p, const LaunchArgs& a, int bx, int by) {
     using S = XR<LOGP>;
     extern __shared__ float2 sm[];
-    const int y0 = blockIdx.x * S::TY, z = blockIdx.y;
+    const int y0 = bx * S::TY, z = by;
     DevState* st = p.st;
     if (!a.keep && a.mode != LM_EVAL && st->done) return;
     const int cur = st->cur;
@@ -965,14 +1019,27 @@ __global__ void __launch_bounds__(XR<LOGP>::NT, XR<LOGP>::MINB) k_xfwd_r(HotPara
     xr_forward_store<LOGP>(p, lines, v, j, act, false, y0, z, sm);
 }
 
+template <int LOGP>
+__global__ void __launch_bounds__(XR<LOGP>::NT, XR<LOGP>::MINB) k_xfwd_r(HotParams p, LaunchArgs a) {
+    xfwd_r_body<LOGP>(p, a, blockIdx.x, blockIdx.y);
+}
+template <int LOGP>
+__global__ void __launch_bounds__(XR<LOGP>::NT, XR<LOGP>::MINB)
+kb_xfwd_r(const HotParams* __restrict__ ps, const int4* __restrict__ work, LaunchArgs a) {
+    const int4 w = work[blockIdx.x];
+    __shared__ HotParams s_hp;
+    load_params(ps + w.x, &s_hp);
+    xfwd_r_body<LOGP>(s_hp, a, w.y, w.z);
+}
+
 // Inverse x pass alone (C2R + crop): H_demag into hbuf [3][ncell], stored
 // straight from the registers of the last pass (thread j holds positions
 // j + r*P/8, so a warp stores consecutive x).
 template <int LOGP>
-__global__ void __launch_bounds__(XR<LOGP>::NT, XR<LOGP>::MINB) k_xinv_h(HotParams p, LaunchArgs a) {
+__device__ __forceinline__ void xinv_h_body(const HotParams& p, const LaunchArgs& a, int bx, int by) {
     using S = XR<LOGP>;
     extern __shared__ float2 sm[];
-    const int y0 = blockIdx.x * S::TY, z = blockIdx.y;
+    const int y0 = bx * S::TY, z = by;
     if (a.mode != LM_EVAL && p.st->done) return;
     const int tid = threadIdx.x;
     int q = tid / S::NB;
@@ -1017,10 +1084,23 @@ __global__ void __launch_bounds__(XR<LOGP>::NT, XR<LOGP>::MINB) k_xinv_h(HotPara
     }
 }
 
+template <int LOGP>
+__global__ void __launch_bounds__(XR<LOGP>::NT, XR<LOGP>::MINB) k_xinv_h(HotParams p, LaunchArgs a) {
+    xinv_h_body<LOGP>(p, a, blockIdx.x, blockIdx.y);
+}
+template <int LOGP>
+__global__ void __launch_bounds__(XR<LOGP>::NT, XR<LOGP>::MINB)
+kb_xinv_h(const HotParams* __restrict__ ps, const int4* __restrict__ work, LaunchArgs a) {
+    const int4 w = work[blockIdx.x];
+    __shared__ HotParams s_hp;
+    load_params(ps + w.x, &s_hp);
+    xinv_h_body<LOGP>(s_hp, a, w.y, w.z);
+}
+
 // Cell pass: local terms, torque and stage update for every cell, with the
 // magnetostatic field from hbuf when demag is on (the inverse x pass wrote
 // it) and without it otherwise.
-__global__ void __launch_bounds__(256, 4) k_local(HotParams p, LaunchArgs a) {
+__device__ __forceinline__ void local_body(const HotParams& p, const LaunchArgs& a, int bx, int nblk) {
     __shared__ StageCoefs s_sc;
     __shared__ long long s_tstep;
     DevState* st = p.st;
@@ -1031,7 +1111,7 @@ __global__ void __launch_bounds__(256, 4) k_local(HotParams p, LaunchArgs a) {
     const int cur = st->cur;
     const float* min = src_ptr(p, a.src, cur);
     const long long n = p.ncell;
-    const long long cell = blockIdx.x * 256ll + threadIdx.x;
+    const long long cell = bx * 256ll + threadIdx.x;
     const bool valid = cell < n;
     const int NX = p.nx, NY = p.ny;
     int x = 0, y = 0, z = 0;
@@ -1057,7 +1137,18 @@ __global__ void __launch_bounds__(256, 4) k_local(HotParams p, LaunchArgs a) {
     __syncthreads();
     Partials pt = {0.f, 0.f, 0.0, 0u};
     if (valid) update_cell(p, a, cur, s_sc, cell, in, hd, s_tstep, pt);
-    reduce_and_finish(p, a, pt);
+    reduce_and_finish(p, a, pt, nblk);
+}
+__global__ void __launch_bounds__(256, 4) k_local(HotParams p, LaunchArgs a) {
+    local_body(p, a, blockIdx.x, gridDim.x);
+}
+// batched: work[b] = (sample, block of that sample, -, blocks of that sample)
+__global__ void __launch_bounds__(256, 4)
+kb_local(const HotParams* __restrict__ ps, const int4* __restrict__ work, LaunchArgs a) {
+    const int4 w = work[blockIdx.x];
+    __shared__ HotParams s_hp;
+    load_params(ps + w.x, &s_hp);
+    local_body(s_hp, a, w.y, w.w);
 }
 
 // ---------------------------------------------------------------------------
@@ -1101,6 +1192,16 @@ static cudaError_t set_attr_all() {
     if constexpr (L >= XREG_MIN_LOGP) {
         if ((e = cudaFuncSetAttribute(k_xfwd_r<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
         if ((e = cudaFuncSetAttribute(k_xinv_h<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    }
+    if constexpr (L >= BATCH_MIN_LOGP && L <= BATCH_MAX_LOGP) {
+        if ((e = cudaFuncSetAttribute(kb_xfwd_r<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+        if ((e = cudaFuncSetAttribute(kb_xinv_h<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+        if ((e = cudaFuncSetAttribute(kb_colconv<L, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+        if ((e = cudaFuncSetAttribute(kb_yfwd<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+        if ((e = cudaFuncSetAttribute(kb_yinv<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    }
+    if constexpr (L >= 1 && L <= BATCH_MAX_LOGP) {
+        if ((e = cudaFuncSetAttribute(kb_colconv<L, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     }
     if constexpr (L > 0) return set_attr_all<L - 1>();
     return cudaSuccess;
@@ -1223,6 +1324,130 @@ cudaError_t launch_pass(const HotParams& p, const LaunchArgs& a, int pass, cudaS
         default:
             return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Batched passes.  One launch covers the blocks of many independent samples
+// that share the pass's FFT length; work[b] = (sample, block x, block y,
+// blocks of that sample in this pass).  The block bodies are the ones of the
+// single-sample kernels, so a sample's result does not depend on the batch.
+
+int batch_pass_logp(const HotParams& p, int pass) {
+    switch (pass) {
+        case PASS_XFWD: case PASS_XFWD_NEXT: case PASS_XINV_H: return p.logpx;
+        case PASS_YCONV: case PASS_YFWD: case PASS_YINV: return p.logpy;
+        case PASS_ZCONV: return p.logpz;
+        default: return 0;
+    }
+}
+
+bool batch_supported(const HotParams& p) {
+    if (!p.demag) return false;
+    if (p.logpx < BATCH_MIN_LOGP || p.logpx > BATCH_MAX_LOGP) return false;
+    if (p.logpy < BATCH_MIN_LOGP || p.logpy > BATCH_MAX_LOGP) return false;
+    if (p.nz > 1 && (p.logpz < 1 || p.logpz > BATCH_MAX_LOGP)) return false;
+    return true;
+}
+
+cudaError_t batch_pass_grid(const HotParams& p, int pass, int* gx, int* gy) {
+    *gx = 0;
+    *gy = 0;
+    switch (pass) {
+        case PASS_XFWD: case PASS_XFWD_NEXT: case PASS_XINV_H:
+#define MM_G(L) { *gx = (p.ny + XR<L>::TY - 1) / XR<L>::TY; *gy = p.nz; }
+            MM_LOGP_SWITCH(p.logpx, MM_G)
+#undef MM_G
+            return cudaSuccess;
+        case PASS_YCONV:
+            if (p.nz != 1) return cudaSuccess;
+#define MM_G(L) { *gx = (p.hx + CC<L>::COLS - 1) / CC<L>::COLS; *gy = 1; }
+            MM_LOGP_SWITCH(p.logpy, MM_G)
+#undef MM_G
+            return cudaSuccess;
+        case PASS_YFWD: case PASS_YINV:
+            if (p.nz == 1) return cudaSuccess;
+            *gx = p.hx;
+            *gy = (p.nz + tz_of(p.logpy) - 1) / tz_of(p.logpy);
+            return cudaSuccess;
+        case PASS_ZCONV:
+            if (p.nz == 1) return cudaSuccess;
+#define MM_G(L) { *gx = p.hx; *gy = (p.py + CC<L>::COLS - 1) / CC<L>::COLS; }
+            MM_LOGP_SWITCH(p.logpz, MM_G)
+#undef MM_G
+            return cudaSuccess;
+        case PASS_LOCAL_H:
+            *gx = (int)((p.ncell + 255) / 256);
+            *gy = 1;
+            return cudaSuccess;
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+template <int L>
+static cudaError_t launch_b(const HotParams* ps, const int4* work, int nb, const LaunchArgs& a, int pass,
+                            cudaStream_t s) {
+    if constexpr (L >= BATCH_MIN_LOGP && L <= BATCH_MAX_LOGP) {
+        switch (pass) {
+            case PASS_XFWD:
+                kb_xfwd_r<L><<<nb, XR<L>::NT, XR<L>::SMEM, s>>>(ps, work, a);
+                return cudaSuccess;
+            case PASS_XFWD_NEXT: {
+                LaunchArgs b = a;
+                b.src = a.next_src;
+                kb_xfwd_r<L><<<nb, XR<L>::NT, XR<L>::SMEM, s>>>(ps, work, b);
+                return cudaSuccess;
+            }
+            case PASS_XINV_H:
+                kb_xinv_h<L><<<nb, XR<L>::NT, XR<L>::SMEM, s>>>(ps, work, a);
+                return cudaSuccess;
+            case PASS_YCONV:
+                kb_colconv<L, 0><<<nb, CC<L>::NT, (size_t)3 * CC<L>::COLS * CC<L>::LS * sizeof(float2), s>>>(ps, work, a);
+                return cudaSuccess;
+            case PASS_YFWD: case PASS_YINV: {
+                using S = CS<L, tz_of(L)>;
+                const size_t sm = (size_t)S::NL * S::LS * sizeof(float2);
+                if (pass == PASS_YFWD) kb_yfwd<L><<<nb, S::NT, sm, s>>>(ps, work, a);
+                else kb_yinv<L><<<nb, S::NT, sm, s>>>(ps, work, a);
+                return cudaSuccess;
+            }
+            default: break;
+        }
+    }
+    if constexpr (L >= 1 && L <= BATCH_MAX_LOGP) {
+        if (pass == PASS_ZCONV) {
+            kb_colconv<L, 1><<<nb, CC<L>::NT, (size_t)3 * CC<L>::COLS * CC<L>::LS * sizeof(float2), s>>>(ps, work, a);
+            return cudaSuccess;
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_pass_batched(const HotParams* ps, const int4* work, int nb, const LaunchArgs& a, int pass,
+                                int logp, cudaStream_t s) {
+    if (nb <= 0) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    if (pass == PASS_LOCAL_H) {
+        kb_local<<<nb, 256, 0, s>>>(ps, work, a);
+        return cudaGetLastError();
+    }
+#define MM_CALL_B(L) e = launch_b<L>(ps, work, nb, a, pass, s)
+    MM_LOGP_SWITCH(logp, MM_CALL_B)
+#undef MM_CALL_B
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+// copies every sample's DevState into one array (one thread per sample)
+__global__ void k_gather_states(const HotParams* __restrict__ ps, DevState* out, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = *ps[i].st;
+}
+
+cudaError_t launch_gather_states(const HotParams* ps, DevState* out, int n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_gather_states<<<(n + 127) / 128, 128, 0, s>>>(ps, out, n);
     return cudaGetLastError();
 }
 

@@ -143,6 +143,14 @@ cudaError_t launch_pass(const HotParams& p, const LaunchArgs& a, int pass, cudaS
 cudaError_t configure_hot_kernels();
 unsigned stage_need_mask(int rk, int mode, int stage);   // host: which k_j a pass reads
 
+// batched passes over independent samples (hotpath.cu)
+bool batch_supported(const HotParams& p);
+int batch_pass_logp(const HotParams& p, int pass);
+cudaError_t batch_pass_grid(const HotParams& p, int pass, int* gx, int* gy);
+cudaError_t launch_pass_batched(const HotParams* ps, const int4* work, int nb, const LaunchArgs& a, int pass,
+                                int logp, cudaStream_t s);
+cudaError_t launch_gather_states(const HotParams* ps, DevState* out, int n, cudaStream_t s);
+
 // kernel setup (setup.cu)
 struct SetupParams {
     int nx, ny, nz;

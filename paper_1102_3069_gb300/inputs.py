@@ -18,7 +18,13 @@ measured on:
                       Heun with dt = 50 fs;
 * ``table1_N2`` / ``table1_N3``  square and cubic grids of the Euler-step
                       timing table, 4 nm cells with the film_1024x1024
-                      material.
+                      material;
+* ``ensemble(n)``     independent samples of the batched ensemble: nx, ny
+                      uniform in 32..256, nz uniform in 1..4, 4 nm cells,
+                      Ms U[4e5, 1.4e6] A/m, A U[5e-12, 2e-11] J/m, Ku
+                      U[0, 5e4] J/m^3, easy axis and field direction uniform
+                      on the sphere, |B| U[0, 50] mT, alpha 0.02, open
+                      boundaries, random unit vectors.
 """
 
 import numpy as np
@@ -108,3 +114,22 @@ def workload(name, seed=0):
         mat = dict(Ms=8e5, Aex=1.3e-11, Ku=5e3, easy_axis=(1.0, 0.0, 0.0), alpha=0.01, B=(0.0, 0.0, 0.01))
         return dict(name=name, shape=shape, cell=cell, pbc=(0, 0, 0), material=mat, m=random_unit(shape, seed))
     raise KeyError(name)
+
+
+def ensemble(n, seed=0, nmin=32, nmax=256, nzmax=4, alpha=0.02):
+    """n independent samples (dicts with shape, cell, pbc, material, m_seed);
+    m = random_unit(shape, m_seed) is drawn on demand."""
+    g = rng(seed + 2000)
+    out = []
+    for i in range(n):
+        nx, ny = (int(v) for v in g.integers(nmin, nmax + 1, size=2))
+        nz = int(g.integers(1, nzmax + 1))
+        Ms = float(g.uniform(4e5, 1.4e6))
+        A = float(g.uniform(5e-12, 2e-11))
+        Ku = float(g.uniform(0.0, 5e4))
+        u = tuple(float(v) for v in random_direction(g))
+        B = tuple(float(v) for v in g.uniform(0.0, 0.05) * random_direction(g))
+        mat = dict(Ms=Ms, Aex=A, Ku=Ku, easy_axis=u, alpha=alpha, B=B)
+        out.append(dict(shape=(nx, ny, nz), cell=(4e-9, 4e-9, 4e-9), pbc=(0, 0, 0), material=mat,
+                        m_seed=seed * 100003 + i))
+    return out
