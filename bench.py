@@ -169,8 +169,9 @@ def algorithmic_bytes(nx, ny):
     }
 
 
-def algorithmic_bytes_3d(shape, pz, images_axes=(True, True, False)):
-    """Bytes per pass for the 3-D sequence (x fused, y forward, z column, y inverse), Heun stages."""
+def algorithmic_bytes_3d(shape, pz, images_axes=(True, True, False), axes=True):
+    """Bytes per pass for the 3-D sequence (x fused, y forward, z column, y inverse), Heun stages;
+    axes: the cell pass also reads a per-cell easy axis (12 B per cell)."""
     nx, ny, nz = shape
     N = nx * ny * nz
     px = nx if images_axes[0] else 2 * nx
@@ -180,15 +181,16 @@ def algorithmic_bytes_3d(shape, pz, images_axes=(True, True, False)):
     s2 = 3 * hx * py * nz * 8
     kern = 6 * hx * (py // 2 + 1) * (pz // 2 + 1) * 4
     m = 12 * N
-    heun1 = s1 + m + 2 * m + s1            # k1 and the predictor written, next spectrum written
-    heun2 = s1 + m + 2 * m + m + s1        # m_n and k1 read, m_{n+1} written, next spectrum written
+    ax = m if axes else 0
+    heun1 = s1 + m + 2 * m + s1 + ax       # k1 and the predictor written, next spectrum written
+    heun2 = s1 + m + 2 * m + m + s1 + ax   # m_n and k1 read, m_{n+1} written, next spectrum written
     return {
         "k_yfwd": float(s1 + s2),
         "k_colconv_z": float(2 * s2 + kern),
         "k_yinv": float(s2 + s1),
         "k_xinv_local_fused": (heun1 + heun2) / 2.0,
         "k_xinv_h": float(s1 + m),
-        "k_local_h": (4 * m + 5 * m) / 2.0,    # H_demag read back + the Heun stage's reads and writes
+        "k_local_h": (4 * m + 5 * m) / 2.0 + ax,   # H_demag read back + the Heun stage's reads and writes
         "k_xfwd_next": float(m + s1),
         "step": float(2 * (2 * (s1 + s2) + 2 * s2 + kern) + heun1 + heun2),
     }
@@ -220,6 +222,10 @@ def run_gpu(args):
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         s = B.Solver(w["shape"], w["cell"], pbc=w["pbc"], stream=stream.cuda_stream, **w["material"])
+        axes = None
+        if w.get("axes") is not None:             # per-cell easy axes (the cube's polycrystal)
+            axes = torch.from_numpy(w["axes"]).cuda()
+            B.mm_set_anisotropy_axes(s.ctx, axes)
         m = torch.from_numpy(w["m"]).cuda()
         ctx = s.ctx
         B.mm_load(ctx, m)
@@ -523,8 +529,9 @@ def cpu_baseline_cube(seconds=20.0):
     w = inputs.workload("cube_256x256x64", seed=0)
     mat = w["material"]
     shape = (32, 32, 32)
-    p = llg.Problem(shape, w["cell"], mat["Ms"], mat["Aex"], mat["alpha"], Ku=mat["Ku"], u=mat["easy_axis"],
-                    B=mat["B"], T=mat["temperature"], seed=mat["seed"], pbc=(True, True, False), images=2)
+    p = llg.Problem(shape, w["cell"], mat["Ms"], mat["Aex"], mat["alpha"], Ku=mat["Ku"],
+                    u=inputs.tilted_axes(shape, 0).astype(np.float64), B=mat["B"], T=mat["temperature"],
+                    seed=mat["seed"], pbc=(True, True, False), images=2)
     m = inputs.random_unit(shape, 0).astype(np.float64)
     N = int(np.prod(shape))
     n = 0

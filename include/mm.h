@@ -113,6 +113,17 @@ int mm_set_material(mm_ctx* ctx, double Ms, double Aex, double Ku, const double 
 int mm_set_cubic_anisotropy(mm_ctx* ctx, double K1, double K2, const double c1[3], const double c2[3]);
 
 /*
+ * Per-cell uniaxial easy axes (Sec. 2.1.3, Eq. 4 with an axis u_i in every
+ * cell, e.g. a polycrystal's random grain axes): u = device array, float32
+ * SoA [3][nz][ny][nx] of unit vectors, caller-owned, read by every later
+ * evaluation (not normalised by the library; keep it valid and unchanged
+ * while in use).  H_an,i = 2Ku/(mu0 Ms) (m_i . u_i) u_i with the Ku of
+ * mm_set_material.  u = NULL returns to the single axis of mm_set_material.
+ * MM_EINVAL for a misaligned pointer.
+ */
+int mm_set_anisotropy_axes(mm_ctx* ctx, const float* u);
+
+/*
  * Spin-transfer torque of Zhang and Li (Sec. 2.1.4, Eq. 7), a torque added to
  * dm/dt (not a field):
  *   dm/dt += -b_j/(1+alpha^2) [ m x (m x (j.grad)m) + (xi - alpha) m x (j.grad)m ],

@@ -49,6 +49,7 @@ _SIGS = {
     "mm_set_workspace": (_i, [_vp, _vp, _sz]),
     "mm_set_material": (_i, [_vp, _d, _d, _d, _dp, _d, _d, _d, _u64, _dp]),
     "mm_set_demag": (_i, [_vp, _i]),
+    "mm_set_anisotropy_axes": (_i, [_vp, _vp]),
     "mm_set_cubic_anisotropy": (_i, [_vp, _d, _d, _dp, _dp]),
     "mm_set_stt": (_i, [_vp, _d, _d, _dp]),
     "mm_demag_kernel": (_i, [_vp, _dp]),
@@ -165,6 +166,11 @@ def mm_set_cubic_anisotropy(ctx, K1, K2, c1=(1.0, 0.0, 0.0), c2=(0.0, 1.0, 0.0))
 def mm_set_stt(ctx, P, xi, j=(0.0, 0.0, 0.0)):
     jj, _kj = _d3(j)
     return _check(ctx, lib().mm_set_stt(ctx, float(P), float(xi), jj))
+
+
+def mm_set_anisotropy_axes(ctx, u):
+    """u: device float32 tensor (3, nz, ny, nx) of unit easy axes, or None."""
+    return _check(ctx, lib().mm_set_anisotropy_axes(ctx, _ptr(u)))
 
 
 def mm_set_demag(ctx, enabled):

@@ -79,6 +79,7 @@ struct mm_ctx {
     double B[3] = {0, 0, 0};
     double K1 = 0, K2 = 0, cub[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
     double stt_P = 0, stt_xi = 0, stt_j[3] = {0, 0, 0};
+    const float* uaxis = nullptr;   // per-cell easy axes (caller-owned device array) or null
     bool demag = true;
     bool kernel_ready = false;
     // workspace
@@ -186,6 +187,7 @@ mm::HotParams hot_params(mm_ctx* c, double dt_internal, bool thermal) {
     p.cex[2] = (float)(ex / (c->dz * c->dz));
     p.kan = (float)(2.0 * c->Ku / (MU0 * Ms * Ms));
     p.ux = (float)c->u[0]; p.uy = (float)c->u[1]; p.uz = (float)c->u[2];
+    p.uaxis = c->uaxis;
     p.hzx = (float)(c->B[0] / (MU0 * Ms));
     p.hzy = (float)(c->B[1] / (MU0 * Ms));
     p.hzz = (float)(c->B[2] / (MU0 * Ms));
@@ -513,6 +515,15 @@ int mm_set_stt(mm_ctx* ctx, double P, double xi, const double j_A_per_m2[3]) {
     ctx->stt_P = P;
     ctx->stt_xi = xi;
     for (int a = 0; a < 3; ++a) ctx->stt_j[a] = j[a];
+    ctx->k1_valid = false;
+    ctx->param_version++;
+    return MM_OK;
+}
+
+int mm_set_anisotropy_axes(mm_ctx* ctx, const float* u) {
+    if (!ctx) return MM_EINVAL;
+    if (u && (reinterpret_cast<uintptr_t>(u) & 3)) return fail(ctx, MM_EINVAL, "axis array must be float aligned");
+    ctx->uaxis = u;
     ctx->k1_valid = false;
     ctx->param_version++;
     return MM_OK;

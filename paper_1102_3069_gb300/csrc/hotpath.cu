@@ -579,6 +579,7 @@ struct CellIn {
     f3 m, mxp, mxm, myp, mym, mzp, mzm;
     f3 q0;
     f3 qk[6];
+    f3 u;             // easy axis of this cell
 };
 
 // Issues every load a cell needs, before any arithmetic, so their latencies
@@ -617,6 +618,7 @@ __device__ __forceinline__ void load_cell(const HotParams& p, const LaunchArgs& 
     in.myp = in.mym = in.mzp = in.mzm = in.m;
     if (usey) { in.myp = ld3(min, iyp, n); in.mym = ld3(min, iym, n); }
     if (usez) { in.mzp = ld3(min, izp, n); in.mzm = ld3(min, izm, n); }
+    in.u = p.uaxis ? ld3(p.uaxis, cell, n) : mk(p.ux, p.uy, p.uz);
     in.q0 = mk(0.f, 0.f, 0.f);
 #pragma unroll
     for (int j = 0; j < 6; ++j) in.qk[j] = in.q0;
@@ -661,7 +663,7 @@ __device__ __forceinline__ f3 update_cell(const HotParams& p, const LaunchArgs& 
     f3 hex = p.cex[0] * ((mxp - m) + (mxm - m));
     if (usey) hex = hex + p.cex[1] * ((myp - m) + (mym - m));
     if (usez) hex = hex + p.cex[2] * ((mzp - m) + (mzm - m));
-    const f3 u = mk(p.ux, p.uy, p.uz);
+    const f3 u = in.u;
     f3 han = (p.kan * dot(m, u)) * u;
     float ecub = 0.f;
     if (p.kc1 != 0.f || p.kc2 != 0.f) {

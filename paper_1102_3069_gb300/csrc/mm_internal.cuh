@@ -76,6 +76,7 @@ struct HotParams {
     float cex[3];            // 2A/(mu0 Ms^2 d^2) per axis
     float kan;               // 2Ku/(mu0 Ms^2)
     float ux, uy, uz;        // easy axis
+    const float* uaxis;      // per-cell unit easy axes [3][ncell] (caller-owned), or null: (ux, uy, uz)
     float hzx, hzy, hzz;     // B/(mu0 Ms)
     float kc1, kc2;          // cubic anisotropy 2K1/(mu0 Ms^2), 2K2/(mu0 Ms^2) (0: off)
     float c[3][3];           // orthonormal cubic axes c1, c2, c3

@@ -13,9 +13,10 @@ measured on:
                       boundaries, vortex-plus-noise start, applied field of
                       magnitude U[0, 50] mT in a uniformly random direction;
 * ``cube_256x256x64`` 256 x 256 x 64 cells of 3 nm, periodic in x and y,
-                      Ms 1.1e6 A/m, A 2e-11 J/m, Ku 2e4 J/m^3 (uniform easy
-                      axis tilted by U[0, 30] deg from z), alpha 0.05, 300 K,
-                      Heun with dt = 50 fs;
+                      Ms 1.1e6 A/m, A 2e-11 J/m, Ku 2e4 J/m^3 along per-cell
+                      easy axes tilted by U[0, 30] deg from z (``axes``; the
+                      material's easy_axis is one such draw), alpha 0.05,
+                      300 K, Heun with dt = 50 fs;
 * ``table1_N2`` / ``table1_N3``  square and cubic grids of the Euler-step
                       timing table, 4 nm cells with the film_1024x1024
                       material;
@@ -80,6 +81,18 @@ def smooth_tilt(shape):
     return m.astype(np.float32)
 
 
+def tilted_axes(shape, seed, max_deg=30.0):
+    """Per-cell unit easy axes tilted from z by theta ~ U[0, max_deg] deg with
+    azimuth phi ~ U[0, 2 pi), float32 (3, nz, ny, nx)."""
+    nx, ny, nz = shape
+    g = rng(seed + 3000)
+    th = np.deg2rad(g.uniform(0.0, max_deg, (nz, ny, nx)))
+    ph = g.uniform(0.0, 2 * np.pi, (nz, ny, nx))
+    u = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)])
+    u /= np.sqrt((u * u).sum(axis=0, keepdims=True))
+    return u.astype(np.float32)
+
+
 def random_direction(g):
     v = g.standard_normal(3)
     return v / np.linalg.norm(v)
@@ -106,7 +119,7 @@ def workload(name, seed=0):
         mat = dict(Ms=1.1e6, Aex=2e-11, Ku=2e4, easy_axis=u, alpha=0.05, temperature=300.0, seed=seed,
                    B=(0.0, 0.0, 0.0))
         return dict(name=name, shape=shape, cell=cell, pbc=(1, 1, 0), material=mat, m=random_unit(shape, seed),
-                    dt=50e-15)
+                    dt=50e-15, axes=tilted_axes(shape, seed))
     if name.startswith("table1_N2_") or name.startswith("table1_N3_"):
         n = int(name.rsplit("_", 1)[1])
         shape = (n, n, 1) if name.startswith("table1_N2_") else (n, n, n)

@@ -1,7 +1,8 @@
 """3-D periodic workload with thermal noise, checked on a 32^3 crop.
 
 The 256 x 256 x 64 cube (3 nm cells, periodic in x and y, Ms 1.1e6 A/m,
-A 2e-11 J/m, Ku 2e4 J/m^3 along a tilted axis, alpha 0.05, 300 K, Heun with
+A 2e-11 J/m, Ku 2e4 J/m^3 along per-cell easy axes tilted up to 30 deg from
+z, alpha 0.05, 300 K, Heun with
 dt = 50 fs) runs the 3-D pass sequence (x, y forward, z column pass, y
 inverse, x inverse + epilogue) and the periodic-image kernel.  The FP64
 oracle cannot build the full periodic kernel in reasonable time, so the same
@@ -29,9 +30,13 @@ IMAGES = 2
 
 @pytest.fixture(scope="module")
 def pair():
+    # the cube's per-cell easy axes (tilted up to 30 deg from z), drawn for the crop
     mat = W["material"]
+    axes = inputs.tilted_axes(SHAPE, 0)
     s = solver(SHAPE, W["cell"], pbc=W["pbc"], images=IMAGES, **mat)
-    p = oracle(SHAPE, W["cell"], pbc=W["pbc"], images=IMAGES, **mat)
+    s.axes = to_dev(axes)
+    B.mm_set_anisotropy_axes(s.ctx, s.axes)
+    p = oracle(SHAPE, W["cell"], pbc=W["pbc"], images=IMAGES, **dict(mat, easy_axis=axes.astype(np.float64)))
     return s, p
 
 

@@ -142,3 +142,37 @@ def test_spin_transfer_torque_matches_oracle(shape, pbc):
     assert rel_l2(to_np(h), p.heff(m64)) <= HEFF_REL_L2          # a torque, not a field
     ref = p.rhs(m64)
     assert rel_l2(to_np(tq), ref) <= 2 * HEFF_REL_L2
+
+
+@pytest.mark.parametrize("shape,pbc", [((33, 7, 1), (0, 0, 0)), ((16, 12, 3), (0, 0, 0)), ((64, 16, 1), (0, 0, 0)),
+                                       ((16, 8, 4), (1, 1, 0))])
+def test_per_cell_easy_axes_match_oracle(shape, pbc):
+    """Eq. 4 with a different unit easy axis in every cell (any direction)."""
+    from paper_1102_3069_gb300 import binding as B
+    cell = (4e-9, 3e-9, 2e-9)
+    axes = inputs.tilted_axes(shape, 5, max_deg=180.0)
+    m = inputs.random_unit(shape, 9)
+    mat = dict(MAT, Ku=4e4)
+    s = solver(shape, cell, pbc=pbc, images=2, **mat)
+    ax = to_dev(axes)
+    B.mm_set_anisotropy_axes(s.ctx, ax)
+    h, tq, e = s.heff(to_dev(m), torque=True, energy=True)
+    p = oracle(shape, cell, pbc=pbc, images=2, **dict(mat, easy_axis=axes.astype(np.float64)))
+    m64 = m.astype(np.float64)
+    t = p.terms(m64)
+    H = t["d"] + t["ex"] + t["an"] + t["z"]
+    assert rel_l2(to_np(h), H) <= HEFF_REL_L2
+    assert rel_max(to_np(h), H) <= HEFF_REL_MAX
+    assert rel_l2(to_np(tq), llg.ll_rhs(m64, H, p.alpha)) <= 2 * HEFF_REL_L2
+    assert e == pytest.approx(p.energy(m64), rel=1e-6)
+    # one Dormand-Prince step with the per-cell axes
+    md = to_dev(m)
+    acc, _, _ = B.mm_step(s.ctx, md, B.MM_RKDP, 0.0, 1e-13, tol=1.0)
+    m0 = m64 / np.sqrt((m64 * m64).sum(axis=0, keepdims=True))
+    ref = llg.rkdp_stages(p, m0, 1e-13)[0]
+    assert acc and float(np.max(np.abs(to_np(md) - ref))) < 1e-6
+    # NULL returns to the single axis of the material
+    B.mm_set_anisotropy_axes(s.ctx, None)
+    h1, _, _ = s.heff(to_dev(m))
+    p1 = oracle(shape, cell, pbc=pbc, images=2, **mat)
+    assert rel_l2(to_np(h1), p1.heff(m64)) <= HEFF_REL_L2

@@ -6,6 +6,7 @@
   (checked on a three-cell chain worked by hand);
 * exchange energy equals the bond sum A V sum_bonds |m_i - m_j|^2 / d^2;
 * anisotropy: |H_an| = 2Ku/(mu0 Ms) cos(theta) along u; energy -Ku V cos^2;
+  the same per cell with a different easy axis in every cell;
 * Zeeman energy -Ms V m.B;
 * demag energy of a uniformly magnetised body: mu0 Ms^2 Vtot N_prism / 2;
 * Philox-4x32-10 known-answer vectors (Salmon et al., SC'11, Random123);
@@ -88,6 +89,29 @@ def test_anisotropy_closed_form():
         mi = m[:, :, :, i:i + 1]
         Ei = F.energy(mi, MS, V, z[:, :, :, :1], z[:, :, :, :1], H[:, :, :, i:i + 1], z[:, :, :, :1])
         assert Ei == pytest.approx(-Ku * V * np.cos(th[i]) ** 2, rel=1e-12, abs=1e-40)
+
+
+def test_per_cell_anisotropy_axes_closed_form():
+    # each cell has its own easy axis u_i and sits at its own angle theta_i to it:
+    # H_an,i = 2Ku/(mu0 Ms) cos(theta_i) u_i, energy -Ku V sum cos^2(theta_i)
+    Ku, V = 2e4, 2.7e-26
+    g = np.random.default_rng(7)
+    n = 11
+    u = g.standard_normal((3, n))
+    u /= np.linalg.norm(u, axis=0)
+    w = np.cross(u, g.standard_normal((3, n)), axis=0)
+    w /= np.linalg.norm(w, axis=0)
+    th = g.uniform(0, np.pi, n)
+    m = np.cos(th) * u + np.sin(th) * w
+    H = F.anisotropy_field(m.reshape(3, 1, 1, n), MS, Ku, u.reshape(3, 1, 1, n)).reshape(3, n)
+    np.testing.assert_allclose(H, (2 * Ku / (F.MU0 * MS)) * np.cos(th) * u, rtol=1e-12, atol=1e-9)
+    z = np.zeros((3, 1, 1, n))
+    E = F.energy(m.reshape(3, 1, 1, n), MS, V, z, z, H.reshape(3, 1, 1, n), z)
+    assert E == pytest.approx(-Ku * V * np.sum(np.cos(th) ** 2), rel=1e-12)
+    # a uniform axis field of per-cell copies is the uniform-axis result
+    Hu = F.anisotropy_field(m.reshape(3, 1, 1, n), MS, Ku, u[:, 0])
+    Hc = F.anisotropy_field(m.reshape(3, 1, 1, n), MS, Ku, np.repeat(u[:, :1], n, axis=1).reshape(3, 1, 1, n))
+    np.testing.assert_array_equal(Hu, Hc)
 
 
 def test_zeeman_energy():
