@@ -124,6 +124,20 @@ int mm_set_cubic_anisotropy(mm_ctx* ctx, double K1, double K2, const double c1[3
 int mm_set_anisotropy_axes(mm_ctx* ctx, const float* u);
 
 /*
+ * Fixed maximum variation of m per step (Sec. 2.2: the methods without an
+ * error estimate take a fixed time step or a fixed maximum variation of m per
+ * step).  With max_dm > 0, mm_advance with MM_EULER, MM_HEUN, MM_RK3 or MM_RK4
+ * chooses every step's size on the device as h = max_dm / max_i |dm/dt(m_n)|_i
+ * (the size that moves the fastest cell by max_dm to first order), capped at
+ * the dt_s argument when that is > 0 (dt_s = 0: no cap), then takes the
+ * method's step with it.  Each step evaluates k1 first and forms the stage-2
+ * input after h is known.  The thermal field is refused in this mode (its
+ * variance depends on the step).  max_dm = 0 (default) returns to fixed dt.
+ * MM_EINVAL unless 0 <= max_dm <= 1.
+ */
+int mm_set_max_dm(mm_ctx* ctx, double max_dm);
+
+/*
  * Spin-transfer torque of Zhang and Li (Sec. 2.1.4, Eq. 7), a torque added to
  * dm/dt (not a field):
  *   dm/dt += -b_j/(1+alpha^2) [ m x (m x (j.grad)m) + (xi - alpha) m x (j.grad)m ],

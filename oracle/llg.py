@@ -18,6 +18,10 @@ Readings where the paper is silent (all listed in the design doc):
 * thermal field: one eta per step, shared by both Heun stages; sigma uses the
   fixed step dt (Eq. 6).  Thermal noise with the adaptive method is refused.
 * relaxation: adaptive RKDP until max_i |m_i x H_i| / Ms < torque_tol.
+* fixed maximum variation of m per step (the methods without an error
+  estimate): every step has h = dm_max / max_i |dm/dt(m_n)|_i (capped at h_cap
+  when given), the size that moves the fastest cell by dm_max to first order;
+  the step itself is the method's (max_dm_step).
 
 Pins: tests/test_oracle_llg.py (macrospin precession and damping closed forms,
 Larmor/Kittel frequencies, convergence orders 1/2/5, |m| conservation, energy
@@ -380,3 +384,40 @@ class TableauStepper(Stepper):
         if self.h < H_MIN:
             raise NotConverged("step size underflow")
         return ok
+
+
+# Fixed maximum variation of m per step (Sec. 2.2): the methods without an
+# error estimate, as tableaus (Euler and Heun next to RK3 and RK4).
+MAXDM_TABLEAUS = {
+    "euler": Tableau("euler", ((),), (1.0,)),
+    "heun": Tableau("heun", ((), (1.0,)), (1 / 2, 1 / 2)),
+    "rk3": TABLEAUS["rk3"],
+    "rk4": TABLEAUS["rk4"],
+}
+
+
+def max_dm_step(p, m, tab, dm_max, h_cap=None):
+    """One step whose size moves the fastest cell by dm_max to first order:
+    h = dm_max / max_i |dm/dt(m)|_i, capped at h_cap.  Returns (m_next, h)."""
+    if p.T > 0.0:
+        raise ValueError("thermal field with a varying step is not supported")
+    k1 = p.rhs(m)
+    kmax = float(np.sqrt((k1 * k1).sum(axis=0)).max())
+    if kmax > 0.0:
+        h = dm_max / kmax
+        if h_cap:
+            h = min(h, h_cap)
+    else:
+        h = float(h_cap or 0.0)
+    mn, _, _ = rk_attempt(p, m, h, tab, k1)
+    return mn, h
+
+
+def max_dm_run(p, m, tab, dm_max, nsteps, h_cap=None):
+    """nsteps max-variation steps; returns (m, t, list of h)."""
+    t, hs = 0.0, []
+    for _ in range(nsteps):
+        m, h = max_dm_step(p, m, tab, dm_max, h_cap)
+        t += h
+        hs.append(h)
+    return m, t, hs

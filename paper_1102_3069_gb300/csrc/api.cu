@@ -92,6 +92,8 @@ struct mm_ctx {
     bool k1_valid = false;
     bool rk_h_set = false;          // an RKDP step size has been given since mm_load
     int last_method = 0;
+    bool last_maxdm = false;        // the last run chose its steps by the maximum variation of m
+    double max_dm = 0.0;            // mm_set_max_dm (0: fixed dt)
     // what the x spectrum in the workspace currently holds: nothing usable, the
     // transform of m_n (ms[cur]) or of the Dormand-Prince stage-2 input m_2
     enum { SPEC_NONE, SPEC_MCUR, SPEC_M2 } spec = SPEC_NONE;
@@ -231,8 +233,10 @@ mm::HotParams hot_params(mm_ctx* c, double dt_internal, bool thermal) {
 
 // run parameters are written by a one-thread kernel so that mm_advance stays asynchronous
 __global__ void k_set_run(mm::DevState* st, double tol, double t_end, double torque_tol, double h,
-                          double h_min, int reset_done, int fixed_h) {
+                          double h_min, int reset_done, int fixed_h, double max_dm, double h_cap) {
     st->tol = tol;
+    st->max_dm = max_dm;
+    st->h_cap = h_cap;
     st->fixed_h = fixed_h;
     st->t_end = t_end;
     st->torque_tol = torque_tol;
@@ -294,6 +298,23 @@ namespace {
 int enqueue_step(mm_ctx* ctx, const mm::HotParams& p, int method, bool first) {
     int rc;
     RkInfo r;
+    if (ctx->max_dm > 0.0 && (method == MM_EULER || method == MM_HEUN || (rk_info(method, &r) && !r.adaptive))) {
+        // fixed maximum variation of m per step: the k1 pass reduces max |k1|
+        // and its last block sets h; the stage-2 input is then formed by the
+        // forward x pass (m_n + h a21 k1) with that h
+        if ((rc = eval(ctx, p, mm::SRC_CUR, mm::LM_K1, 1, false, false))) return rc;
+        if (method == MM_EULER) {
+            CK(mm::launch_euler_update(p, ctx->stream));
+            return MM_OK;
+        }
+        const int S = p.rk_stages;
+        auto src_of = [&](int st) { return (st & 1) ? mm::SRC_STAGE1 : mm::SRC_STAGE0; };
+        if (S == 2) return eval(ctx, p, mm::SRC_COMBINE2, mm::LM_RKFINAL, 2, false, false);
+        if ((rc = eval(ctx, p, mm::SRC_COMBINE2, mm::LM_RK, 2, true, false))) return rc;
+        for (int st = 3; st < S; ++st)
+            if ((rc = eval(ctx, p, src_of(st), mm::LM_RK, st, true, true))) return rc;
+        return eval(ctx, p, src_of(S), mm::LM_RKFINAL, S, false, true);
+    }
     if (rk_info(method, &r)) {
         const int S = r.stages;
         // stage s reads its input from mstage[s & 1]; with first same as last
@@ -529,6 +550,16 @@ int mm_set_anisotropy_axes(mm_ctx* ctx, const float* u) {
     return MM_OK;
 }
 
+int mm_set_max_dm(mm_ctx* ctx, double max_dm) {
+    if (!ctx) return MM_EINVAL;
+    if (!(max_dm >= 0.0) || !std::isfinite(max_dm) || max_dm > 1.0)
+        return fail(ctx, MM_EINVAL, "max_dm must be in [0, 1]");
+    ctx->max_dm = max_dm;
+    ctx->k1_valid = false;
+    ctx->param_version++;
+    return MM_OK;
+}
+
 int mm_set_demag(mm_ctx* ctx, int enabled) {
     if (!ctx) return MM_EINVAL;
     ctx->demag = enabled != 0;
@@ -663,8 +694,16 @@ int mm_advance(mm_ctx* ctx, int method, long nsteps, double dt_s, double tol, do
         return fail(ctx, MM_EINVAL, "non-finite argument");
     const double tu = ctx->gamma0 * ctx->Ms;
     RkInfo rk = {0, 7, 1, 1};
-    const bool is_rk = rk_info(method, &rk);
-    if (method == MM_EULER || method == MM_HEUN || (is_rk && !rk.adaptive)) {
+    bool is_rk = rk_info(method, &rk);
+    // the methods without an error estimate take a fixed dt or, with
+    // mm_set_max_dm, the step that moves the fastest cell by max_dm
+    const bool maxdm = ctx->max_dm > 0.0 && (method == MM_EULER || method == MM_HEUN || (is_rk && !rk.adaptive));
+    if (maxdm) {
+        if (ctx->T > 0.0) return fail(ctx, MM_EINVAL, "thermal field needs a fixed dt (maximum-variation steps vary it)");
+        if (!(dt_s >= 0)) return fail(ctx, MM_EINVAL, "dt (the step cap) must be >= 0");
+        if (method == MM_HEUN) { rk = {6, 2, 0, 0}; is_rk = true; }     // Heun as a two-stage tableau
+        if (method == MM_EULER) rk = {6, 2, 0, 0};                     // only its k1 pass runs
+    } else if (method == MM_EULER || method == MM_HEUN || (is_rk && !rk.adaptive)) {
         if (!(dt_s > 0)) return fail(ctx, MM_EINVAL, "fixed-step methods need dt > 0");
     } else if (is_rk) {
         if (ctx->T > 0.0) return fail(ctx, MM_EINVAL, "thermal field needs a fixed-step method (fixed dt)");
@@ -683,10 +722,12 @@ int mm_advance(mm_ctx* ctx, int method, long nsteps, double dt_s, double tol, do
     p.rk = rk.index;
     p.rk_stages = rk.stages;
     p.rk_fsal = rk.fsal;
-    const bool fixed_steps = is_rk && (!rk.adaptive || tol < 0.0);
+    const bool fixed_steps = (is_rk && (!rk.adaptive || tol < 0.0)) || maxdm;
     k_set_run<<<1, 1, 0, ctx->stream>>>(dstate(ctx), fixed_steps ? 1.0 : tol, t_end_s > 0 ? t_end_s * tu : 0.0,
                                         torque_tol > 0 ? torque_tol : 0.0,
-                                        is_rk ? (dt > 0 ? dt : 0.0) : 0.0, 1e-20 * tu, 1, fixed_steps ? 1 : 0);
+                                        (is_rk || maxdm) ? (dt > 0 ? dt : 0.0) : 0.0, 1e-20 * tu, 1,
+                                        fixed_steps ? 1 : 0, maxdm ? ctx->max_dm : 0.0,
+                                        maxdm && dt > 0 ? dt : 0.0);
     CK(cudaGetLastError());
     if (is_rk && rk.fsal) {
         if (dt > 0 && ctx->spec == mm_ctx::SPEC_M2) ctx->spec = mm_ctx::SPEC_NONE;   // m_2 depends on h
@@ -706,8 +747,10 @@ int mm_advance(mm_ctx* ctx, int method, long nsteps, double dt_s, double tol, do
     // FSAL tableaus: right after k1 the stage-2 input and its spectrum are in place;
     // others: the first step finds the spectrum of m_n in place only if a previous
     // Euler/Heun run left it (their standard step needs it, the tableaus' does not)
+    ctx->last_maxdm = maxdm;
     bool first_special;
-    if (is_rk && rk.fsal) first_special = ctx->spec == mm_ctx::SPEC_M2;
+    if (maxdm) first_special = false;              // every step starts from its own k1 pass
+    else if (is_rk && rk.fsal) first_special = ctx->spec == mm_ctx::SPEC_M2;
     else if (is_rk) first_special = ctx->spec == mm_ctx::SPEC_MCUR;
     else first_special = ctx->spec != mm_ctx::SPEC_MCUR;
     if (nsteps > 0 && first_special) {
@@ -747,7 +790,7 @@ int mm_advance(mm_ctx* ctx, int method, long nsteps, double dt_s, double tol, do
             }
         }
     }
-    if (nsteps > 0) ctx->spec = is_rk ? mm_ctx::SPEC_NONE : mm_ctx::SPEC_MCUR;
+    if (nsteps > 0) ctx->spec = (is_rk || maxdm) ? mm_ctx::SPEC_NONE : mm_ctx::SPEC_MCUR;
     if (is_rk && !rk.fsal) ctx->k1_valid = false;
     return MM_OK;
 }
@@ -767,7 +810,7 @@ int mm_get_stats(mm_ctx* ctx, mm_stats* stats) {
         stats->step_index = h.step_index;
         stats->t = h.t / tu;
         RkInfo ri;
-        stats->dt = ((rk_info(ctx->last_method, &ri) && ri.adaptive) ? h.h : ctx->last_fixed_dt) / tu;
+        stats->dt = ((rk_info(ctx->last_method, &ri) && ri.adaptive) || ctx->last_maxdm ? h.h : ctx->last_fixed_dt) / tu;
         stats->last_err = h.last_err;
         stats->max_torque = h.max_torque;
         const double V = ctx->dx * ctx->dy * ctx->dz;
@@ -1070,7 +1113,7 @@ int batch_advance(mm_batch* b, int method, long nsteps, double dt_s, double tol,
         p.rk_stages = r.stages;
         p.rk_fsal = r.fsal;
         k_set_run<<<1, 1, 0, b->stream>>>(dstate(c), fixed_steps ? 1.0 : tol, 0.0, torque_tol > 0 ? torque_tol : 0.0,
-                                          dt0 > 0 ? dt0 * tu : 0.0, 1e-20 * tu, 1, fixed_steps ? 1 : 0);
+                                          dt0 > 0 ? dt0 * tu : 0.0, 1e-20 * tu, 1, fixed_steps ? 1 : 0, 0.0, 0.0);
         BCK(cudaGetLastError());
         c->spec = mm_ctx::SPEC_NONE;               // single-context calls start afresh after a batch
         c->k1_valid = false;

@@ -34,10 +34,11 @@ namespace r8 = mmfft::r8;
 // Explicit Runge-Kutta tableaus of Sec. 2.2, double precision, by method
 // index: 0 Dormand-Prince 5(4) (Dormand & Prince 1980, first same as last),
 // 1 Bogacki-Shampine 3(2) (1989, first same as last), 2 Cash-Karp 5(4) (1990),
-// 3 classical RK4, 4 Kutta's RK3, 5 Heun-Euler 2(1).
+// 3 classical RK4, 4 Kutta's RK3, 5 Heun-Euler 2(1), 6 Heun (RK2, used when
+// the step follows the maximum variation of m).
 // c_rka[r][s][j]: weight of k_j in the input of stage s (1-based); with first
 // same as last the last stage's row is b.  c_rke[r][j] = b_j - b*_j.
-constexpr int NRK = 6;
+constexpr int NRK = 7;
 #define MM_RKA_INIT { \
     {{0}, {0}, {0, 1.0 / 5}, {0, 3.0 / 40, 9.0 / 40}, {0, 44.0 / 45, -56.0 / 15, 32.0 / 9}, \
      {0, 19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729}, \
@@ -50,6 +51,7 @@ constexpr int NRK = 6;
     {{0}, {0}, {0, 1.0 / 2}, {0, 0.0, 1.0 / 2}, {0, 0.0, 0.0, 1.0}}, \
     {{0}, {0}, {0, 1.0 / 2}, {0, -1.0, 2.0}}, \
     {{0}, {0}, {0, 1.0}}, \
+    {{0}, {0}, {0, 1.0}}, \
 }
 #define MM_RKB_INIT { \
     {0, 35.0 / 384, 0.0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84, 0.0}, \
@@ -57,6 +59,7 @@ constexpr int NRK = 6;
     {0, 37.0 / 378, 0.0, 250.0 / 621, 125.0 / 594, 0.0, 512.0 / 1771}, \
     {0, 1.0 / 6, 1.0 / 3, 1.0 / 3, 1.0 / 6}, \
     {0, 1.0 / 6, 2.0 / 3, 1.0 / 6}, \
+    {0, 1.0 / 2, 1.0 / 2}, \
     {0, 1.0 / 2, 1.0 / 2}, \
 }
 #define MM_RKE_INIT { \
@@ -67,6 +70,7 @@ constexpr int NRK = 6;
      -277.0 / 14336, 512.0 / 1771 - 1.0 / 4}, \
     {0}, {0}, \
     {0, 1.0 / 2 - 1.0, 1.0 / 2}, \
+    {0}, \
 }
 __constant__ double c_rka[NRK][8][8] = MM_RKA_INIT;
 __constant__ double c_rkb[NRK][8] = MM_RKB_INIT;
@@ -76,9 +80,9 @@ static constexpr double h_rka[NRK][8][8] = MM_RKA_INIT;
 static constexpr double h_rkb[NRK][8] = MM_RKB_INIT;
 static constexpr double h_rke[NRK][8] = MM_RKE_INIT;
 // stages, first-same-as-last, exponent denominator q of the step-size factor (0: fixed step)
-__constant__ int c_rks[NRK] = {7, 4, 6, 4, 3, 2};
-__constant__ int c_rkfsal[NRK] = {1, 1, 0, 0, 0, 0};
-__constant__ double c_rkq[NRK] = {5.0, 3.0, 5.0, 0.0, 0.0, 2.0};
+__constant__ int c_rks[NRK] = {7, 4, 6, 4, 3, 2, 2};
+__constant__ int c_rkfsal[NRK] = {1, 1, 0, 0, 0, 0, 0};
+__constant__ double c_rkq[NRK] = {5.0, 3.0, 5.0, 0.0, 0.0, 2.0, 0.0};
 
 // ---------------------------------------------------------------------------
 // small helpers
@@ -472,6 +476,13 @@ __device__ void finalize(const HotParams& p, const LaunchArgs& a) {
             st->max_torque = tq;
             if (bad) { st->status = -5; st->done = 1; }
             else if (st->torque_tol > 0.0 && tq < st->torque_tol) st->done = 1;
+            if (st->max_dm > 0.0 && !st->done) {
+                // fixed maximum variation of m per step: the fastest cell moves
+                // by max_dm to first order (err = max |k1|)
+                double hn = err > 0.0f ? st->max_dm / (double)err : st->h_cap;
+                if (st->h_cap > 0.0 && !(hn <= st->h_cap)) hn = st->h_cap;
+                if (hn > 0.0) st->h = hn;
+            }
             break;
         case LM_RKFINAL: {
             st->last_err = err;
@@ -709,6 +720,7 @@ __device__ __forceinline__ f3 update_cell(const HotParams& p, const LaunchArgs& 
         case LM_K1:
             st3(p.ks[cur], cell, n, k);
             pt.torque = fmaxf(pt.torque, tq);
+            pt.err = fmaxf(pt.err, sqrtf(dot(k, k)));    // max |dm/dt| (maximum-variation steps)
             pt.bad |= !finite3(k);
             next = axpy(sc.c[1], k, m);                 // m_2 = m_n + h a21 k1
             st3(p.mstage[0], cell, n, next);
@@ -1171,6 +1183,28 @@ __global__ void k_combine2(HotParams p) {
         st3(p.mstage[0], i, n, axpy(c, ld3(p.ks[cur], i, n), ld3(p.ms[cur], i, n)));
 }
 
+// Euler step of size st->h (set by the k1 pass): m_{n+1} = normalised(m_n + h k1),
+// then one thread advances the clock and flips the state slots
+__global__ void k_euler_update(HotParams p) {
+    const DevState* st = p.st;
+    if (st->done) return;
+    const long long n = p.ncell;
+    const int cur = st->cur;
+    const Coef c = split(st->h);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        st3(p.ms[1 - cur], i, n, normalized(axpy(c, ld3(p.ks[cur], i, n), ld3(p.ms[cur], i, n))));
+}
+
+__global__ void k_euler_finish(HotParams p) {
+    DevState* st = p.st;
+    if (st->done) return;
+    st->t += st->h;
+    st->cur ^= 1;
+    st->step_index += 1;
+    st->accepted += 1;
+    if (st->t_end > 0.0 && st->t >= st->t_end * (1.0 - 1e-12)) st->done = 1;
+}
+
 __global__ void k_copy_out(HotParams p, float* __restrict__ m_user) {
     const long long n = p.ncell;
     const float* src = p.ms[p.st->cur];
@@ -1455,6 +1489,13 @@ cudaError_t launch_gather_states(const HotParams* ps, DevState* out, int n, cuda
 
 cudaError_t launch_normalize_load(const HotParams& p, const float* m_user, cudaStream_t s) {
     k_normalize_load<<<4 * 152, 256, 0, s>>>(p, m_user);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_euler_update(const HotParams& p, cudaStream_t s) {
+    const long long blocks = (p.ncell + 255) / 256;
+    k_euler_update<<<(unsigned)(blocks < 4 * 152 ? blocks : 4 * 152), 256, 0, s>>>(p);
+    k_euler_finish<<<1, 1, 0, s>>>(p);
     return cudaGetLastError();
 }
 

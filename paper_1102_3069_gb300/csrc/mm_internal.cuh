@@ -17,6 +17,8 @@ struct DevState {
     double last_err;      // last RKDP error estimate
     double max_torque;    // max |m x h| of the last accepted state
     double energy_acc;    // sum of energy densities (EVAL mode)
+    double max_dm;        // > 0: fixed maximum variation of m per step (h set by the k1 pass)
+    double h_cap;         // upper bound on that h (<= 0: none)
     unsigned long long kre_bits;  // max |Re K^| seen by the kernel setup (double bits)
     unsigned long long kim_bits;  // max |Im K^| seen by the kernel setup (double bits)
     long long step_index; // thermal clock (Euler/Heun)
@@ -139,6 +141,8 @@ enum Pass : int {
 // hot path (hotpath.cu)
 cudaError_t launch_normalize_load(const HotParams& p, const float* m_user, cudaStream_t s);
 cudaError_t launch_copy_out(const HotParams& p, float* m_user, cudaStream_t s);
+// Euler step with the h its k1 pass set (fixed maximum variation of m per step)
+cudaError_t launch_euler_update(const HotParams& p, cudaStream_t s);
 int eval_passes(const HotParams& p, const LaunchArgs& a, int* ids);     // fills <= 7 pass ids
 cudaError_t launch_pass(const HotParams& p, const LaunchArgs& a, int pass, cudaStream_t s);
 cudaError_t configure_hot_kernels();

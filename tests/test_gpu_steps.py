@@ -213,3 +213,40 @@ def test_host_buffer_run_matches_device_run():
     B.mm_advance(s.ctx, B.MM_RKDP, 5, dt_s=1e-13, tol=1e-6)
     B.mm_store(s.ctx, md)
     assert np.array_equal(mh, md.cpu().numpy())
+
+
+@pytest.mark.parametrize("method,name", [(B.MM_EULER, "euler"), (B.MM_HEUN, "heun"), (B.MM_RK3, "rk3"),
+                                         (B.MM_RK4, "rk4")])
+@pytest.mark.parametrize("shape", [(40, 12, 1), (12, 9, 2)])
+def test_max_dm_steps_match_oracle(method, name, shape):
+    """Fixed maximum variation of m per step (Sec. 2.2): every step's size is
+    max_dm / max|dm/dt(m_n)|; m and the accumulated time follow the oracle.
+    (40, 12, 1) runs the split x passes, (12, 9, 2) the fused 3-D path."""
+    cell = (4e-9, 4e-9, 3e-9)
+    mat = dict(Ms=8e5, Aex=1.3e-11, Ku=2e4, easy_axis=(0.3, 0.0, 1.0), alpha=0.2, B=(0.0, 0.01, 0.02))
+    s = solver(shape, cell, **mat)
+    p = oracle(shape, cell, **mat)
+    m = inputs.random_unit(shape, 21)
+    md = to_dev(m)
+    dm, n = 0.01, 12
+    B.mm_set_max_dm(s.ctx, dm)
+    B.mm_load(s.ctx, md)
+    B.mm_advance(s.ctx, method, n, dt_s=0.0)
+    B.mm_store(s.ctx, md)
+    st = B.mm_get_stats(s.ctx)
+    ref, t, hs = llg.max_dm_run(p, _m64(m), llg.MAXDM_TABLEAUS[name], dm, n)
+    assert st["status"] == 0 and st["accepted"] == n
+    assert st["evals"] == n * {"euler": 1, "heun": 2, "rk3": 3, "rk4": 4}[name]
+    assert st["t"] == pytest.approx(t, rel=1e-5)
+    assert st["dt"] == pytest.approx(hs[-1], rel=1e-4)          # the last step's size
+    assert float(np.max(np.abs(to_np(md) - ref))) < 1e-5
+    # a cap below the natural step size binds every step
+    cap = 0.5 * min(hs)
+    B.mm_load(s.ctx, to_dev(m))
+    B.mm_advance(s.ctx, method, 4, dt_s=cap)
+    st = B.mm_get_stats(s.ctx)
+    assert st["t"] == pytest.approx(4 * cap, rel=1e-12)
+    # back to fixed steps: dt is required again
+    B.mm_set_max_dm(s.ctx, 0.0)
+    with pytest.raises(B.MMError):
+        B.mm_advance(s.ctx, method, 1, dt_s=0.0)

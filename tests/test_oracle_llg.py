@@ -246,3 +246,52 @@ def test_adaptive_tableaus_hit_the_closed_form(name):
     st.run_until(1e-10)
     assert st.t == pytest.approx(1e-10, rel=1e-12)
     np.testing.assert_allclose(st.m, _exact(alpha, B, th0, 0.0, st.t), atol=2e-5)
+
+
+# ---- fixed maximum variation of m per step (Sec. 2.2) -----------------------
+
+def test_max_dm_step_size_is_the_first_order_variation():
+    # Euler with the max-variation rule: the fastest cell moves by dm_max before
+    # normalisation, every other cell by less, and h = dm_max / max |dm/dt|
+    p = llg.Problem((6, 4, 1), CELL, MS, 1.3e-11, 0.1, Ku=3e4, u=(0, 0.6, 0.8), B=(0.01, 0, 0.02))
+    g = np.random.default_rng(3)
+    m = llg.normalize(g.standard_normal(p.mshape))
+    k1 = p.rhs(m)
+    dm = 0.02
+    m1, h = llg.max_dm_step(p, m, llg.MAXDM_TABLEAUS["euler"], dm)
+    move = np.sqrt(((h * k1) ** 2).sum(axis=0))
+    assert move.max() == pytest.approx(dm, rel=1e-14)
+    np.testing.assert_allclose(m1, llg.normalize(m + h * k1), rtol=0, atol=1e-15)
+    # the cap wins when it is smaller
+    _, hc = llg.max_dm_step(p, m, llg.MAXDM_TABLEAUS["euler"], dm, h_cap=0.5 * h)
+    assert hc == 0.5 * h
+
+
+@pytest.mark.parametrize("name", ["euler", "heun", "rk3", "rk4"])
+def test_max_dm_tableaus_equal_the_fixed_step_methods(name):
+    # with the same h the max-variation step is the method's own step
+    p = _macrospin(0.1)
+    m = _m0(1.0, 0.2)
+    _, h = llg.max_dm_step(p, m, llg.MAXDM_TABLEAUS[name], 0.01)
+    ref = {"euler": lambda: llg.euler_step(p, m, h), "heun": lambda: llg.heun_step(p, m, h),
+           "rk3": lambda: llg.rk_fixed(p, m, h, 1, llg.TABLEAUS["rk3"]),
+           "rk4": lambda: llg.rk_fixed(p, m, h, 1, llg.TABLEAUS["rk4"])}[name]()
+    mn, _ = llg.max_dm_step(p, m, llg.MAXDM_TABLEAUS[name], 0.01)
+    np.testing.assert_allclose(mn, ref, atol=1e-15)
+
+
+@pytest.mark.parametrize("name,order", [("euler", 1), ("heun", 2), ("rk4", 4)])
+def test_max_dm_runs_follow_the_closed_form_with_the_method_order(name, order):
+    # the macrospin's |dm/dt| = gamma' H sin(theta) sqrt(1+alpha^2) shrinks as it
+    # damps, so the steps grow; the state after N steps must match the closed
+    # form at the accumulated time, with an error that falls as dm_max^order
+    alpha, B, th0, ph0 = 0.1, 0.05, 1.2, 0.3
+    p = _macrospin(alpha, B)
+    tab = llg.MAXDM_TABLEAUS[name]
+    errs = []
+    for dm in (0.02, 0.01):
+        m, t, hs = llg.max_dm_run(p, _m0(th0, ph0), tab, dm, int(round(4.0 / dm)))
+        assert hs[-1] > hs[0]                        # slower precession, larger steps
+        errs.append(float(np.abs(m - _exact(alpha, B, th0, ph0, t)).max()))
+    assert np.log2(errs[0] / errs[1]) == pytest.approx(order, abs=0.3)
+    assert errs[1] < {1: 3e-2, 2: 3e-4, 4: 1e-7}[order]
