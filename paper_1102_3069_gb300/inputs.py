@@ -25,7 +25,12 @@ measured on:
                       Ms U[4e5, 1.4e6] A/m, A U[5e-12, 2e-11] J/m, Ku
                       U[0, 5e4] J/m^3, easy axis and field direction uniform
                       on the sphere, |B| U[0, 50] mT, alpha 0.02, open
-                      boundaries, random unit vectors.
+                      boundaries, random unit vectors;
+* ``relax_films(n)``  128 x 128 x 1 films of 4 x 4 x 3 nm cells, Ms
+                      U[6e5, 1e6] A/m, A 1.3e-11 J/m, Ku U[0, 5e4] J/m^3 along
+                      a random in-plane axis, in-plane field of magnitude
+                      U[0, 80] mT in a random direction, alpha 1 (relaxation),
+                      random unit vectors.
 """
 
 import numpy as np
@@ -145,4 +150,21 @@ def ensemble(n, seed=0, nmin=32, nmax=256, nzmax=4, alpha=0.02):
         mat = dict(Ms=Ms, Aex=A, Ku=Ku, easy_axis=u, alpha=alpha, B=B)
         out.append(dict(shape=(nx, ny, nz), cell=(4e-9, 4e-9, 4e-9), pbc=(0, 0, 0), material=mat,
                         m_seed=seed * 100003 + i))
+    return out
+
+
+def relax_films(n, seed=0, size=128, alpha=1.0):
+    """n independent 128 x 128 x 1 films for relaxation (dicts as ``ensemble``)."""
+    g = rng(seed + 4000)
+    out = []
+    for i in range(n):
+        Ms = float(g.uniform(6e5, 1e6))
+        Ku = float(g.uniform(0.0, 5e4))
+        pu = g.uniform(0.0, 2 * np.pi)
+        pb = g.uniform(0.0, 2 * np.pi)
+        b = g.uniform(0.0, 0.08)
+        mat = dict(Ms=Ms, Aex=1.3e-11, Ku=Ku, easy_axis=(float(np.cos(pu)), float(np.sin(pu)), 0.0), alpha=alpha,
+                   B=(float(b * np.cos(pb)), float(b * np.sin(pb)), 0.0))
+        out.append(dict(shape=(size, size, 1), cell=(4e-9, 4e-9, 3e-9), pbc=(0, 0, 0), material=mat,
+                        m_seed=seed * 100003 + 50000 + i))
     return out
