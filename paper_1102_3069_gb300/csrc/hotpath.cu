@@ -169,6 +169,9 @@ __device__ __forceinline__ void load_params(const HotParams* __restrict__ src, H
     __syncthreads();
 }
 
+// FFT lengths from which the x and y passes use the register radix-8 kernels
+constexpr int XREG_MIN_LOGP = 6;
+
 // ---------------------------------------------------------------------------
 // compile-time shapes of the passes (shared with the host through fft32.cuh)
 template <int LOGP>
@@ -377,8 +380,9 @@ kb_colconv(const HotParams* __restrict__ ps, const int4* __restrict__ work, Laun
 
 // ---------------------------------------------------------------------------
 // 3-D: y forward pass.  s1 [c][kx][z][y]  ->  s2 [c][kx][ky][z]
+// (P < 64: radix-16 shared-memory lines; P >= 64: yfwd_r_body below)
 template <int LOGP>
-__device__ __forceinline__ void yfwd_body(const HotParams& p, const LaunchArgs& a, int bx, int by) {
+__device__ __forceinline__ void yfwd_body_s(const HotParams& p, const LaunchArgs& a, int bx, int by) {
     constexpr int TZ = tz_of(LOGP);
     using S = CS<LOGP, TZ>;
     extern __shared__ float2 sm[];
@@ -400,23 +404,9 @@ __device__ __forceinline__ void yfwd_body(const HotParams& p, const LaunchArgs& 
     }
 }
 
-template <int LOGP>
-__global__ void __launch_bounds__(CS<LOGP, tz_of(LOGP)>::NT, CS<LOGP, tz_of(LOGP)>::MINB)
-k_yfwd(HotParams p, LaunchArgs a) {
-    yfwd_body<LOGP>(p, a, blockIdx.x, blockIdx.y);
-}
-template <int LOGP>
-__global__ void __launch_bounds__(CS<LOGP, tz_of(LOGP)>::NT, CS<LOGP, tz_of(LOGP)>::MINB)
-kb_yfwd(const HotParams* __restrict__ ps, const int4* __restrict__ work, LaunchArgs a) {
-    const int4 w = work[blockIdx.x];
-    __shared__ HotParams s_hp;
-    load_params(ps + w.x, &s_hp);
-    yfwd_body<LOGP>(s_hp, a, w.y, w.z);
-}
-
 // 3-D: y inverse pass.  s2 [c][kx][ky][z]  ->  s1 [c][kx][z][y]
 template <int LOGP>
-__device__ __forceinline__ void yinv_body(const HotParams& p, const LaunchArgs& a, int bx, int by) {
+__device__ __forceinline__ void yinv_body_s(const HotParams& p, const LaunchArgs& a, int bx, int by) {
     constexpr int TZ = tz_of(LOGP);
     using S = CS<LOGP, TZ>;
     extern __shared__ float2 sm[];
@@ -436,13 +426,144 @@ __device__ __forceinline__ void yinv_body(const HotParams& p, const LaunchArgs& 
     }
 }
 
+// 3-D y passes in the register style of the column pass (P >= 64): a block
+// holds TZ z lines of one kx; each thread owns the same radix-8 butterflies
+// of the three component lines of one z.  The forward pass's first radix-8
+// pass reads s1 directly (y contiguous) and its output goes through shared
+// memory to the z-contiguous s2; the inverse pass reads s2 through shared
+// memory and writes s1 from the registers of its last pass.  TZ equals
+// tz_of(LOGP) for these lengths, so the s2 padding and the grid are unchanged.
 template <int LOGP>
-__global__ void __launch_bounds__(CS<LOGP, tz_of(LOGP)>::NT, CS<LOGP, tz_of(LOGP)>::MINB)
+struct YR {
+    using PL = r8::Plan8<LOGP>;
+    static constexpr int P = PL::P, NB = PL::NB, LS = PL::LS;
+    static constexpr int TZ = NB >= 256 ? 1 : (256 / NB > 8 ? 8 : 256 / NB);
+    static constexpr int NT = (TZ * NB + 31) / 32 * 32 < 64 ? 64 : (TZ * NB + 31) / 32 * 32;
+    static constexpr int NL = 3 * TZ;
+    static constexpr int LASTF = PL::NPASS - 1;
+    static constexpr int MINB = NT >= 256 ? 3 : 1024 / NT;
+    static constexpr size_t SMEM = (size_t)NL * LS * sizeof(float2);
+};
+
+// launch shape of the y passes (either style), shared with the host
+template <int LOGP>
+struct YS {
+    static constexpr bool REG = LOGP >= XREG_MIN_LOGP;
+    static constexpr int TZ = tz_of(LOGP);
+    static constexpr int NT = REG ? YR<LOGP>::NT : CS<LOGP, tz_of(LOGP)>::NT;
+    static constexpr int MINB = REG ? YR<LOGP>::MINB : CS<LOGP, tz_of(LOGP)>::MINB;
+    static constexpr size_t SMEM = REG ? YR<LOGP>::SMEM
+                                       : (size_t)CS<LOGP, tz_of(LOGP)>::NL * CS<LOGP, tz_of(LOGP)>::LS * sizeof(float2);
+    static_assert(!REG || YR<LOGP>::TZ == tz_of(LOGP), "y tile must match the s2 padding");
+};
+
+template <int LOGP>
+__device__ __forceinline__ void yfwd_r_body(const HotParams& p, const LaunchArgs& a, int bx, int by) {
+    using S = YR<LOGP>;
+    extern __shared__ float2 sm[];
+    const int kx = bx, z0 = by * S::TZ;
+    if (a.mode != LM_EVAL && p.st->done) return;
+    const int HX = p.hx, NY = p.ny, NZ = p.nz;
+    const int tid = threadIdx.x;
+    int zt = tid / S::NB;
+    const int j = tid - zt * S::NB;
+    const bool act = zt < S::TZ;
+    if (!act) zt = 0;
+    const int z = z0 + zt;
+    float2* lines[3] = {sm + (0 * S::TZ + zt) * S::LS, sm + (1 * S::TZ + zt) * S::LS,
+                        sm + (2 * S::TZ + zt) * S::LS};
+    float2 v[3][8];
+    if (act) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int y = r8::in_pos<LOGP, false, 0>(j, i);
+                v[c][i] = (y < NY && z < NZ) ? p.s1[((long long)(c * HX + kx) * NZ + z) * p.nyp + y]
+                                             : make_float2(0.f, 0.f);
+            }
+    }
+    r8::run<LOGP, false, false, 0, 3>(lines, v, j, act, p.tw, false);
+    __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) lines[c][pad(r8::out_pos<LOGP, false, S::LASTF>(j, i))] = v[c][i];
+    }
+    __syncthreads();
+    for (int idx = tid; idx < S::NL * S::P; idx += S::NT) {
+        const int zz = idx % S::TZ, r = idx / S::TZ, ky = r & (S::P - 1), c = r >> LOGP;
+        p.s2[((long long)(c * HX + kx) * S::P + ky) * p.nzp + z0 + zz] = sm[(c * S::TZ + zz) * S::LS + pad(ky)];
+    }
+}
+
+template <int LOGP>
+__device__ __forceinline__ void yinv_r_body(const HotParams& p, const LaunchArgs& a, int bx, int by) {
+    using S = YR<LOGP>;
+    extern __shared__ float2 sm[];
+    const int kx = bx, z0 = by * S::TZ;
+    if (a.mode != LM_EVAL && p.st->done) return;
+    const int HX = p.hx, NY = p.ny, NZ = p.nz;
+    for (int idx = threadIdx.x; idx < S::NL * S::P; idx += S::NT) {
+        const int zz = idx % S::TZ, r = idx / S::TZ, ky = r & (S::P - 1), c = r >> LOGP;
+        sm[(c * S::TZ + zz) * S::LS + pad(ky)] = p.s2[((long long)(c * HX + kx) * S::P + ky) * p.nzp + z0 + zz];
+    }
+    __syncthreads();
+    const int tid = threadIdx.x;
+    int zt = tid / S::NB;
+    const int j = tid - zt * S::NB;
+    const bool act = zt < S::TZ;
+    if (!act) zt = 0;
+    const int z = z0 + zt;
+    float2* lines[3] = {sm + (0 * S::TZ + zt) * S::LS, sm + (1 * S::TZ + zt) * S::LS,
+                        sm + (2 * S::TZ + zt) * S::LS};
+    float2 v[3][8];
+    r8::run<LOGP, true, true, 0, 3>(lines, v, j, act, p.tw, true);
+    if (act && z < NZ) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int y = r8::out_pos<LOGP, true, S::LASTF>(j, i);
+                if (y < NY) p.s1[((long long)(c * HX + kx) * NZ + z) * p.nyp + y] = v[c][i];
+            }
+    }
+}
+
+template <int LOGP>
+__device__ __forceinline__ void yfwd_body(const HotParams& p, const LaunchArgs& a, int bx, int by) {
+    if constexpr (YS<LOGP>::REG) yfwd_r_body<LOGP>(p, a, bx, by);
+    else yfwd_body_s<LOGP>(p, a, bx, by);
+}
+template <int LOGP>
+__device__ __forceinline__ void yinv_body(const HotParams& p, const LaunchArgs& a, int bx, int by) {
+    if constexpr (YS<LOGP>::REG) yinv_r_body<LOGP>(p, a, bx, by);
+    else yinv_body_s<LOGP>(p, a, bx, by);
+}
+
+
+template <int LOGP>
+__global__ void __launch_bounds__(YS<LOGP>::NT, YS<LOGP>::MINB)
+k_yfwd(HotParams p, LaunchArgs a) {
+    yfwd_body<LOGP>(p, a, blockIdx.x, blockIdx.y);
+}
+template <int LOGP>
+__global__ void __launch_bounds__(YS<LOGP>::NT, YS<LOGP>::MINB)
+kb_yfwd(const HotParams* __restrict__ ps, const int4* __restrict__ work, LaunchArgs a) {
+    const int4 w = work[blockIdx.x];
+    __shared__ HotParams s_hp;
+    load_params(ps + w.x, &s_hp);
+    yfwd_body<LOGP>(s_hp, a, w.y, w.z);
+}
+
+template <int LOGP>
+__global__ void __launch_bounds__(YS<LOGP>::NT, YS<LOGP>::MINB)
 k_yinv(HotParams p, LaunchArgs a) {
     yinv_body<LOGP>(p, a, blockIdx.x, blockIdx.y);
 }
 template <int LOGP>
-__global__ void __launch_bounds__(CS<LOGP, tz_of(LOGP)>::NT, CS<LOGP, tz_of(LOGP)>::MINB)
+__global__ void __launch_bounds__(YS<LOGP>::NT, YS<LOGP>::MINB)
 kb_yinv(const HotParams* __restrict__ ps, const int4* __restrict__ work, LaunchArgs a) {
     const int4 w = work[blockIdx.x];
     __shared__ HotParams s_hp;
@@ -925,7 +1046,6 @@ __global__ void __launch_bounds__(XS<LOGP>::NT, XS<LOGP>::MINB) k_xinv_local(Hot
 // global memory directly (unpacking each row pair's two real spectra into one
 // complex line), and the forward transform of the next evaluation's input
 // starts from the epilogue's output.
-constexpr int XREG_MIN_LOGP = 6;
 // FFT lengths the batched passes are compiled for: 2^6..2^10 along x and y,
 // 2^1..2^10 along z
 constexpr int BATCH_MIN_LOGP = 6, BATCH_MAX_LOGP = 10;
@@ -1274,9 +1394,9 @@ static void launch_y(const HotParams& p, const LaunchArgs& a, int pass, cudaStre
         const dim3 g((p.hx + S::COLS - 1) / S::COLS);
         k_colconv<L, 0><<<g, S::NT, (size_t)3 * S::COLS * S::LS * sizeof(float2), s>>>(p, a);
     } else {
-        using S = CS<L, tz_of(L)>;
+        using S = YS<L>;
         const dim3 g(p.hx, (p.nz + tz_of(L) - 1) / tz_of(L));
-        const size_t sm = (size_t)S::NL * S::LS * sizeof(float2);
+        const size_t sm = S::SMEM;
         if (pass == PASS_YFWD) k_yfwd<L><<<g, S::NT, sm, s>>>(p, a);
         else k_yinv<L><<<g, S::NT, sm, s>>>(p, a);
     }
@@ -1442,8 +1562,8 @@ static cudaError_t launch_b(const HotParams* ps, const int4* work, int nb, const
                 kb_colconv<L, 0><<<nb, CC<L>::NT, (size_t)3 * CC<L>::COLS * CC<L>::LS * sizeof(float2), s>>>(ps, work, a);
                 return cudaSuccess;
             case PASS_YFWD: case PASS_YINV: {
-                using S = CS<L, tz_of(L)>;
-                const size_t sm = (size_t)S::NL * S::LS * sizeof(float2);
+                using S = YS<L>;
+                const size_t sm = S::SMEM;
                 if (pass == PASS_YFWD) kb_yfwd<L><<<nb, S::NT, sm, s>>>(ps, work, a);
                 else kb_yinv<L><<<nb, S::NT, sm, s>>>(ps, work, a);
                 return cudaSuccess;

@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 MAT = dict(Ms=8e5, Aex=1.3e-11, Ku=5e3, easy_axis=(1.0, 2.0, 3.0), alpha=0.1, B=(0.01, -0.02, 0.03))
 
 SHAPES = [(1, 1, 1), (2, 1, 1), (1, 7, 1), (3, 5, 1), (5, 3, 2), (7, 8, 3), (8, 8, 1), (33, 7, 1),
-          (64, 16, 1), (16, 12, 3), (100, 37, 1), (31, 17, 5)]
+          (64, 16, 1), (16, 12, 3), (100, 37, 1), (31, 17, 5), (20, 70, 3), (40, 33, 2)]
 
 
 def _compare(shape, cell, pbc=(0, 0, 0), images=10, demag=True, seed=0, mat=MAT):
