@@ -111,6 +111,20 @@ def _dist():
     return ws, rank
 
 
+def aggregate_ranks(ms, cell_evals, device):
+    """Replicas: the job's time is the slowest rank's, its work the sum of all
+    ranks' cell-evaluations.  Returns (max ms, whole-job cell-evals/s)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms, cell_evals], device=device, dtype=torch.float64)
+    mx = t[:1].clone()
+    tot = t[1:].clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    ms_max = float(mx[0])
+    return ms_max, float(tot[0]) / (ms_max * 1e-3)
+
+
 HOT_SOURCES = ("fft32.cuh", "hotpath.cu", "mm_internal.cuh")   # the kernels of the timed step
 
 
@@ -274,17 +288,10 @@ def run_gpu(args):
         te = time.perf_counter() - te
         del e0
 
-    value_local = evals * N / (gpu_ms * 1e-3)
     if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([gpu_ms, float(evals * N)], device="cuda", dtype=torch.float64)
-        mx = t.clone()
-        dist.all_reduce(mx[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        gpu_ms_max, total_cells = float(mx[0]), float(t[1])
-        value = total_cells / (gpu_ms_max * 1e-3)
+        gpu_ms_max, value = aggregate_ranks(gpu_ms, float(evals * N), "cuda")
     else:
-        gpu_ms_max, value = gpu_ms, value_local
+        gpu_ms_max, value = gpu_ms, evals * N / (gpu_ms * 1e-3)
     if rank != 0:
         return None
 
