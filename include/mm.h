@@ -350,6 +350,20 @@ int mm_batch_advance(mm_batch* b, int method, long nsteps, double dt_s, double t
 int mm_batch_get_stats(mm_batch* b, mm_stats* out);
 int mm_batch_relax(mm_batch* b, float* const* m, double torque_tol, double err_tol, long max_steps,
                    long* steps_out, double* torque_out, int* n_converged);
+/*
+ * Batch autotuner.  Every batched FFT pass is compiled with two register
+ * budgets (an occupancy-first one and one of at least 80 registers per
+ * thread, fewer resident blocks); where they differ, the batch times both on
+ * its samples when it builds its launch lists (first advance, and after
+ * finished samples leave a relaxation) and keeps the faster.  Choices are
+ * cached for the process, keyed by pass, FFT length and block count (power of
+ * two).  mode 1 (default) tunes, 0 always launches the default budget, 2 the
+ * other budget wherever there is one (for tests; results are the same).
+ * mm_batch_tuning reports the current launch groups, how many of them had two
+ * budgets, and how many run the second.
+ */
+int mm_batch_set_tuning(mm_batch* b, int mode);
+int mm_batch_tuning(const mm_batch* b, int* n_groups, int* n_tunable, int* n_alternative);
 const char* mm_batch_last_error(const mm_batch* b);
 void mm_batch_destroy(mm_batch* b);
 

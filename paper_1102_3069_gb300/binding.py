@@ -78,6 +78,8 @@ _SIGS = {
     "mm_batch_get_stats": (_i, [_vp, ctypes.POINTER(mm_stats)]),
     "mm_batch_relax": (_i, [_vp, ctypes.POINTER(_vp), _d, _d, _l, ctypes.POINTER(_l), _dp,
                             ctypes.POINTER(_i)]),
+    "mm_batch_set_tuning": (_i, [_vp, _i]),
+    "mm_batch_tuning": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "mm_batch_last_error": (ctypes.c_char_p, [_vp]),
     "mm_batch_destroy": (None, [_vp]),
 }
@@ -347,6 +349,17 @@ def mm_batch_relax(b, ms, torque_tol=1e-4, err_tol=1e-5, max_steps=100000, check
     if check and rc not in (MM_OK, MM_ENOTCONVERGED):
         _bcheck(b, rc)
     return rc, list(steps), list(tq), conv.value
+
+
+def mm_batch_set_tuning(b, mode):
+    return _bcheck(b, lib().mm_batch_set_tuning(b, int(mode)))
+
+
+def mm_batch_tuning(b):
+    """(launch groups, groups with two register budgets, groups running the second)."""
+    g, t, a = _i(0), _i(0), _i(0)
+    _bcheck(b, lib().mm_batch_tuning(b, ctypes.byref(g), ctypes.byref(t), ctypes.byref(a)))
+    return g.value, t.value, a.value
 
 
 def mm_batch_last_error(b):

@@ -7,8 +7,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -989,8 +991,9 @@ struct mm_batch {
     size_t max_work = 0;                      // int4 entries for all samples
     std::vector<mm::HotParams> hp;            // host copies of the device descriptors
     std::vector<int> active;                  // samples in the current work lists
-    struct Group { int pass, logp, nb; size_t off; };
+    struct Group { int pass, logp, nb; size_t off; int variant; };
     std::vector<Group> groups;
+    int tune_mode = 1;                        // 0 default kernels, 1 autotune, 2 alternative budget everywhere
     bool groups_ready = false;
     bool loaded = false;
     bool k1_valid = false;
@@ -1033,10 +1036,55 @@ int batch_work(mm_batch* b, const std::vector<int>& which, std::vector<int4>* ou
         }
         for (int lp = 0; lp < 16; ++lp) {
             if (by_logp[lp].empty()) continue;
-            if (groups) groups->push_back({pass, lp, (int)by_logp[lp].size(), out->size()});
+            if (groups) groups->push_back({pass, lp, (int)by_logp[lp].size(), out->size(), 0});
             out->insert(out->end(), by_logp[lp].begin(), by_logp[lp].end());
         }
     }
+    return MM_OK;
+}
+
+// Autotuner: each batched FFT pass is compiled with two register budgets
+// (mm::batch_variants); for every group (pass, FFT length) whose budgets
+// differ, time both on the loaded samples and keep the faster.  Choices are
+// cached for the process, keyed by pass, FFT length and the power of two of
+// the group's block count.  The timing launches run in evaluation mode and
+// write only scratch (spectra, H_demag), which the next k1 pass rewrites.
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, int, int>, int> g_tune_cache;
+
+int batch_tune(mm_batch* b) {
+    if (b->tune_mode == 0 || b->active.empty()) return MM_OK;
+    const mm::LaunchArgs a = make_args(b->hp[b->active[0]], mm::SRC_CUR, mm::LM_EVAL, 0, false, false);
+    const mm::HotParams* ps = reinterpret_cast<const mm::HotParams*>(b->ws + b->off_ps);
+    const int4* work = reinterpret_cast<const int4*>(b->ws + b->off_work);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    for (auto& g : b->groups) {
+        if (mm::batch_variants(g.pass, g.logp) < 2) continue;
+        if (b->tune_mode == 2) { g.variant = 1; continue; }
+        const auto key = std::make_tuple(g.pass, g.logp, ilog2(g.nb));
+        {
+            std::lock_guard<std::mutex> lock(g_tune_mutex);
+            auto it = g_tune_cache.find(key);
+            if (it != g_tune_cache.end()) { g.variant = it->second; continue; }
+        }
+        if (!e0) { BCK(cudaEventCreate(&e0)); BCK(cudaEventCreate(&e1)); }
+        float best = 0.f;
+        int pick = 0;
+        for (int v = 0; v < 2; ++v) {
+            BCK(mm::launch_pass_batched(ps, work + g.off, g.nb, a, g.pass, g.logp, v, b->stream));   // warm-up
+            BCK(cudaEventRecord(e0, b->stream));
+            for (int r = 0; r < 3; ++r) BCK(mm::launch_pass_batched(ps, work + g.off, g.nb, a, g.pass, g.logp, v, b->stream));
+            BCK(cudaEventRecord(e1, b->stream));
+            BCK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            BCK(cudaEventElapsedTime(&ms, e0, e1));
+            if (v == 0 || ms < best) { best = ms; pick = v; }
+        }
+        g.variant = pick;
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune_cache[key] = pick;
+    }
+    if (e0) { cudaEventDestroy(e0); cudaEventDestroy(e1); }
     return MM_OK;
 }
 
@@ -1052,6 +1100,8 @@ int batch_build_groups(mm_batch* b) {
                             b->stream));
     BCK(cudaStreamSynchronize(b->stream));    // the host vector goes out of scope
     b->groups = groups;
+    int rc2 = batch_tune(b);
+    if (rc2) return rc2;
     b->groups_ready = true;
     if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
     return MM_OK;
@@ -1064,7 +1114,7 @@ int batch_eval(mm_batch* b, int src, int mode, int stage, bool fuse, bool have_s
     for (const auto& g : b->groups) {
         if (g.pass == mm::PASS_XFWD && have_spectrum) continue;
         if (g.pass == mm::PASS_XFWD_NEXT && !fuse) continue;
-        BCK(mm::launch_pass_batched(ps, work + g.off, g.nb, a, g.pass, g.logp, b->stream));
+        BCK(mm::launch_pass_batched(ps, work + g.off, g.nb, a, g.pass, g.logp, g.variant, b->stream));
     }
     return MM_OK;
 }
@@ -1340,6 +1390,31 @@ int mm_batch_relax(mm_batch* b, float* const* m, double torque_tol, double err_t
     b->active = all;
     b->groups_ready = false;
     if (conv < n) return bfail(b, MM_ENOTCONVERGED, std::to_string(n - conv) + " samples did not reach the torque bound");
+    return MM_OK;
+}
+
+int mm_batch_set_tuning(mm_batch* b, int mode) {
+    if (!b) return MM_EINVAL;
+    if (mode < 0 || mode > 2) return bfail(b, MM_EINVAL, "tuning mode must be 0, 1 or 2");
+    if (mode != b->tune_mode) {
+        b->tune_mode = mode;
+        b->groups_ready = false;                     // chosen again at the next advance
+        if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+    }
+    return MM_OK;
+}
+
+int mm_batch_tuning(const mm_batch* b, int* n_groups, int* n_tunable, int* n_alternative) {
+    if (!b) return MM_EINVAL;
+    int g = 0, t = 0, alt = 0;
+    for (const auto& gr : b->groups) {
+        ++g;
+        t += mm::batch_variants(gr.pass, gr.logp) > 1;
+        alt += gr.variant != 0;
+    }
+    if (n_groups) *n_groups = g;
+    if (n_tunable) *n_tunable = t;
+    if (n_alternative) *n_alternative = alt;
     return MM_OK;
 }
 

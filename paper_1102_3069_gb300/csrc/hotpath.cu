@@ -270,6 +270,11 @@ struct CC {
     static constexpr int COLS = NB >= 256 ? 1 : (256 / NB > 64 ? 64 : 256 / NB);
     static constexpr int NT = (COLS * NB + 31) / 32 * 32 < 64 ? 64 : (COLS * NB + 31) / 32 * 32;
     static constexpr int LASTF = PL::NPASS > 0 ? PL::NPASS - 1 : 0;
+    // resident blocks per SM the compiler is asked for: the default (up to
+    // 85 registers for 256 threads) and, for the batched autotuner, a budget
+    // of at least 128 registers per thread
+    static constexpr int MINB0 = NT <= 256 ? 3 : 1;
+    static constexpr int MINB1 = 65536 / (NT * 128) > 0 ? 65536 / (NT * 128) : 1;
 };
 
 template <int LOGP, bool REV>
@@ -369,8 +374,8 @@ template <int LOGP, int MODE>
 __global__ void __launch_bounds__(CC<LOGP>::NT, CC<LOGP>::NT <= 256 ? 3 : 1) k_colconv(HotParams p, LaunchArgs a) {
     colconv_body<LOGP, MODE>(p, a, blockIdx.x, blockIdx.y);
 }
-template <int LOGP, int MODE>
-__global__ void __launch_bounds__(CC<LOGP>::NT, CC<LOGP>::NT <= 256 ? 3 : 1)
+template <int LOGP, int MODE, int V>
+__global__ void __launch_bounds__(CC<LOGP>::NT, V ? CC<LOGP>::MINB1 : CC<LOGP>::MINB0)
 kb_colconv(const HotParams* __restrict__ ps, const int4* __restrict__ work, LaunchArgs a) {
     const int4 w = work[blockIdx.x];
     __shared__ HotParams s_hp;
@@ -442,6 +447,7 @@ struct YR {
     static constexpr int NL = 3 * TZ;
     static constexpr int LASTF = PL::NPASS - 1;
     static constexpr int MINB = NT >= 256 ? 3 : 1024 / NT;
+    static constexpr int MINB1 = NT >= 256 ? 3 : 65536 / (NT * 80);   // >= 80 registers (autotuner)
     static constexpr size_t SMEM = (size_t)NL * LS * sizeof(float2);
 };
 
@@ -452,6 +458,7 @@ struct YS {
     static constexpr int TZ = tz_of(LOGP);
     static constexpr int NT = REG ? YR<LOGP>::NT : CS<LOGP, tz_of(LOGP)>::NT;
     static constexpr int MINB = REG ? YR<LOGP>::MINB : CS<LOGP, tz_of(LOGP)>::MINB;
+    static constexpr int MINB1 = REG ? YR<LOGP>::MINB1 : CS<LOGP, tz_of(LOGP)>::MINB;
     static constexpr size_t SMEM = REG ? YR<LOGP>::SMEM
                                        : (size_t)CS<LOGP, tz_of(LOGP)>::NL * CS<LOGP, tz_of(LOGP)>::LS * sizeof(float2);
     static_assert(!REG || YR<LOGP>::TZ == tz_of(LOGP), "y tile must match the s2 padding");
@@ -548,8 +555,8 @@ __global__ void __launch_bounds__(YS<LOGP>::NT, YS<LOGP>::MINB)
 k_yfwd(HotParams p, LaunchArgs a) {
     yfwd_body<LOGP>(p, a, blockIdx.x, blockIdx.y);
 }
-template <int LOGP>
-__global__ void __launch_bounds__(YS<LOGP>::NT, YS<LOGP>::MINB)
+template <int LOGP, int V>
+__global__ void __launch_bounds__(YS<LOGP>::NT, V ? YS<LOGP>::MINB1 : YS<LOGP>::MINB)
 kb_yfwd(const HotParams* __restrict__ ps, const int4* __restrict__ work, LaunchArgs a) {
     const int4 w = work[blockIdx.x];
     __shared__ HotParams s_hp;
@@ -562,8 +569,8 @@ __global__ void __launch_bounds__(YS<LOGP>::NT, YS<LOGP>::MINB)
 k_yinv(HotParams p, LaunchArgs a) {
     yinv_body<LOGP>(p, a, blockIdx.x, blockIdx.y);
 }
-template <int LOGP>
-__global__ void __launch_bounds__(YS<LOGP>::NT, YS<LOGP>::MINB)
+template <int LOGP, int V>
+__global__ void __launch_bounds__(YS<LOGP>::NT, V ? YS<LOGP>::MINB1 : YS<LOGP>::MINB)
 kb_yinv(const HotParams* __restrict__ ps, const int4* __restrict__ work, LaunchArgs a) {
     const int4 w = work[blockIdx.x];
     __shared__ HotParams s_hp;
@@ -1064,6 +1071,7 @@ struct XR {
     static constexpr int NL = 3 * PAIRS;
     static constexpr int LASTF = PL::NPASS - 1;
     static constexpr int MINB = NT >= 256 ? XR_MINB256 : 1024 / NT;
+    static constexpr int MINB1 = NT >= 256 ? XR_MINB256 : 65536 / (NT * 80);   // >= 80 registers (autotuner)
     static constexpr size_t SMEM = (size_t)NL * LS * sizeof(float2);
 };
 
@@ -1157,8 +1165,8 @@ template <int LOGP>
 __global__ void __launch_bounds__(XR<LOGP>::NT, XR<LOGP>::MINB) k_xfwd_r(HotParams p, LaunchArgs a) {
     xfwd_r_body<LOGP>(p, a, blockIdx.x, blockIdx.y);
 }
-template <int LOGP>
-__global__ void __launch_bounds__(XR<LOGP>::NT, XR<LOGP>::MINB)
+template <int LOGP, int V>
+__global__ void __launch_bounds__(XR<LOGP>::NT, V ? XR<LOGP>::MINB1 : XR<LOGP>::MINB)
 kb_xfwd_r(const HotParams* __restrict__ ps, const int4* __restrict__ work, LaunchArgs a) {
     const int4 w = work[blockIdx.x];
     __shared__ HotParams s_hp;
@@ -1222,8 +1230,8 @@ template <int LOGP>
 __global__ void __launch_bounds__(XR<LOGP>::NT, XR<LOGP>::MINB) k_xinv_h(HotParams p, LaunchArgs a) {
     xinv_h_body<LOGP>(p, a, blockIdx.x, blockIdx.y);
 }
-template <int LOGP>
-__global__ void __launch_bounds__(XR<LOGP>::NT, XR<LOGP>::MINB)
+template <int LOGP, int V>
+__global__ void __launch_bounds__(XR<LOGP>::NT, V ? XR<LOGP>::MINB1 : XR<LOGP>::MINB)
 kb_xinv_h(const HotParams* __restrict__ ps, const int4* __restrict__ work, LaunchArgs a) {
     const int4 w = work[blockIdx.x];
     __shared__ HotParams s_hp;
@@ -1334,6 +1342,17 @@ __global__ void k_copy_out(HotParams p, float* __restrict__ m_user) {
 
 // ---------------------------------------------------------------------------
 // launch helpers
+template <int L, int V>
+static cudaError_t set_attr_batched_xy() {
+    cudaError_t e;
+    const int mx = 200 * 1024;
+    if ((e = cudaFuncSetAttribute(kb_xfwd_r<L, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(kb_xinv_h<L, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(kb_colconv<L, 0, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(kb_yfwd<L, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    return cudaFuncSetAttribute(kb_yinv<L, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+}
+
 template <int L>
 static cudaError_t set_attr_all() {
     cudaError_t e;
@@ -1350,14 +1369,12 @@ static cudaError_t set_attr_all() {
         if ((e = cudaFuncSetAttribute(k_xinv_h<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     }
     if constexpr (L >= BATCH_MIN_LOGP && L <= BATCH_MAX_LOGP) {
-        if ((e = cudaFuncSetAttribute(kb_xfwd_r<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
-        if ((e = cudaFuncSetAttribute(kb_xinv_h<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
-        if ((e = cudaFuncSetAttribute(kb_colconv<L, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
-        if ((e = cudaFuncSetAttribute(kb_yfwd<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
-        if ((e = cudaFuncSetAttribute(kb_yinv<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+        if ((e = set_attr_batched_xy<L, 0>())) return e;
+        if ((e = set_attr_batched_xy<L, 1>())) return e;
     }
     if constexpr (L >= 1 && L <= BATCH_MAX_LOGP) {
-        if ((e = cudaFuncSetAttribute(kb_colconv<L, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+        if ((e = cudaFuncSetAttribute(kb_colconv<L, 1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+        if ((e = cudaFuncSetAttribute(kb_colconv<L, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     }
     if constexpr (L > 0) return set_attr_all<L - 1>();
     return cudaSuccess;
@@ -1419,6 +1436,18 @@ static void launch_z(const HotParams& p, const LaunchArgs& a, cudaStream_t s) {
         case 10: CALL(10); break; case 11: CALL(11); break;                 \
         case 12: CALL(12); break;                                           \
         default: return cudaErrorInvalidValue;                              \
+    }
+
+#define MM_LOGP_SWITCH_INT(LOGP, CALL)                                      \
+    switch (LOGP) {                                                         \
+        case 0: CALL(0); break;   case 1: CALL(1); break;                   \
+        case 2: CALL(2); break;   case 3: CALL(3); break;                   \
+        case 4: CALL(4); break;   case 5: CALL(5); break;                   \
+        case 6: CALL(6); break;   case 7: CALL(7); break;                   \
+        case 8: CALL(8); break;   case 9: CALL(9); break;                   \
+        case 10: CALL(10); break; case 11: CALL(11); break;                 \
+        case 12: CALL(12); break;                                           \
+        default: break;                                                     \
     }
 
 int eval_passes(const HotParams& p, const LaunchArgs& a, int* ids) {
@@ -1541,31 +1570,31 @@ cudaError_t batch_pass_grid(const HotParams& p, int pass, int* gx, int* gy) {
     }
 }
 
-template <int L>
+template <int L, int V>
 static cudaError_t launch_b(const HotParams* ps, const int4* work, int nb, const LaunchArgs& a, int pass,
                             cudaStream_t s) {
     if constexpr (L >= BATCH_MIN_LOGP && L <= BATCH_MAX_LOGP) {
         switch (pass) {
             case PASS_XFWD:
-                kb_xfwd_r<L><<<nb, XR<L>::NT, XR<L>::SMEM, s>>>(ps, work, a);
+                kb_xfwd_r<L, V><<<nb, XR<L>::NT, XR<L>::SMEM, s>>>(ps, work, a);
                 return cudaSuccess;
             case PASS_XFWD_NEXT: {
                 LaunchArgs b = a;
                 b.src = a.next_src;
-                kb_xfwd_r<L><<<nb, XR<L>::NT, XR<L>::SMEM, s>>>(ps, work, b);
+                kb_xfwd_r<L, V><<<nb, XR<L>::NT, XR<L>::SMEM, s>>>(ps, work, b);
                 return cudaSuccess;
             }
             case PASS_XINV_H:
-                kb_xinv_h<L><<<nb, XR<L>::NT, XR<L>::SMEM, s>>>(ps, work, a);
+                kb_xinv_h<L, V><<<nb, XR<L>::NT, XR<L>::SMEM, s>>>(ps, work, a);
                 return cudaSuccess;
             case PASS_YCONV:
-                kb_colconv<L, 0><<<nb, CC<L>::NT, (size_t)3 * CC<L>::COLS * CC<L>::LS * sizeof(float2), s>>>(ps, work, a);
+                kb_colconv<L, 0, V><<<nb, CC<L>::NT, (size_t)3 * CC<L>::COLS * CC<L>::LS * sizeof(float2), s>>>(ps, work, a);
                 return cudaSuccess;
             case PASS_YFWD: case PASS_YINV: {
                 using S = YS<L>;
                 const size_t sm = S::SMEM;
-                if (pass == PASS_YFWD) kb_yfwd<L><<<nb, S::NT, sm, s>>>(ps, work, a);
-                else kb_yinv<L><<<nb, S::NT, sm, s>>>(ps, work, a);
+                if (pass == PASS_YFWD) kb_yfwd<L, V><<<nb, S::NT, sm, s>>>(ps, work, a);
+                else kb_yinv<L, V><<<nb, S::NT, sm, s>>>(ps, work, a);
                 return cudaSuccess;
             }
             default: break;
@@ -1573,7 +1602,7 @@ static cudaError_t launch_b(const HotParams* ps, const int4* work, int nb, const
     }
     if constexpr (L >= 1 && L <= BATCH_MAX_LOGP) {
         if (pass == PASS_ZCONV) {
-            kb_colconv<L, 1><<<nb, CC<L>::NT, (size_t)3 * CC<L>::COLS * CC<L>::LS * sizeof(float2), s>>>(ps, work, a);
+            kb_colconv<L, 1, V><<<nb, CC<L>::NT, (size_t)3 * CC<L>::COLS * CC<L>::LS * sizeof(float2), s>>>(ps, work, a);
             return cudaSuccess;
         }
     }
@@ -1581,18 +1610,49 @@ static cudaError_t launch_b(const HotParams* ps, const int4* work, int nb, const
 }
 
 cudaError_t launch_pass_batched(const HotParams* ps, const int4* work, int nb, const LaunchArgs& a, int pass,
-                                int logp, cudaStream_t s) {
+                                int logp, int variant, cudaStream_t s) {
     if (nb <= 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
     if (pass == PASS_LOCAL_H) {
         kb_local<<<nb, 256, 0, s>>>(ps, work, a);
         return cudaGetLastError();
     }
-#define MM_CALL_B(L) e = launch_b<L>(ps, work, nb, a, pass, s)
-    MM_LOGP_SWITCH(logp, MM_CALL_B)
+    if (variant) {
+#define MM_CALL_B(L) e = launch_b<L, 1>(ps, work, nb, a, pass, s)
+        MM_LOGP_SWITCH(logp, MM_CALL_B)
 #undef MM_CALL_B
+    } else {
+#define MM_CALL_B(L) e = launch_b<L, 0>(ps, work, nb, a, pass, s)
+        MM_LOGP_SWITCH(logp, MM_CALL_B)
+#undef MM_CALL_B
+    }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
+}
+
+// number of compiled register budgets of a batched pass at this FFT length
+// (1 where both budgets give the same kernel)
+int batch_variants(int pass, int logp) {
+    int n = 1;
+    switch (pass) {
+        case PASS_XFWD: case PASS_XFWD_NEXT: case PASS_XINV_H:
+#define MM_V(L) n = XR<L>::MINB1 != XR<L>::MINB ? 2 : 1
+            MM_LOGP_SWITCH_INT(logp, MM_V)
+#undef MM_V
+            break;
+        case PASS_YCONV: case PASS_ZCONV:
+#define MM_V(L) n = CC<L>::MINB1 != CC<L>::MINB0 ? 2 : 1
+            MM_LOGP_SWITCH_INT(logp, MM_V)
+#undef MM_V
+            break;
+        case PASS_YFWD: case PASS_YINV:
+#define MM_V(L) n = YS<L>::MINB1 != YS<L>::MINB ? 2 : 1
+            MM_LOGP_SWITCH_INT(logp, MM_V)
+#undef MM_V
+            break;
+        default: break;
+    }
+    return n;
 }
 
 // copies every sample's DevState into one array (one thread per sample)

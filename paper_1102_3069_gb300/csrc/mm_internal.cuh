@@ -153,7 +153,8 @@ bool batch_supported(const HotParams& p);
 int batch_pass_logp(const HotParams& p, int pass);
 cudaError_t batch_pass_grid(const HotParams& p, int pass, int* gx, int* gy);
 cudaError_t launch_pass_batched(const HotParams* ps, const int4* work, int nb, const LaunchArgs& a, int pass,
-                                int logp, cudaStream_t s);
+                                int logp, int variant, cudaStream_t s);
+int batch_variants(int pass, int logp);     // 1 or 2 register budgets compiled for this pass
 cudaError_t launch_gather_states(const HotParams* ps, DevState* out, int n, cudaStream_t s);
 
 // kernel setup (setup.cu)

@@ -143,3 +143,32 @@ def test_batch_rejects_unsupported_contexts():
     with pytest.raises(B.MMError) as e:
         B.mm_batch_advance(bt.b, B.MM_RK4, 1, dt_s=1e-14, tol=-1.0)   # thermal field refused in a batch
     assert e.value.code == B.MM_EINVAL
+
+
+def test_batch_autotuner_register_budgets_agree():
+    """The two compiled register budgets of each batched FFT pass run the same
+    block body: forcing the second everywhere changes no result beyond float32
+    rounding, and the autotuner reports which groups it could tune."""
+    import torch
+    samples = inputs.ensemble(6, seed=8, nmin=32, nmax=70, nzmax=3)   # FFT lengths 64..256
+    stream = torch.cuda.Stream()
+    outs, reports = {}, {}
+    with torch.cuda.stream(stream):
+        for mode in (0, 2, 1):
+            sol = _solvers(samples, stream.cuda_stream)
+            m0 = _m0(samples)
+            bt = B.Batch(sol, stream.cuda_stream)
+            B.mm_batch_set_tuning(bt.b, mode)
+            B.mm_batch_load(bt.b, m0)
+            B.mm_batch_advance(bt.b, B.MM_RKDP, 6, dt_s=5e-14, tol=-1.0)
+            out = [torch.empty_like(m) for m in m0]
+            B.mm_batch_store(bt.b, out)
+            torch.cuda.synchronize()
+            outs[mode] = out
+            reports[mode] = B.mm_batch_tuning(bt.b)
+    groups, tunable, alt = reports[2]
+    assert tunable > 0 and alt == tunable and groups >= tunable
+    assert reports[0][2] == 0 and reports[1][1] == tunable
+    for mode in (1, 2):
+        for a, b in zip(outs[0], outs[mode]):
+            assert float((a - b).abs().max()) <= 1e-6
