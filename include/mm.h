@@ -223,6 +223,31 @@ int mm_advance(mm_ctx* ctx, int method, long nsteps, double dt_s, double tol,
 int mm_get_stats(mm_ctx* ctx, mm_stats* stats);
 
 /*
+ * Checkpoint and resume.  mm_get_state copies the current state m (device
+ * SoA, may be NULL) and fills the integrator scalars: simulated time, the
+ * step size the next adaptive step will try, the thermal step counter, the
+ * step and evaluation counters and whether the last attempt was rejected
+ * (synchronises).  mm_set_state loads m exactly as given (no renormalisation)
+ * with those scalars, so that mm_advance(..., dt_s = 0, ...) afterwards
+ * continues the run as if it had not stopped (the first-same-as-last k1 is
+ * evaluated again from m, which gives the same values).  MM_ESTATE without a
+ * loaded state, MM_EINVAL for a checkpoint with negative or non-finite fields.
+ */
+typedef struct mm_checkpoint {
+    double t;               /* simulated time, s                                  */
+    double dt;              /* next adaptive step size, s                         */
+    long long step_index;   /* thermal-noise step counter                         */
+    long long accepted, rejected, evals;
+    int after_reject;       /* the last attempt was rejected (caps the next growth) */
+    int reserved_;
+    double t_internal;      /* t and dt in the library's internal time unit         */
+    double dt_internal;     /* (1/(gamma0 Ms)); used on restore when they agree with  */
+                            /* t and dt, so that the step size is restored exactly    */
+} mm_checkpoint;
+int mm_get_state(mm_ctx* ctx, float* m, mm_checkpoint* out);
+int mm_set_state(mm_ctx* ctx, const float* m, const mm_checkpoint* in);
+
+/*
  * One step (Sec. 2.2) from m (device, in/out): loads m at time *t_s, takes
  * one step of `method` with the proposed/fixed step *dt_s (and error bound
  * tol for MM_RKDP), stores the result back into m and synchronises.

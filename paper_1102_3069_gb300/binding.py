@@ -39,6 +39,13 @@ class mm_stats(ctypes.Structure):
                 ("status", ctypes.c_int), ("done", ctypes.c_int)]
 
 
+class mm_checkpoint(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("dt", ctypes.c_double), ("step_index", ctypes.c_longlong),
+                ("accepted", ctypes.c_longlong), ("rejected", ctypes.c_longlong), ("evals", ctypes.c_longlong),
+                ("after_reject", ctypes.c_int), ("reserved_", ctypes.c_int), ("t_internal", ctypes.c_double),
+                ("dt_internal", ctypes.c_double)]
+
+
 _lib = None
 _vp, _dp, _i, _l, _d, _sz, _u64 = (ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_long,
                                    ctypes.c_double, ctypes.c_size_t, ctypes.c_uint64)
@@ -62,6 +69,8 @@ _SIGS = {
     "mm_advance": (_i, [_vp, _i, _l, _d, _d, _d, _d]),
     "mm_get_stats": (_i, [_vp, ctypes.POINTER(mm_stats)]),
     "mm_step": (_i, [_vp, _vp, _i, _dp, _dp, _d, ctypes.POINTER(_i)]),
+    "mm_get_state": (_i, [_vp, _vp, ctypes.POINTER(mm_checkpoint)]),
+    "mm_set_state": (_i, [_vp, _vp, ctypes.POINTER(mm_checkpoint)]),
     "mm_relax": (_i, [_vp, _vp, _d, _d, _l, ctypes.POINTER(_l), _dp]),
     "mm_run_host": (_i, [_vp, _vp, _i, _l, _d, _d]),
     "mm_eval_heff_static": (_i, [_vp, _vp, _vp, _vp]),
@@ -230,6 +239,19 @@ def mm_get_stats(ctx):
     s = mm_stats()
     _check(ctx, lib().mm_get_stats(ctx, ctypes.byref(s)))
     return {f: getattr(s, f) for f, _ in mm_stats._fields_}
+
+
+def mm_get_state(ctx, m=None):
+    """Checkpoint: copies the state into m (device tensor, optional); returns the scalars as a dict."""
+    c = mm_checkpoint()
+    _check(ctx, lib().mm_get_state(ctx, _ptr(m), ctypes.byref(c)))
+    return {f: getattr(c, f) for f, _ in mm_checkpoint._fields_ if f != "reserved_"}
+
+
+def mm_set_state(ctx, m, cp):
+    c = mm_checkpoint(**{k: cp[k] for k in ("t", "dt", "step_index", "accepted", "rejected", "evals",
+                                            "after_reject", "t_internal", "dt_internal") if k in cp})
+    return _check(ctx, lib().mm_set_state(ctx, _ptr(m), ctypes.byref(c)))
 
 
 def mm_step(ctx, m, method, t_s, dt_s, tol=1e-6):

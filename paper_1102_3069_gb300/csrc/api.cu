@@ -823,6 +823,67 @@ int mm_get_stats(mm_ctx* ctx, mm_stats* stats) {
     return MM_OK;
 }
 
+int mm_get_state(mm_ctx* ctx, float* m, mm_checkpoint* out) {
+    if (!ctx) return MM_EINVAL;
+    if (!ctx->state_loaded) return fail(ctx, MM_ESTATE, "no state loaded (mm_load)");
+    if (!out) return fail(ctx, MM_EINVAL, "null checkpoint");
+    if (m) {
+        mm::HotParams p = hot_params(ctx, 0.0, false);
+        CK(mm::launch_copy_out(p, m, ctx->stream));
+    }
+    mm::DevState h;
+    CK(cudaMemcpyAsync(&h, dstate(ctx), sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const double tu = ctx->gamma0 * ctx->Ms;
+    std::memset(out, 0, sizeof(*out));
+    out->t = h.t / tu;
+    out->dt = h.h / tu;
+    out->step_index = h.step_index;
+    out->accepted = h.accepted;
+    out->rejected = h.rejected;
+    out->evals = h.evals;
+    out->after_reject = h.after_reject;
+    out->t_internal = h.t;
+    out->dt_internal = h.h;
+    return MM_OK;
+}
+
+int mm_set_state(mm_ctx* ctx, const float* m, const mm_checkpoint* in) {
+    int rc = check_ready(ctx, false);
+    if (rc) return rc;
+    if (!m || !in) return fail(ctx, MM_EINVAL, "null argument");
+    if (!std::isfinite(in->t) || !std::isfinite(in->dt) || in->dt < 0.0 || in->step_index < 0 || in->accepted < 0 ||
+        in->rejected < 0 || in->evals < 0)
+        return fail(ctx, MM_EINVAL, "bad checkpoint");
+    const double tu = ctx->gamma0 * ctx->Ms;
+    mm::DevState h;
+    std::memset(&h, 0, sizeof(h));
+    h.t = in->t * tu;
+    h.h = in->dt * tu;
+    // the exact internal values when they are this checkpoint's (same time unit)
+    if (std::isfinite(in->t_internal) && std::fabs(in->t_internal / tu - in->t) <= 1e-12 * std::fabs(in->t) + 1e-300)
+        h.t = in->t_internal;
+    if (std::isfinite(in->dt_internal) && in->dt_internal >= 0.0 &&
+        std::fabs(in->dt_internal / tu - in->dt) <= 1e-12 * in->dt + 1e-300)
+        h.h = in->dt_internal;
+    h.step_index = in->step_index;
+    h.accepted = in->accepted;
+    h.rejected = in->rejected;
+    h.evals = in->evals;
+    h.after_reject = in->after_reject ? 1 : 0;
+    mm::DevState* st = dstate(ctx);
+    CK(cudaMemcpyAsync(st, &h, sizeof(h), cudaMemcpyHostToDevice, ctx->stream));
+    mm::HotParams p = hot_params(ctx, 0.0, false);
+    CK(mm::launch_copy_in(p, m, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));       // h lives on this stack frame
+    ctx->state_loaded = true;
+    ctx->k1_valid = false;
+    ctx->rk_h_set = in->dt > 0.0;
+    ctx->spec = mm_ctx::SPEC_NONE;
+    ctx->step_counter = in->step_index;
+    return MM_OK;
+}
+
 int mm_step(mm_ctx* ctx, float* m, int method, double* t_s, double* dt_s, double tol, int* accepted) {
     if (!ctx) return MM_EINVAL;
     if (!m || !t_s || !dt_s) return fail(ctx, MM_EINVAL, "null argument");

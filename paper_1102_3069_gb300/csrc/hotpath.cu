@@ -1679,6 +1679,18 @@ cudaError_t launch_euler_update(const HotParams& p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// m_user -> state slot 0 as it is (no renormalisation: a checkpoint resumes bit for bit)
+__global__ void k_copy_in(HotParams p, const float* __restrict__ m_user) {
+    const long long n = 3 * p.ncell;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p.ms[0][i] = m_user[i];
+}
+
+cudaError_t launch_copy_in(const HotParams& p, const float* m_user, cudaStream_t s) {
+    k_copy_in<<<4 * 152, 256, 0, s>>>(p, m_user);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_copy_out(const HotParams& p, float* m_user, cudaStream_t s) {
     k_copy_out<<<4 * 152, 256, 0, s>>>(p, m_user);
     return cudaGetLastError();

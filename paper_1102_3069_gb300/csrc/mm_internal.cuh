@@ -141,6 +141,7 @@ enum Pass : int {
 // hot path (hotpath.cu)
 cudaError_t launch_normalize_load(const HotParams& p, const float* m_user, cudaStream_t s);
 cudaError_t launch_copy_out(const HotParams& p, float* m_user, cudaStream_t s);
+cudaError_t launch_copy_in(const HotParams& p, const float* m_user, cudaStream_t s);
 // Euler step with the h its k1 pass set (fixed maximum variation of m per step)
 cudaError_t launch_euler_update(const HotParams& p, cudaStream_t s);
 int eval_passes(const HotParams& p, const LaunchArgs& a, int* ids);     // fills <= 7 pass ids

@@ -250,3 +250,36 @@ def test_max_dm_steps_match_oracle(method, name, shape):
     B.mm_set_max_dm(s.ctx, 0.0)
     with pytest.raises(B.MMError):
         B.mm_advance(s.ctx, method, 1, dt_s=0.0)
+
+
+@pytest.mark.parametrize("method,dt,tol", [(B.MM_RKDP, 0.0, 1e-5), (B.MM_RK23, 0.0, 1e-5), (B.MM_HEUN, 2e-14, 0.0)])
+def test_checkpoint_resumes_bit_for_bit(method, dt, tol):
+    """mm_get_state / mm_set_state: a run stopped after 25 steps and resumed in
+    a fresh context ends exactly where an uninterrupted run of 25 + 20 steps
+    ends (same m bits, same time, step size and counters)."""
+    import torch
+    s1, _ = _pair()
+    m = to_dev(W["m"])
+    first = 1e-13 if dt == 0.0 else dt
+    B.mm_load(s1.ctx, m)
+    B.mm_advance(s1.ctx, method, 25, dt_s=first, tol=tol)
+    m_cp = torch.empty_like(m)
+    cp = B.mm_get_state(s1.ctx, m_cp)
+    assert cp["accepted"] >= 1 and cp["t"] > 0
+    B.mm_advance(s1.ctx, method, 20, dt_s=dt, tol=tol)
+    m_a = torch.empty_like(m)
+    B.mm_store(s1.ctx, m_a)
+    st_a = B.mm_get_stats(s1.ctx)
+    s2, _ = _pair()
+    B.mm_set_state(s2.ctx, m_cp, cp)
+    assert B.mm_get_state(s2.ctx) == cp
+    B.mm_advance(s2.ctx, method, 20, dt_s=dt, tol=tol)
+    m_b = torch.empty_like(m)
+    B.mm_store(s2.ctx, m_b)
+    st_b = B.mm_get_stats(s2.ctx)
+    torch.cuda.synchronize()
+    assert torch.equal(m_a, m_b)
+    for k in ("t", "dt", "accepted", "rejected", "step_index"):
+        assert st_a[k] == st_b[k], k
+    with pytest.raises(B.MMError):
+        B.mm_set_state(s2.ctx, m_cp, dict(cp, dt=-1.0))
