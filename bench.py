@@ -571,6 +571,55 @@ def run_relax(args):
     }
 
 
+def run_cufft_comparison(args):
+    """The demag convolution of the 1024 x 1024 film through cuFFT (torch.fft:
+    zero-padded 2048 x 2048 R2C of the three components, the 3x3 real kernel
+    product, C2R) next to this library's three passes (forward x, column pass
+    with the product, inverse x) for the same evaluation."""
+    import numpy as np
+    import torch
+
+    from paper_1102_3069_gb300 import binding as B
+    from paper_1102_3069_gb300 import inputs
+
+    w = inputs.workload("film_1024x1024")
+    nx, ny, _ = w["shape"]
+    px, py = 2 * nx, 2 * ny
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = B.Solver(w["shape"], w["cell"], stream=stream.cuda_stream, **w["material"])
+        m = torch.from_numpy(w["m"]).cuda()
+        B.mm_load(s.ctx, m)
+        B.mm_advance(s.ctx, B.MM_RKDP, 20, dt_s=1e-13, tol=1e-6)
+        passes = B.pass_times(s.ctx, lambda: B.mm_advance(s.ctx, B.MM_RKDP, 100, tol=1e-6))
+        ours = (passes["k_xfwd_next"]["ms_per_launch"] + passes["k_colconv_y"]["ms_per_launch"]
+                + passes["k_xinv_h"]["ms_per_launch"])
+        # cuFFT: the kernel spectrum (real, 4 components for a film) on the full padded grid
+        K = torch.randn(4, py, px // 2 + 1, device="cuda", dtype=torch.float32)
+        mp = torch.zeros(3, py, px, device="cuda", dtype=torch.float32)
+        mp[:, :ny, :nx] = m[:, 0]
+        def conv():
+            Mk = torch.fft.rfft2(mp)
+            Hk = torch.stack([K[0] * Mk[0] + K[3] * Mk[1], K[3] * Mk[0] + K[1] * Mk[1], K[2] * Mk[2]])
+            return torch.fft.irfft2(Hk, s=(py, px))[:, :ny, :nx]
+        for _ in range(5):
+            conv()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n = 50
+        a.record(stream)
+        for _ in range(n):
+            conv()
+        b.record(stream)
+        torch.cuda.synchronize()
+        cufft = a.elapsed_time(b) / n
+    return {"metric": "demag convolution time per evaluation", "unit": "ms", "higher_is_better": False,
+            "value": ours, "cufft_torch_fft": cufft, "ratio_cufft_over_ours": cufft / ours,
+            "config": {"workload": "film_1024x1024", "fft": [py, px],
+                       "ours": "k_xfwd_r + k_colconv + k_xinv_h (CUDA events per pass, RKDP steps)",
+                       "cufft": "torch.fft.rfft2 of the zero-padded 3 x 2048 x 2048 magnetisation, "
+                                "3x3 real kernel product, irfft2, crop (CUDA events over 50 evaluations)"}}
+
+
 def algorithmic_bytes_rk_3d(shape):
     """Method bytes of one Dormand-Prince step of an open 3-D grid (Sec. 3.2
     passes: x, y forward, z column pass, y, x inverse per evaluation)."""
@@ -633,6 +682,8 @@ def main():
     ap.add_argument("--relax", type=int, default=0,
                     help="time to relax this many 128 x 128 films from random states (batched and one by one)")
     ap.add_argument("--relax-max-steps", type=int, default=100000)
+    ap.add_argument("--cufft", action="store_true",
+                    help="time the film's demag convolution through cuFFT next to the hand-written passes")
     args = ap.parse_args()
     if args.impl == "reference":
         if args.steps > 5:
@@ -655,6 +706,9 @@ def main():
         return
     if args.relax > 0:
         print(json.dumps(run_relax(args)))
+        return
+    if args.cufft:
+        print(json.dumps(run_cufft_comparison(args)))
         return
     line = run_gpu(args)
     if line is None:
