@@ -172,3 +172,34 @@ def test_batch_autotuner_register_budgets_agree():
     for mode in (1, 2):
         for a, b in zip(outs[0], outs[mode]):
             assert float((a - b).abs().max()) <= 1e-6
+
+
+def test_batch_periodic_samples_match_oracle():
+    """Samples with periodic axes (image sums in the kernel, no padding along
+    them) in one batch with an open one: one fixed Dormand-Prince step each
+    against the FP64 oracle."""
+    import torch
+    mat = dict(Ms=9e5, Aex=1.5e-11, Ku=1e4, easy_axis=(0.2, 0.3, 1.0), alpha=0.1, B=(0.02, 0.0, 0.01))
+    samples = [dict(shape=(64, 64, 2), cell=(3e-9, 3e-9, 3e-9), pbc=(1, 1, 0), m_seed=31),
+               dict(shape=(64, 40, 1), cell=(4e-9, 4e-9, 2e-9), pbc=(1, 0, 0), m_seed=32),
+               dict(shape=(48, 36, 3), cell=(4e-9, 4e-9, 4e-9), pbc=(0, 0, 0), m_seed=33)]
+    images, h = 2, 1e-13
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sol = [B.Solver(s["shape"], s["cell"], pbc=s["pbc"], images=images, stream=stream.cuda_stream,
+                        tensor=False, **mat) for s in samples]
+        m0 = _m0(samples)
+        bt = B.Batch(sol, stream.cuda_stream)
+        B.mm_batch_load(bt.b, m0)
+        B.mm_batch_advance(bt.b, B.MM_RKDP, 1, dt_s=h, tol=-1.0)
+        out = [torch.empty_like(m) for m in m0]
+        B.mm_batch_store(bt.b, out)
+        torch.cuda.synchronize()
+    for i, s in enumerate(samples):
+        p = llg.Problem(s["shape"], s["cell"], mat["Ms"], mat["Aex"], mat["alpha"], Ku=mat["Ku"],
+                        u=mat["easy_axis"], B=mat["B"], pbc=tuple(bool(v) for v in s["pbc"]), images=images)
+        m = m0[i].cpu().numpy().astype(np.float64)
+        m /= np.sqrt((m * m).sum(axis=0, keepdims=True))
+        ref = llg.rkdp_stages(p, m, h)[0]
+        d = float(np.max(np.abs(out[i].cpu().numpy() - ref)))
+        assert d < 1e-6, (i, s["shape"], s["pbc"], d)
