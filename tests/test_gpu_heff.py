@@ -176,3 +176,12 @@ def test_per_cell_easy_axes_match_oracle(shape, pbc):
     h1, _, _ = s.heff(to_dev(m))
     p1 = oracle(shape, cell, pbc=pbc, images=2, **mat)
     assert rel_l2(to_np(h1), p1.heff(m64)) <= HEFF_REL_L2
+
+
+@pytest.mark.parametrize("shape,pbc", [((2048, 3, 1), (0, 0, 0)), ((3, 1500, 1), (0, 0, 0)), ((4096, 2, 1), (1, 0, 0)),
+                                       ((1025, 4, 2), (0, 0, 0))])
+def test_heff_largest_fft_lengths(shape, pbc):
+    """The largest padded lengths the library accepts: 4096 along x and along
+    y (open axes up to 2048 cells, periodic axes up to 4096), and just past a
+    power of two (1025 -> 4096)."""
+    _compare(shape, (4e-9, 3e-9, 2e-9), pbc=pbc, images=1)
