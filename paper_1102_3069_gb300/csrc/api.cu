@@ -220,6 +220,7 @@ mm::HotParams hot_params(mm_ctx* c, double dt_internal, bool thermal) {
     }
     p.h_scale = (float)Ms;
     p.t_scale = (float)(c->gamma0 * Ms);
+    p.t_unit = c->gamma0 * Ms;
     p.tw = reinterpret_cast<const float2*>(c->ws + c->off_tw);
     p.kt = reinterpret_cast<const float*>(c->ws + c->off_kt);
     p.s1 = reinterpret_cast<float2*>(c->ws + c->off_s1);
@@ -1048,7 +1049,8 @@ struct mm_batch {
     cudaStream_t stream = nullptr;
     char* ws = nullptr;
     size_t ws_size = 0;
-    size_t off_ps = 0, off_work = 0, off_states = 0, total = 0;
+    size_t off_ps = 0, off_work = 0, off_states = 0, off_active = 0, total = 0;
+    std::vector<mm::HotParams> hp_dev;        // what the device descriptors hold (uploaded on change)
     size_t max_work = 0;                      // int4 entries for all samples
     std::vector<mm::HotParams> hp;            // host copies of the device descriptors
     std::vector<int> active;                  // samples in the current work lists
@@ -1159,6 +1161,9 @@ int batch_build_groups(mm_batch* b) {
     if (!work.empty())
         BCK(cudaMemcpyAsync(b->ws + b->off_work, work.data(), work.size() * sizeof(int4), cudaMemcpyHostToDevice,
                             b->stream));
+    if (!b->active.empty())
+        BCK(cudaMemcpyAsync(b->ws + b->off_active, b->active.data(), b->active.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, b->stream));
     BCK(cudaStreamSynchronize(b->stream));    // the host vector goes out of scope
     b->groups = groups;
     int rc2 = batch_tune(b);
@@ -1216,23 +1221,29 @@ int batch_advance(mm_batch* b, int method, long nsteps, double dt_s, double tol,
     if (!(dt0 > 0) && !b->h_set) dt0 = 1e-13;        // default first step 100 fs
     for (int i : b->active) {
         mm_ctx* c = b->ctx[i];
-        const double tu = c->gamma0 * c->Ms;
         if (c->T > 0.0) return bfail(b, MM_EINVAL, "batches run without the thermal field (temperature 0)");
         mm::HotParams& p = b->hp[i];
-        p = hot_params(c, dt0 > 0 ? dt0 * tu : 0.0, true);
+        p = hot_params(c, 0.0, true);       // the step lives in each sample's device state
         p.rk = r.index;
         p.rk_stages = r.stages;
         p.rk_fsal = r.fsal;
-        k_set_run<<<1, 1, 0, b->stream>>>(dstate(c), fixed_steps ? 1.0 : tol, 0.0, torque_tol > 0 ? torque_tol : 0.0,
-                                          dt0 > 0 ? dt0 * tu : 0.0, 1e-20 * tu, 1, fixed_steps ? 1 : 0, 0.0, 0.0);
-        BCK(cudaGetLastError());
         c->spec = mm_ctx::SPEC_NONE;               // single-context calls start afresh after a batch
         c->k1_valid = false;
     }
     if (dt0 > 0) b->h_set = true;
-    BCK(cudaMemcpyAsync(b->ws + b->off_ps, b->hp.data(), b->hp.size() * sizeof(mm::HotParams),
-                        cudaMemcpyHostToDevice, b->stream));
-    BCK(cudaStreamSynchronize(b->stream));
+    // sample descriptors: copied only when they changed (a copy from pageable
+    // memory waits for the stream); then one launch sets every active
+    // sample's run parameters
+    if (b->hp_dev.size() != b->hp.size() ||
+        std::memcmp(b->hp_dev.data(), b->hp.data(), b->hp.size() * sizeof(mm::HotParams)) != 0) {
+        BCK(cudaMemcpyAsync(b->ws + b->off_ps, b->hp.data(), b->hp.size() * sizeof(mm::HotParams),
+                            cudaMemcpyHostToDevice, b->stream));
+        b->hp_dev = b->hp;
+    }
+    BCK(mm::launch_set_run_batch(reinterpret_cast<const mm::HotParams*>(b->ws + b->off_ps),
+                                 reinterpret_cast<const int*>(b->ws + b->off_active), (int)b->active.size(),
+                                 fixed_steps ? 1.0 : tol, torque_tol > 0 ? torque_tol : 0.0, dt0 > 0 ? dt0 : 0.0,
+                                 fixed_steps ? 1 : 0, b->stream));
     int rc;
     if (r.fsal) {
         if (dt_s > 0) b->spec_m2 = false;          // m_2 depends on h
@@ -1338,6 +1349,7 @@ int mm_batch_create(mm_batch** out, mm_ctx* const* ctxs, int n, void* cuda_strea
     b->off_ps = off; off += align256((size_t)n * sizeof(mm::HotParams));
     b->off_work = off; off += align256(b->max_work * sizeof(int4));
     b->off_states = off; off += align256((size_t)n * sizeof(mm::DevState));
+    b->off_active = off; off += align256((size_t)n * sizeof(int));
     b->total = off;
     b->active = all;
     *out = b;
@@ -1353,10 +1365,12 @@ int mm_batch_set_workspace(mm_batch* b, void* dev_ptr, size_t bytes) {
     b->ws = static_cast<char*>(dev_ptr);
     b->ws_size = bytes;
     b->groups_ready = false;
+    b->hp_dev.clear();
     if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
     BCK(cudaMemcpyAsync(b->ws + b->off_ps, b->hp.data(), b->hp.size() * sizeof(mm::HotParams),
                         cudaMemcpyHostToDevice, b->stream));
     BCK(cudaStreamSynchronize(b->stream));
+    b->hp_dev = b->hp;
     return MM_OK;
 }
 

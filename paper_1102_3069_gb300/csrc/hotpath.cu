@@ -1661,6 +1661,31 @@ __global__ void k_gather_states(const HotParams* __restrict__ ps, DevState* out,
     if (i < n) out[i] = *ps[i].st;
 }
 
+__global__ void k_set_run_batch(const HotParams* __restrict__ ps, const int* __restrict__ active, int n,
+                                double tol, double torque_tol, double dt0_s, int fixed_h) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const HotParams& p = ps[active[k]];
+    DevState* st = p.st;
+    st->tol = tol;
+    st->fixed_h = fixed_h;
+    st->t_end = 0.0;
+    st->torque_tol = torque_tol;
+    st->max_dm = 0.0;
+    st->h_cap = 0.0;
+    if (dt0_s > 0.0) st->h = dt0_s * p.t_unit;
+    st->h_min = 1e-20 * p.t_unit;
+    st->done = 0;
+    st->status = 0;
+}
+
+cudaError_t launch_set_run_batch(const HotParams* ps, const int* active, int n_active, double tol,
+                                 double torque_tol, double dt0_s, int fixed_h, cudaStream_t s) {
+    if (n_active <= 0) return cudaSuccess;
+    k_set_run_batch<<<(n_active + 127) / 128, 128, 0, s>>>(ps, active, n_active, tol, torque_tol, dt0_s, fixed_h);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gather_states(const HotParams* ps, DevState* out, int n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     k_gather_states<<<(n + 127) / 128, 128, 0, s>>>(ps, out, n);

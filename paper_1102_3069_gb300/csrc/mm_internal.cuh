@@ -99,6 +99,7 @@ struct HotParams {
     // output scales
     float h_scale;           // Ms (A/m)
     float t_scale;           // gamma0 Ms (1/s)
+    double t_unit;           // gamma0 Ms (1/s) in double: seconds -> internal time
     // buffers
     const float2* tw;
     const float* kt;
@@ -157,6 +158,10 @@ cudaError_t launch_pass_batched(const HotParams* ps, const int4* work, int nb, c
                                 int logp, int variant, cudaStream_t s);
 int batch_variants(int pass, int logp);     // 1 or 2 register budgets compiled for this pass
 cudaError_t launch_gather_states(const HotParams* ps, DevState* out, int n, cudaStream_t s);
+// run parameters of the active samples of a batch, one launch (as a per-context
+// mm_advance would set them; dt0_s > 0 sets the step, in seconds)
+cudaError_t launch_set_run_batch(const HotParams* ps, const int* active, int n_active, double tol,
+                                 double torque_tol, double dt0_s, int fixed_h, cudaStream_t s);
 
 // kernel setup (setup.cu)
 struct SetupParams {
