@@ -64,6 +64,11 @@ typedef struct mm_stats {
     double energy;          /* last energy computed by mm_eval_heff, J              */
     int status;             /* device-side status: 0 or a negative mm_status        */
     int done;               /* 1 when t_end / torque target reached or on failure   */
+    double dissipation;     /* W, from the last mm_eval_heff with energy: the rate   */
+                            /* -mu0 Ms V gamma0 alpha/(1+alpha^2) sum |m x H|^2 at   */
+                            /* which damping removes energy (Eq. 1); it is dE/dt     */
+                            /* without spin-transfer torque and thermal field; the   */
+                            /* sum is accumulated in FP64                            */
 } mm_stats;
 
 /*

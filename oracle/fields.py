@@ -164,3 +164,12 @@ def torque_max(m, H, Ms):
     """max_i |m_i x H_i| / Ms (dimensionless)."""
     c = np.cross(m, H, axis=0)
     return float(np.sqrt((c * c).sum(axis=0)).max() / Ms)
+
+
+def dissipation(m, H, Ms, V, alpha, gamma0=GAMMA0):
+    """Rate at which damping removes energy (W): with the LL right-hand side of
+    Eq. 1 and a field that is minus the energy gradient (no spin-transfer
+    torque, no thermal field), dE/dt = H.dm/dt summed = -mu0 Ms V gamma0 alpha
+    / (1 + alpha^2) sum_i |m_i x H_i|^2 <= 0."""
+    c = np.cross(m, H, axis=0)
+    return -MU0 * Ms * V * gamma0 * alpha / (1.0 + alpha * alpha) * float((c * c).sum())

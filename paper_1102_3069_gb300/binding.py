@@ -36,7 +36,7 @@ class mm_stats(ctypes.Structure):
     _fields_ = [("evals", ctypes.c_longlong), ("accepted", ctypes.c_longlong), ("rejected", ctypes.c_longlong),
                 ("step_index", ctypes.c_longlong), ("t", ctypes.c_double), ("dt", ctypes.c_double),
                 ("last_err", ctypes.c_double), ("max_torque", ctypes.c_double), ("energy", ctypes.c_double),
-                ("status", ctypes.c_int), ("done", ctypes.c_int)]
+                ("status", ctypes.c_int), ("done", ctypes.c_int), ("dissipation", ctypes.c_double)]
 
 
 class mm_checkpoint(ctypes.Structure):

@@ -640,6 +640,7 @@ int mm_eval_heff(mm_ctx* ctx, const float* m, float* h_out, float* torque_out, d
     p.thermal_step = (long long)ctx->th_step;
     mm::DevState* st = dstate(ctx);
     CK(cudaMemsetAsync(&st->energy_acc, 0, sizeof(double), ctx->stream));
+    CK(cudaMemsetAsync(&st->tsq_acc, 0, sizeof(double), ctx->stream));
     CK(cudaMemsetAsync(&st->status, 0, sizeof(int), ctx->stream));
     ctx->spec = mm_ctx::SPEC_NONE;          // the evaluation reuses the spectrum buffer
     rc = eval(ctx, p, mm::SRC_PTR, mm::LM_EVAL, 0);
@@ -818,6 +819,8 @@ int mm_get_stats(mm_ctx* ctx, mm_stats* stats) {
         stats->max_torque = h.max_torque;
         const double V = ctx->dx * ctx->dy * ctx->dz;
         stats->energy = MU0 * ctx->Ms * ctx->Ms * V * h.energy_acc;
+        stats->dissipation = -MU0 * ctx->Ms * ctx->Ms * ctx->Ms * V * ctx->gamma0 * ctx->alpha /
+                             (1.0 + ctx->alpha * ctx->alpha) * h.tsq_acc;
         stats->status = h.status;
         stats->done = h.done;
     }
@@ -1306,6 +1309,8 @@ void fill_stats(mm_ctx* c, const mm::DevState& h, int method, mm_stats* s) {
     s->max_torque = h.max_torque;
     const double V = c->dx * c->dy * c->dz;
     s->energy = MU0 * c->Ms * c->Ms * V * h.energy_acc;
+    s->dissipation = -MU0 * c->Ms * c->Ms * c->Ms * V * c->gamma0 * c->alpha / (1.0 + c->alpha * c->alpha) *
+                     h.tsq_acc;
     s->status = h.status;
     s->done = h.done;
 }

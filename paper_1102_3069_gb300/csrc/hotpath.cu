@@ -583,6 +583,7 @@ kb_yinv(const HotParams* __restrict__ ps, const int4* __restrict__ work, LaunchA
 struct Partials {
     float err, torque;
     double energy;
+    double tsq;           // sum |m x h|^2 (EVAL mode with energy): the damping dissipation
     unsigned bad;
 };
 
@@ -659,7 +660,9 @@ __device__ void finalize(const HotParams& p, const LaunchArgs& a) {
     }
 }
 
-// nblk: the blocks of this evaluation that report (the last of them runs finalize)
+// nblk: the blocks of this evaluation that report (the last of them runs finalize).
+// EV = false: a pass that never runs in evaluation mode (no energy sums).
+template <bool EV = true>
 __device__ void reduce_and_finish(const HotParams& p, const LaunchArgs& a, Partials pt, int nblk) {
     if (a.mode == LM_RK || a.mode == LM_HEUN1) {
         // intermediate stages reduce nothing but the non-finite flag, which the
@@ -668,7 +671,7 @@ __device__ void reduce_and_finish(const HotParams& p, const LaunchArgs& a, Parti
         return;
     }
     __shared__ float r_err[32], r_tq[32];
-    __shared__ double r_e[32];
+    __shared__ double r_e[32], r_t[32];
     __shared__ unsigned r_bad[32];
     __shared__ int s_last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -676,23 +679,32 @@ __device__ void reduce_and_finish(const HotParams& p, const LaunchArgs& a, Parti
     for (int o = 16; o > 0; o >>= 1) {
         pt.err = fmaxf(pt.err, __shfl_xor_sync(0xffffffffu, pt.err, o));
         pt.torque = fmaxf(pt.torque, __shfl_xor_sync(0xffffffffu, pt.torque, o));
-        pt.energy += __shfl_xor_sync(0xffffffffu, pt.energy, o);
+        if constexpr (EV) {
+            pt.energy += __shfl_xor_sync(0xffffffffu, pt.energy, o);
+            pt.tsq += __shfl_xor_sync(0xffffffffu, pt.tsq, o);
+        }
         pt.bad |= __shfl_xor_sync(0xffffffffu, pt.bad, o);
     }
-    if (lane == 0) { r_err[wid] = pt.err; r_tq[wid] = pt.torque; r_e[wid] = pt.energy; r_bad[wid] = pt.bad; }
+    if (lane == 0) { r_err[wid] = pt.err; r_tq[wid] = pt.torque; r_e[wid] = pt.energy; r_t[wid] = pt.tsq; r_bad[wid] = pt.bad; }
     __syncthreads();
     if (threadIdx.x == 0) {
         const int nw = (blockDim.x + 31) >> 5;
         for (int w = 1; w < nw; ++w) {
             pt.err = fmaxf(pt.err, r_err[w]);
             pt.torque = fmaxf(pt.torque, r_tq[w]);
-            pt.energy += r_e[w];
+            if constexpr (EV) {
+                pt.energy += r_e[w];
+                pt.tsq += r_t[w];
+            }
             pt.bad |= r_bad[w];
         }
         DevState* st = p.st;
         if (pt.err > 0.f) atomicMax(&st->err_bits, __float_as_uint(pt.err));
         if (pt.torque > 0.f) atomicMax(&st->torque_bits, __float_as_uint(pt.torque));
-        if (a.mode == LM_EVAL && p.want_energy) atomicAdd(&st->energy_acc, pt.energy);
+        if (EV && a.mode == LM_EVAL && p.want_energy) {
+            atomicAdd(&st->energy_acc, pt.energy);
+            atomicAdd(&st->tsq_acc, pt.tsq);
+        }
         if (pt.bad) atomicOr(&st->bad, 1u);
         __threadfence();
         const unsigned prev = atomicAdd(&st->blocks_done, 1u);
@@ -788,6 +800,7 @@ __device__ __forceinline__ void load_cell(const HotParams& p, const LaunchArgs& 
 // Everything that happens to one cell once its inputs and demag field are
 // known.  Returns the magnetisation the next evaluation of this step reads at
 // this cell (m_{s+1}, m_2, the predictor or m_{n+1}); zero when there is none.
+template <bool EV = true>
 __device__ __forceinline__ f3 update_cell(const HotParams& p, const LaunchArgs& a, int cur, const StageCoefs& sc,
                                           long long cell, const CellIn& in, f3 hd, long long tstep, Partials& pt) {
     const long long n = p.ncell;
@@ -834,6 +847,7 @@ __device__ __forceinline__ f3 update_cell(const HotParams& p, const LaunchArgs& 
 
     switch (a.mode) {
         case LM_EVAL: {
+            if constexpr (!EV) break;
             if (p.h_out) st3(p.h_out, cell, n, p.h_scale * h);
             if (p.tq_out) st3(p.tq_out, cell, n, p.t_scale * k);
             pt.torque = fmaxf(pt.torque, tq);
@@ -841,6 +855,7 @@ __device__ __forceinline__ f3 update_cell(const HotParams& p, const LaunchArgs& 
                 // quadratic terms as -m.H/2; the quartic cubic term by its density
                 const f3 hquad = hd + hex + (p.kan * dot(m, u)) * u;
                 pt.energy += -0.5 * (double)dot(m, hquad) - (double)dot(m, hz) + (double)ecub;
+                pt.tsq += (double)dot(mxh, mxh);
             }
             pt.bad |= !finite3(h);
             break;
@@ -1008,7 +1023,7 @@ __global__ void __launch_bounds__(XS<LOGP>::NT, XS<LOGP>::MINB) k_xinv_local(Hot
     fft_lines<LOGP, S::NL, true>(sm, p.tw);
     const int cur = s_cur;
     const float* min = src_ptr(p, a.src, cur);
-    Partials pt = {0.f, 0.f, 0.0, 0u};
+    Partials pt = {0.f, 0.f, 0.0, 0.0, 0u};
     const StageCoefs& sc = s_sc;
     const int NX = p.nx, NY = p.ny;
     // one item = one x and a pair of rows (2q, 2q+1): component c of that pair
@@ -1242,6 +1257,7 @@ kb_xinv_h(const HotParams* __restrict__ ps, const int4* __restrict__ work, Launc
 // Cell pass: local terms, torque and stage update for every cell, with the
 // magnetostatic field from hbuf when demag is on (the inverse x pass wrote
 // it) and without it otherwise.
+template <bool EV>
 __device__ __forceinline__ void local_body(const HotParams& p, const LaunchArgs& a, int bx, int nblk) {
     __shared__ StageCoefs s_sc;
     __shared__ long long s_tstep;
@@ -1277,12 +1293,16 @@ __device__ __forceinline__ void local_body(const HotParams& p, const LaunchArgs&
         if (p.demag) hd = ld3(p.hbuf, cell, n);
     }
     __syncthreads();
-    Partials pt = {0.f, 0.f, 0.0, 0u};
-    if (valid) update_cell(p, a, cur, s_sc, cell, in, hd, s_tstep, pt);
-    reduce_and_finish(p, a, pt, nblk);
+    Partials pt = {0.f, 0.f, 0.0, 0.0, 0u};
+    if (valid) update_cell<EV>(p, a, cur, s_sc, cell, in, hd, s_tstep, pt);
+    reduce_and_finish<EV>(p, a, pt, nblk);
 }
 __global__ void __launch_bounds__(256, 4) k_local(HotParams p, LaunchArgs a) {
-    local_body(p, a, blockIdx.x, gridDim.x);
+    local_body<true>(p, a, blockIdx.x, gridDim.x);
+}
+// the cell pass of time steps (never evaluation mode: no energy sums)
+__global__ void __launch_bounds__(256, 4) k_local_step(HotParams p, LaunchArgs a) {
+    local_body<false>(p, a, blockIdx.x, gridDim.x);
 }
 // batched: work[b] = (sample, block of that sample, -, blocks of that sample)
 __global__ void __launch_bounds__(256, 4)
@@ -1290,7 +1310,7 @@ kb_local(const HotParams* __restrict__ ps, const int4* __restrict__ work, Launch
     const int4 w = work[blockIdx.x];
     __shared__ HotParams s_hp;
     load_params(ps + w.x, &s_hp);
-    local_body(s_hp, a, w.y, w.w);
+    local_body<false>(s_hp, a, w.y, w.w);
 }
 
 // ---------------------------------------------------------------------------
@@ -1502,9 +1522,11 @@ cudaError_t launch_pass(const HotParams& p, const LaunchArgs& a, int pass, cudaS
         case PASS_COMBINE2:
             k_combine2<<<4 * 152, 256, 0, s>>>(p);
             break;
-        case PASS_LOCAL:
-        case PASS_LOCAL_H:          // one cell per thread: every load in flight at once
+        case PASS_LOCAL:            // one cell per thread: every load in flight at once
             k_local<<<(unsigned)((p.ncell + 255) / 256), 256, 0, s>>>(p, a);
+            break;
+        case PASS_LOCAL_H:          // time steps only
+            k_local_step<<<(unsigned)((p.ncell + 255) / 256), 256, 0, s>>>(p, a);
             break;
         default:
             return cudaErrorInvalidValue;

@@ -17,6 +17,7 @@ struct DevState {
     double last_err;      // last RKDP error estimate
     double max_torque;    // max |m x h| of the last accepted state
     double energy_acc;    // sum of energy densities (EVAL mode)
+    double tsq_acc;       // sum of |m x h|^2 (EVAL mode), internal units
     double max_dm;        // > 0: fixed maximum variation of m per step (h set by the k1 pass)
     double h_cap;         // upper bound on that h (<= 0: none)
     unsigned long long kre_bits;  // max |Re K^| seen by the kernel setup (double bits)

@@ -185,3 +185,20 @@ def test_heff_largest_fft_lengths(shape, pbc):
     y (open axes up to 2048 cells, periodic axes up to 4096), and just past a
     power of two (1025 -> 4096)."""
     _compare(shape, (4e-9, 3e-9, 2e-9), pbc=pbc, images=1)
+
+
+@pytest.mark.parametrize("shape", [(33, 7, 1), (16, 12, 3), (64, 16, 1)])
+def test_dissipation_matches_oracle(shape):
+    """The FP64 sum of |m x H|^2 behind mm_stats.dissipation (damping's energy
+    rate, Eq. 1) against the oracle."""
+    from paper_1102_3069_gb300 import binding as B
+    cell = (4e-9, 3e-9, 2e-9)
+    m = inputs.random_unit(shape, 14)
+    s = solver(shape, cell, **MAT)
+    s.heff(to_dev(m), energy=True)
+    st = B.mm_get_stats(s.ctx)
+    p = oracle(shape, cell, **MAT)
+    m64 = m.astype(np.float64)
+    D = F.dissipation(m64, p.heff(m64), p.Ms, p.V, p.alpha)
+    assert st["dissipation"] < 0
+    assert st["dissipation"] == pytest.approx(D, rel=2e-6)

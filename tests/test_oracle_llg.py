@@ -295,3 +295,22 @@ def test_max_dm_runs_follow_the_closed_form_with_the_method_order(name, order):
         errs.append(float(np.abs(m - _exact(alpha, B, th0, ph0, t)).max()))
     assert np.log2(errs[0] / errs[1]) == pytest.approx(order, abs=0.3)
     assert errs[1] < {1: 3e-2, 2: 3e-4, 4: 1e-7}[order]
+
+
+def test_dissipation_is_the_energy_rate_along_a_trajectory():
+    # dE/dt from a one-sided second-order difference of the energy along a
+    # Dormand-Prince trajectory equals -mu0 Ms V gamma' alpha sum |m x H|^2
+    p = llg.Problem((8, 6, 1), CELL, MS, 1.3e-11, 0.3, Ku=2e4, u=(0.2, 0.4, 1.0), B=(0.01, -0.02, 0.03))
+    g = np.random.default_rng(12)
+    m0 = llg.normalize(g.standard_normal(p.mshape))
+    h = 2e-15
+    m1 = llg.rkdp_fixed(p, m0, h, 1)
+    m2 = llg.rkdp_fixed(p, m1, h, 1)
+    E = [p.energy(x) for x in (m0, m1, m2)]
+    dEdt = (-3 * E[0] + 4 * E[1] - E[2]) / (2 * h)
+    D = F.dissipation(m0, p.heff(m0), p.Ms, p.V, p.alpha)
+    assert D < 0
+    assert dEdt == pytest.approx(D, rel=1e-4)
+    # no damping, no dissipation
+    p0 = llg.Problem((8, 6, 1), CELL, MS, 1.3e-11, 0.0, Ku=2e4, u=(0.2, 0.4, 1.0), B=(0.01, -0.02, 0.03))
+    assert F.dissipation(m0, p0.heff(m0), p0.Ms, p0.V, 0.0) == 0.0
