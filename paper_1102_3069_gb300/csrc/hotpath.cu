@@ -169,8 +169,10 @@ __device__ __forceinline__ void load_params(const HotParams* __restrict__ src, H
     __syncthreads();
 }
 
-// FFT lengths from which the x and y passes use the register radix-8 kernels
-constexpr int XREG_MIN_LOGP = 6;
+// FFT lengths for which the x and y passes use the register radix-8 kernels
+// (at 4096 points a line needs 512 threads, whose register budget spills:
+// the shared-memory radix-16 passes are faster there)
+constexpr int XREG_MIN_LOGP = 6, XREG_MAX_LOGP = 11;
 
 // ---------------------------------------------------------------------------
 // compile-time shapes of the passes (shared with the host through fft32.cuh)
@@ -454,7 +456,7 @@ struct YR {
 // launch shape of the y passes (either style), shared with the host
 template <int LOGP>
 struct YS {
-    static constexpr bool REG = LOGP >= XREG_MIN_LOGP;
+    static constexpr bool REG = LOGP >= XREG_MIN_LOGP && LOGP <= XREG_MAX_LOGP;
     static constexpr int TZ = tz_of(LOGP);
     static constexpr int NT = REG ? YR<LOGP>::NT : CS<LOGP, tz_of(LOGP)>::NT;
     static constexpr int MINB = REG ? YR<LOGP>::MINB : CS<LOGP, tz_of(LOGP)>::MINB;
@@ -1384,7 +1386,7 @@ static cudaError_t set_attr_all() {
     if ((e = cudaFuncSetAttribute(k_yinv<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_xinv_local<L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_xinv_local<L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
-    if constexpr (L >= XREG_MIN_LOGP) {
+    if constexpr (L >= XREG_MIN_LOGP && L <= XREG_MAX_LOGP) {
         if ((e = cudaFuncSetAttribute(k_xfwd_r<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
         if ((e = cudaFuncSetAttribute(k_xinv_h<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     }
@@ -1404,7 +1406,7 @@ cudaError_t configure_hot_kernels() { return set_attr_all<12>(); }
 
 template <int L>
 static void launch_x(const HotParams& p, const LaunchArgs& a, int pass, cudaStream_t s) {
-    if constexpr (L >= XREG_MIN_LOGP) {
+    if constexpr (L >= XREG_MIN_LOGP && L <= XREG_MAX_LOGP) {
         using R = XR<L>;
         const dim3 g((p.ny + R::TY - 1) / R::TY, p.nz);
         if (pass == PASS_XFWD) { k_xfwd_r<L><<<g, R::NT, R::SMEM, s>>>(p, a); return; }
@@ -1481,7 +1483,7 @@ int eval_passes(const HotParams& p, const LaunchArgs& a, int* ids) {
             ids[n++] = PASS_ZCONV;
             ids[n++] = PASS_YINV;
         }
-        if (p.logpx >= XREG_MIN_LOGP && a.mode != LM_EVAL && p.hbuf) {
+        if (p.logpx >= XREG_MIN_LOGP && p.logpx <= XREG_MAX_LOGP && a.mode != LM_EVAL && p.hbuf) {
             // a step: inverse x transform, cell pass, forward x transform of the next input
             ids[n++] = PASS_XINV_H;
             ids[n++] = PASS_LOCAL_H;

@@ -283,3 +283,19 @@ def test_checkpoint_resumes_bit_for_bit(method, dt, tol):
         assert st_a[k] == st_b[k], k
     with pytest.raises(B.MMError):
         B.mm_set_state(s2.ctx, m_cp, dict(cp, dt=-1.0))
+
+
+@pytest.mark.parametrize("method,dt", [(B.MM_RKDP, 1e-13), (B.MM_EULER, 1e-14)])
+def test_steps_at_the_largest_fft_length(method, dt):
+    """Time steps on a grid padded to 4096 points along x (the shared-memory
+    x passes) against the oracle."""
+    shape, cell = (2048, 3, 1), (4e-9, 4e-9, 4e-9)
+    mat = dict(Ms=8e5, Aex=1.3e-11, Ku=5e3, easy_axis=(1.0, 0.0, 0.0), alpha=0.1, B=(0.0, 0.01, 0.0))
+    s = solver(shape, cell, **mat)
+    p = oracle(shape, cell, **mat)
+    m = inputs.random_unit(shape, 5)
+    md = to_dev(m)
+    acc, t, _ = B.mm_step(s.ctx, md, method, 0.0, dt, tol=1.0)
+    m0 = _m64(m)
+    ref = llg.rkdp_stages(p, m0, dt)[0] if method == B.MM_RKDP else llg.euler_step(p, m0, dt)
+    assert acc and float(np.max(np.abs(to_np(md) - ref))) < 1e-6
