@@ -143,6 +143,20 @@ int mm_set_anisotropy_axes(mm_ctx* ctx, const float* u);
 int mm_set_max_dm(mm_ctx* ctx, double max_dm);
 
 /*
+ * Layout of the x passes in time steps (an implementation choice with no
+ * counterpart in the paper).  For padded x lengths 64 to 2048 an evaluation
+ * inside a step can either run the inverse x transform, the cell-local terms
+ * with the stage update, and the forward x transform of the next stage's input
+ * as one kernel (MM_LAYOUT_FUSED), or as three kernels with H_demag passing
+ * through device memory (MM_LAYOUT_SPLIT).  MM_LAYOUT_AUTO (default) takes the
+ * one measured faster on GB300, the fused kernel, for every method.  Results
+ * agree to float32 rounding.  Other lengths and mm_eval_heff always use the
+ * fused kernel; batches (mm_batch_*) always use the split passes.
+ */
+enum { MM_LAYOUT_AUTO = 0, MM_LAYOUT_FUSED = 1, MM_LAYOUT_SPLIT = 2 };
+int mm_set_pass_layout(mm_ctx* ctx, int layout);
+
+/*
  * Spin-transfer torque of Zhang and Li (Sec. 2.1.4, Eq. 7), a torque added to
  * dm/dt (not a field):
  *   dm/dt += -b_j/(1+alpha^2) [ m x (m x (j.grad)m) + (xi - alpha) m x (j.grad)m ],

@@ -58,6 +58,7 @@ _SIGS = {
     "mm_set_demag": (_i, [_vp, _i]),
     "mm_set_anisotropy_axes": (_i, [_vp, _vp]),
     "mm_set_max_dm": (_i, [_vp, _d]),
+    "mm_set_pass_layout": (_i, [_vp, _i]),
     "mm_set_cubic_anisotropy": (_i, [_vp, _d, _d, _dp, _dp]),
     "mm_set_stt": (_i, [_vp, _d, _d, _dp]),
     "mm_demag_kernel": (_i, [_vp, _dp]),
@@ -183,6 +184,13 @@ def mm_set_stt(ctx, P, xi, j=(0.0, 0.0, 0.0)):
 def mm_set_anisotropy_axes(ctx, u):
     """u: device float32 tensor (3, nz, ny, nx) of unit easy axes, or None."""
     return _check(ctx, lib().mm_set_anisotropy_axes(ctx, _ptr(u)))
+
+
+MM_LAYOUT_AUTO, MM_LAYOUT_FUSED, MM_LAYOUT_SPLIT = 0, 1, 2
+
+
+def mm_set_pass_layout(ctx, layout):
+    return _check(ctx, lib().mm_set_pass_layout(ctx, int(layout)))
 
 
 def mm_set_max_dm(ctx, max_dm):

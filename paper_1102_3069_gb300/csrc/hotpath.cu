@@ -1409,7 +1409,10 @@ static void launch_x(const HotParams& p, const LaunchArgs& a, int pass, cudaStre
     if constexpr (L >= XREG_MIN_LOGP && L <= XREG_MAX_LOGP) {
         using R = XR<L>;
         const dim3 g((p.ny + R::TY - 1) / R::TY, p.nz);
-        if (pass == PASS_XFWD) { k_xfwd_r<L><<<g, R::NT, R::SMEM, s>>>(p, a); return; }
+        // a time step in the fused layout transforms with the fused kernel's own
+        // radix-16 passes, so that a spectrum is the same bits whichever pass made it
+        const bool fused_step = a.mode != LM_EVAL && !p.hbuf;
+        if (pass == PASS_XFWD && !fused_step) { k_xfwd_r<L><<<g, R::NT, R::SMEM, s>>>(p, a); return; }
         if (pass == PASS_XFWD_NEXT) {
             LaunchArgs b = a;
             b.src = a.next_src;

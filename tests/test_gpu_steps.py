@@ -299,3 +299,29 @@ def test_steps_at_the_largest_fft_length(method, dt):
     m0 = _m64(m)
     ref = llg.rkdp_stages(p, m0, dt)[0] if method == B.MM_RKDP else llg.euler_step(p, m0, dt)
     assert acc and float(np.max(np.abs(to_np(md) - ref))) < 1e-6
+
+
+@pytest.mark.parametrize("method,dt,tol", [(B.MM_RKDP, 1e-13, -1.0), (B.MM_EULER, 1e-14, 0.0), (B.MM_HEUN, 2e-14, 0.0)])
+@pytest.mark.parametrize("shape", [(40, 12, 1), (20, 70, 3)])
+def test_pass_layouts_agree(method, dt, tol, shape):
+    """The fused and the split x-pass layouts of a time step give the same
+    trajectory up to float32 rounding (a few fixed steps from a non-chaotic
+    start; with an adaptive step, rounding-level differences in the error
+    estimate move the step size and with it the trajectory)."""
+    import torch
+    cell = (4e-9, 4e-9, 3e-9)
+    mat = dict(Ms=8e5, Aex=1.3e-11, Ku=2e4, easy_axis=(0.3, 0.0, 1.0), alpha=0.2, B=(0.0, 0.01, 0.02))
+    outs = []
+    for layout in (B.MM_LAYOUT_FUSED, B.MM_LAYOUT_SPLIT):
+        s = solver(shape, cell, **mat)
+        B.mm_set_pass_layout(s.ctx, layout)
+        md = to_dev(inputs.smooth_tilt(shape))
+        B.mm_load(s.ctx, md)
+        B.mm_advance(s.ctx, method, 8, dt_s=dt, tol=tol)
+        B.mm_store(s.ctx, md)
+        outs.append((md, B.mm_get_stats(s.ctx)))
+    torch.cuda.synchronize()
+    assert float((outs[0][0] - outs[1][0]).abs().max()) < 1e-6
+    assert outs[0][1]["accepted"] == outs[1][1]["accepted"]
+    with pytest.raises(B.MMError):
+        B.mm_set_pass_layout(s.ctx, 7)
