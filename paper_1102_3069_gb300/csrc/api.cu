@@ -1145,12 +1145,23 @@ int batch_work(mm_batch* b, const std::vector<int>& which, std::vector<int4>* ou
 std::mutex g_tune_mutex;
 std::map<std::tuple<int, int, int>, int> g_tune_cache;
 
+// destroys the timing events on every return path
+struct EventPair {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ~EventPair() {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    }
+};
+
 int batch_tune(mm_batch* b) {
     if (b->tune_mode == 0 || b->active.empty()) return MM_OK;
     const mm::LaunchArgs a = make_args(b->hp[b->active[0]], mm::SRC_CUR, mm::LM_EVAL, 0, false, false);
     const mm::HotParams* ps = reinterpret_cast<const mm::HotParams*>(b->ws + b->off_ps);
     const int4* work = reinterpret_cast<const int4*>(b->ws + b->off_work);
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    EventPair ev;
+    cudaEvent_t& e0 = ev.e0;
+    cudaEvent_t& e1 = ev.e1;
     for (auto& g : b->groups) {
         if (mm::batch_variants(g.pass, g.logp) < 2) continue;
         if (b->tune_mode == 2) { g.variant = 1; continue; }
@@ -1177,7 +1188,6 @@ int batch_tune(mm_batch* b) {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         g_tune_cache[key] = pick;
     }
-    if (e0) { cudaEventDestroy(e0); cudaEventDestroy(e1); }
     return MM_OK;
 }
 
@@ -1361,7 +1371,6 @@ int mm_batch_create(mm_batch** out, mm_ctx* const* ctxs, int n, void* cuda_strea
             delete b;
             return MM_EINVAL;
         }
-        c->stream = b->stream;                     // every sample's work goes on the batch stream
         b->hp[i] = hot_params(c, 0.0, false);
         b->hp[i].rk_stages = 7;
         if (!mm::batch_supported(b->hp[i])) {
@@ -1377,6 +1386,7 @@ int mm_batch_create(mm_batch** out, mm_ctx* const* ctxs, int n, void* cuda_strea
         return MM_EINVAL;
     }
     b->max_work = work.size();
+    for (int i = 0; i < n; ++i) ctxs[i]->stream = b->stream;    // every sample's work goes on the batch stream
     size_t off = 0;
     b->off_ps = off; off += align256((size_t)n * sizeof(mm::HotParams));
     b->off_work = off; off += align256(b->max_work * sizeof(int4));
