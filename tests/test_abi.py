@@ -89,3 +89,43 @@ def test_larger_grids_need_larger_workspaces():
     finally:
         for x in (a, b, c):
             B.mm_destroy(x)
+
+
+def test_option_calls_check_their_arguments_on_host():
+    """The option and checkpoint calls reject bad arguments before any device
+    work (no GPU needed)."""
+    _ensure_built()
+    ctx = B.mm_init_geometry(64, 16, 1, 4e-9, 4e-9, 4e-9)
+    try:
+        for bad in (-1, 3, 7):
+            with pytest.raises(B.MMError) as e:
+                B.mm_set_pass_layout(ctx, bad)
+            assert e.value.code == B.MM_EINVAL
+        for layout in (B.MM_LAYOUT_AUTO, B.MM_LAYOUT_FUSED, B.MM_LAYOUT_SPLIT):
+            B.mm_set_pass_layout(ctx, layout)
+        for bad in (-0.1, 1.5, float("nan")):
+            with pytest.raises(B.MMError) as e:
+                B.mm_set_max_dm(ctx, bad)
+            assert e.value.code == B.MM_EINVAL
+        B.mm_set_max_dm(ctx, 0.02)
+        B.mm_set_max_dm(ctx, 0.0)
+        with pytest.raises(B.MMError) as e:            # not float aligned
+            B.mm_set_anisotropy_axes(ctx, 0x1002)
+        assert e.value.code == B.MM_EINVAL
+        B.mm_set_anisotropy_axes(ctx, None)
+        with pytest.raises(B.MMError) as e:            # nothing loaded to checkpoint
+            B.mm_get_state(ctx)
+        assert e.value.code == B.MM_ESTATE
+        with pytest.raises(B.MMError) as e:            # no workspace to restore into
+            B.mm_set_state(ctx, 0x1000, dict(t=0.0, dt=1e-13, step_index=0, accepted=0, rejected=0, evals=0,
+                                             after_reject=0))
+        assert e.value.code == B.MM_ENOMEM
+        with pytest.raises(B.MMError) as e:            # a context without workspace cannot join a batch
+            B.mm_batch_create([ctx])
+        assert e.value.code == B.MM_EINVAL
+    finally:
+        B.mm_destroy(ctx)
+    b = ctypes.c_void_p()
+    assert B.lib().mm_batch_create(ctypes.byref(b), None, 0, None) == B.MM_EINVAL
+    assert B.mm_batch_workspace_bytes(None) == 0
+    B.lib().mm_batch_destroy(None)
