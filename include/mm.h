@@ -224,16 +224,18 @@ int mm_store(mm_ctx* ctx, float* m);
 /*
  * Enqueue nsteps time steps on the stream without waiting (device-side step
  * control, Sec. 2.2).  Fixed-step methods (MM_EULER, MM_HEUN, MM_RK3, MM_RK4)
- * take dt_s > 0.  Adaptive methods (MM_RK12, MM_RK23, MM_RKCK, MM_RKDP) take
+ * take dt_s > 0 (or, after mm_set_max_dm, choose each step themselves with
+ * dt_s as an optional cap).  Adaptive methods (MM_RK12, MM_RK23, MM_RKCK, MM_RKDP) take
  * the per-step error bound tol (max over cells of |dm|) and the proposed step
  * dt_s (> 0 sets it; <= 0 keeps the current one, 100 fs after mm_load); the
  * step factor is 0.9 (tol/err)^(1/q), q = 2, 3, 5, 5 respectively, clamped to
  * [0.2, 5].  tol < 0 selects fixed steps of dt_s for an adaptive method (the
  * error estimate is still computed and reported).  The thermal field (T > 0)
- * needs a fixed-step method.  t_end_s > 0 stops the
+ * needs a fixed-step method with a fixed dt (MM_EULER, MM_HEUN, MM_RK3 or
+ * MM_RK4; one noise draw per step shared by its stages).  t_end_s > 0 stops the
  * run exactly at t_end_s (the last step is shortened); torque_tol > 0 stops
  * it once max |m x H|/Ms < torque_tol (relaxation).  Once stopped, queued
- * steps do no work.  The thermal field (T > 0) needs MM_EULER or MM_HEUN.
+ * steps do no work.
  */
 int mm_advance(mm_ctx* ctx, int method, long nsteps, double dt_s, double tol,
                double t_end_s, double torque_tol);
@@ -269,7 +271,7 @@ int mm_set_state(mm_ctx* ctx, const float* m, const mm_checkpoint* in);
 /*
  * One step (Sec. 2.2) from m (device, in/out): loads m at time *t_s, takes
  * one step of `method` with the proposed/fixed step *dt_s (and error bound
- * tol for MM_RKDP), stores the result back into m and synchronises.
+ * tol for the adaptive methods), stores the result back into m and synchronises.
  * On return *accepted = 1/0, *t_s is the new time and *dt_s the next step.
  */
 int mm_step(mm_ctx* ctx, float* m, int method, double* t_s, double* dt_s, double tol, int* accepted);
