@@ -4,6 +4,7 @@
 #include "mm_internal.cuh"
 #include "fft32.cuh"
 
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -286,17 +287,23 @@ int eval(mm_ctx* ctx, const mm::HotParams& p, int src, int mode, int stage, bool
     int ids[8];
     const int n = mm::eval_passes(p, a, ids);
     for (int i = 0; i < n; ++i) {
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (ctx->profiling) {
-            CK(cudaEventCreate(&e0));
-            CK(cudaEventCreate(&e1));
-            CK(cudaEventRecord(e0, ctx->stream));
+        if (!ctx->profiling) {
+            CK(mm::launch_pass(p, a, ids[i], ctx->stream));
+            continue;
         }
+        // the context owns the pair as soon as both exist: mm_pass_times and
+        // mm_destroy release them on every path
+        mm_ctx::Rec r{ids[i], nullptr, nullptr};
+        cudaError_t e = cudaEventCreate(&r.a);
+        if (e == cudaSuccess) e = cudaEventCreate(&r.b);
+        if (e != cudaSuccess) {
+            if (r.a) cudaEventDestroy(r.a);
+            return cuda_fail(ctx, e, "cudaEventCreate");
+        }
+        ctx->prof.push_back(r);
+        CK(cudaEventRecord(r.a, ctx->stream));
         CK(mm::launch_pass(p, a, ids[i], ctx->stream));
-        if (ctx->profiling) {
-            CK(cudaEventRecord(e1, ctx->stream));
-            ctx->prof.push_back({ids[i], e0, e1});
-        }
+        CK(cudaEventRecord(r.b, ctx->stream));
     }
     return MM_OK;
 }
@@ -458,12 +465,13 @@ int mm_set_workspace(mm_ctx* ctx, void* dev_ptr, size_t bytes) {
     if (bytes < ctx->total) return fail(ctx, MM_ENOMEM, "workspace smaller than mm_workspace_bytes()");
     // opt every hot kernel into large dynamic shared memory (once per process and device)
     {
-        static int configured_mask = 0;
+        static std::atomic<unsigned long long> configured_mask{0};
         int dev = 0;
         CK(cudaGetDevice(&dev));
-        if (dev < 31 && !(configured_mask & (1 << dev))) {
+        const unsigned long long bit = (dev >= 0 && dev < 64) ? 1ull << dev : 0ull;   // 0: configure every time
+        if (!(configured_mask.load() & bit)) {
             CK(mm::configure_hot_kernels());
-            configured_mask |= 1 << dev;
+            configured_mask.fetch_or(bit);
         }
     }
     ctx->ws = static_cast<char*>(dev_ptr);
@@ -987,16 +995,22 @@ int mm_profile(mm_ctx* ctx, int enable) {
 
 int mm_pass_times(mm_ctx* ctx, double* ms_out, long long* count_out) {
     if (!ctx) return MM_EINVAL;
-    CK(cudaStreamSynchronize(ctx->stream));
+    // every recorded pair is released, also when a query fails (the first error is returned)
+    cudaError_t first = cudaStreamSynchronize(ctx->stream);
     for (auto& r : ctx->prof) {
         float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, r.a, r.b));
-        ctx->pass_ms[r.pass] += ms;
-        ctx->pass_n[r.pass] += 1;
+        const cudaError_t e = first == cudaSuccess ? cudaEventElapsedTime(&ms, r.a, r.b) : first;
+        if (e == cudaSuccess) {
+            ctx->pass_ms[r.pass] += ms;
+            ctx->pass_n[r.pass] += 1;
+        } else if (first == cudaSuccess) {
+            first = e;
+        }
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
     }
     ctx->prof.clear();
+    if (first != cudaSuccess) return cuda_fail(ctx, first, "mm_pass_times");
     for (int i = 0; i < mm::NPASS; ++i) {
         if (ms_out) ms_out[i] = ctx->pass_ms[i];
         if (count_out) count_out[i] = ctx->pass_n[i];
@@ -1252,6 +1266,8 @@ int batch_advance(mm_batch* b, int method, long nsteps, double dt_s, double tol,
     const bool fixed_steps = !r.adaptive || tol < 0.0;
     if (r.adaptive && !fixed_steps && tol == 0.0) return bfail(b, MM_EINVAL, "adaptive methods need tol > 0");
     if (fixed_steps && !(dt_s > 0) && !b->h_set) return bfail(b, MM_EINVAL, "fixed steps need dt > 0");
+    for (int i : b->active)        // checked before any sample's descriptor changes
+        if (b->ctx[i]->T > 0.0) return bfail(b, MM_EINVAL, "batches run without the thermal field (temperature 0)");
     if (method != b->graph_method && b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
     if (!b->groups_ready) {
         int rc = batch_build_groups(b);
@@ -1261,7 +1277,6 @@ int batch_advance(mm_batch* b, int method, long nsteps, double dt_s, double tol,
     if (!(dt0 > 0) && !b->h_set) dt0 = 1e-13;        // default first step 100 fs
     for (int i : b->active) {
         mm_ctx* c = b->ctx[i];
-        if (c->T > 0.0) return bfail(b, MM_EINVAL, "batches run without the thermal field (temperature 0)");
         mm::HotParams& p = b->hp[i];
         p = hot_params(c, 0.0, true);       // the step lives in each sample's device state
         p.rk = r.index;

@@ -325,3 +325,23 @@ def test_pass_layouts_agree(method, dt, tol, shape):
     assert outs[0][1]["accepted"] == outs[1][1]["accepted"]
     with pytest.raises(B.MMError):
         B.mm_set_pass_layout(s.ctx, 7)
+
+
+def test_pass_times_account_for_every_evaluation():
+    """Per-pass event timing (mm_profile, mm_pass_times) of steps run without
+    the step graph: every evaluation makes exactly one launch that ends in the
+    cell terms, so those launches count the evaluations the device state
+    reports; reading the times releases them, and a second read with nothing
+    new run returns the same totals."""
+    s, _ = _pair()
+    md = to_dev(W["m"])
+    B.mm_load(s.ctx, md)
+    B.mm_profile(s.ctx, True)
+    B.mm_advance(s.ctx, B.MM_RKDP, 3, dt_s=1e-13, tol=-1.0)
+    t1 = B.mm_pass_times(s.ctx)
+    st = B.mm_get_stats(s.ctx)
+    cell_passes = ("k_xinv_local", "k_xinv_local_fused", "k_local", "k_local_h")
+    assert sum(v["launches"] for k, v in t1.items() if k in cell_passes) == st["evals"] == 19
+    assert all(v["ms_total"] >= 0.0 for v in t1.values()) and sum(v["ms_total"] for v in t1.values()) > 0.0
+    assert B.mm_pass_times(s.ctx) == t1
+    B.mm_profile(s.ctx, False)
