@@ -38,7 +38,7 @@ def test_single_step_matches_tableau(name):
     tab = llg.TABLEAUS[name]
     h = 5e-14
     acc, t, _ = B.mm_step(s.ctx, md, METHODS[name], 0.0, h, tol=1.0)
-    assert acc and t == pytest.approx(h, rel=1e-12)
+    assert acc and t == pytest.approx(h, rel=1e-12, abs=0.0)
     ref = llg.rk_attempt(p, _m64(m), h, tab)[0]
     assert np.max(np.abs(to_np(md) - ref)) <= 1e-6
 
@@ -71,7 +71,7 @@ def test_adaptive_run_matches_oracle(name):
     B.mm_store(s.ctx, md)
     st = B.mm_get_stats(s.ctx)
     assert st["done"] == 1 and st["status"] == 0
-    assert st["t"] == pytest.approx(2e-10, rel=1e-12)
+    assert st["t"] == pytest.approx(2e-10, rel=1e-12, abs=0.0)
     ref = llg.TableauStepper(p, _m64(m), llg.TABLEAUS[name], h0=1e-13, tol=tol)
     ref.run_until(2e-10)
     mg = to_np(md)

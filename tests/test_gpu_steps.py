@@ -36,7 +36,7 @@ def test_single_step(method, dt):
     md = to_dev(m)
     acc, t, dt_next = B.mm_step(s.ctx, md, method, 0.0, dt, tol=1.0)
     assert acc
-    assert t == pytest.approx(dt, rel=1e-12)
+    assert t == pytest.approx(dt, rel=1e-12, abs=0.0)
     m0 = _m64(m)
     if method == B.MM_EULER:
         ref = llg.euler_step(p, m0, dt)
@@ -69,7 +69,7 @@ def _fixed_run(m, nsteps, h=1e-13):
     B.mm_store(s.ctx, md)
     st = B.mm_get_stats(s.ctx)
     assert st["accepted"] == nsteps and st["rejected"] == 0
-    assert st["t"] == pytest.approx(nsteps * h, rel=1e-12)
+    assert st["t"] == pytest.approx(nsteps * h, rel=1e-12, abs=0.0)
     ref = llg.rkdp_fixed(p, _m64(m), h, nsteps)
     return float(np.max(np.abs(to_np(md) - ref))), float(np.max(np.abs(ref - _m64(m))))
 
@@ -102,7 +102,7 @@ def test_adaptive_run_to_1ns_smooth_state():
     B.mm_store(s.ctx, md)
     st = B.mm_get_stats(s.ctx)
     assert st["done"] == 1 and st["status"] == 0
-    assert st["t"] == pytest.approx(1e-9, rel=1e-12)
+    assert st["t"] == pytest.approx(1e-9, rel=1e-12, abs=0.0)
     ref = llg.Stepper(p, _m64(m), h0=1e-13, tol=1e-6)
     ref.run_until(1e-9)
     mg = to_np(md)
@@ -126,7 +126,7 @@ def test_adaptive_run_to_1ns_random_state():
     B.mm_store(s.ctx, md)
     st = B.mm_get_stats(s.ctx)
     assert st["done"] == 1 and st["status"] == 0
-    assert st["t"] == pytest.approx(1e-9, rel=1e-12)
+    assert st["t"] == pytest.approx(1e-9, rel=1e-12, abs=0.0)
     ref = llg.Stepper(p, _m64(m), h0=1e-13, tol=1e-6)
     ref.run_until(1e-9)
     mg = to_np(md)
@@ -237,15 +237,15 @@ def test_max_dm_steps_match_oracle(method, name, shape):
     ref, t, hs = llg.max_dm_run(p, _m64(m), llg.MAXDM_TABLEAUS[name], dm, n)
     assert st["status"] == 0 and st["accepted"] == n
     assert st["evals"] == n * {"euler": 1, "heun": 2, "rk3": 3, "rk4": 4}[name]
-    assert st["t"] == pytest.approx(t, rel=1e-5)
-    assert st["dt"] == pytest.approx(hs[-1], rel=1e-4)          # the last step's size
+    assert st["t"] == pytest.approx(t, rel=1e-4, abs=0.0)
+    assert st["dt"] == pytest.approx(hs[-1], rel=1e-4, abs=0.0)          # the last step's size
     assert float(np.max(np.abs(to_np(md) - ref))) < 1e-5
     # a cap below the natural step size binds every step
     cap = 0.5 * min(hs)
     B.mm_load(s.ctx, to_dev(m))
     B.mm_advance(s.ctx, method, 4, dt_s=cap)
     st = B.mm_get_stats(s.ctx)
-    assert st["t"] == pytest.approx(4 * cap, rel=1e-12)
+    assert st["t"] == pytest.approx(4 * cap, rel=1e-12, abs=0.0)
     # back to fixed steps: dt is required again
     B.mm_set_max_dm(s.ctx, 0.0)
     with pytest.raises(B.MMError):

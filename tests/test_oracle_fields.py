@@ -71,7 +71,7 @@ def test_exchange_energy_equals_bond_sum():
     for axis, d in ((3, cell[0]), (2, cell[1]), (1, cell[2])):
         diff = np.diff(m, axis=axis)
         bonds += (diff ** 2).sum() / d ** 2
-    assert E == pytest.approx(AEX * V * bonds, rel=1e-12)
+    assert E == pytest.approx(AEX * V * bonds, rel=1e-12, abs=0.0)
 
 
 def test_anisotropy_closed_form():
@@ -107,7 +107,7 @@ def test_per_cell_anisotropy_axes_closed_form():
     np.testing.assert_allclose(H, (2 * Ku / (F.MU0 * MS)) * np.cos(th) * u, rtol=1e-12, atol=1e-9)
     z = np.zeros((3, 1, 1, n))
     E = F.energy(m.reshape(3, 1, 1, n), MS, V, z, z, H.reshape(3, 1, 1, n), z)
-    assert E == pytest.approx(-Ku * V * np.sum(np.cos(th) ** 2), rel=1e-12)
+    assert E == pytest.approx(-Ku * V * np.sum(np.cos(th) ** 2), rel=1e-12, abs=0.0)
     # a uniform axis field of per-cell copies is the uniform-axis result
     Hu = F.anisotropy_field(m.reshape(3, 1, 1, n), MS, Ku, u[:, 0])
     Hc = F.anisotropy_field(m.reshape(3, 1, 1, n), MS, Ku, np.repeat(u[:, :1], n, axis=1).reshape(3, 1, 1, n))
@@ -123,7 +123,7 @@ def test_zeeman_energy():
     Hz = F.zeeman_field(m, B)
     z = np.zeros_like(m)
     E = F.energy(m, MS, V, z, z, z, Hz)
-    assert E == pytest.approx(-MS * V * ((0.6 * 0.01 - 0.8 * 0.02) + (-0.03)), rel=1e-12)
+    assert E == pytest.approx(-MS * V * ((0.6 * 0.01 - 0.8 * 0.02) + (-0.03)), rel=1e-12, abs=0.0)
 
 
 def test_uniform_body_demag_energy():
@@ -136,7 +136,7 @@ def test_uniform_body_demag_energy():
     z = np.zeros_like(m)
     E = F.energy(m, MS, V, Hd, z, z, z)
     Nxx = float(newell.newell_tensor(0, 0, 0, nx * cell[0], ny * cell[1], nz * cell[2])["xx"])
-    assert E == pytest.approx(0.5 * F.MU0 * MS ** 2 * V * nx * ny * nz * Nxx, rel=1e-10)
+    assert E == pytest.approx(0.5 * F.MU0 * MS ** 2 * V * nx * ny * nz * Nxx, rel=1e-10, abs=0.0)
 
 
 KAT = [
@@ -178,7 +178,7 @@ def test_uniform_open_interval_exact_in_binary32():
 def test_thermal_sigma_units():
     # sigma^2 * gamma0 mu0 Ms V dt = 2 alpha kB T  (Eq. 6)
     s = F.thermal_sigma(0.05, 300.0, 1.1e6, 27e-27, 50e-15)
-    assert s * s * F.GAMMA0 * F.MU0 * 1.1e6 * 27e-27 * 50e-15 == pytest.approx(2 * 0.05 * F.KB * 300.0, rel=1e-12)
+    assert s * s * F.GAMMA0 * F.MU0 * 1.1e6 * 27e-27 * 50e-15 == pytest.approx(2 * 0.05 * F.KB * 300.0, rel=1e-12, abs=0.0)
 
 
 def test_cubic_anisotropy_is_minus_energy_gradient():
@@ -202,8 +202,8 @@ def test_cubic_anisotropy_special_directions():
     m_111 = (np.ones(3) / np.sqrt(3)).reshape(3, 1, 1, 1)
     m_110 = (np.array([1.0, 1.0, 0.0]) / np.sqrt(2)).reshape(3, 1, 1, 1)
     assert F.cubic_energy_density(m_axis, K1, K2, c1, c2).item() == pytest.approx(0.0, abs=1e-9)
-    assert F.cubic_energy_density(m_111, K1, K2, c1, c2).item() == pytest.approx(K1 / 3 + K2 / 27, rel=1e-12)
-    assert F.cubic_energy_density(m_110, K1, K2, c1, c2).item() == pytest.approx(K1 / 4, rel=1e-12)
+    assert F.cubic_energy_density(m_111, K1, K2, c1, c2).item() == pytest.approx(K1 / 3 + K2 / 27, rel=1e-12, abs=0.0)
+    assert F.cubic_energy_density(m_110, K1, K2, c1, c2).item() == pytest.approx(K1 / 4, rel=1e-12, abs=0.0)
     # along a cube axis, [110] and [111] the field is parallel to m (no torque)
     for mm in (m_axis, m_111, m_110):
         H = F.cubic_anisotropy_field(mm, MS, K1, K2, c1, c2)
@@ -262,7 +262,7 @@ def test_stt_on_a_spiral_has_the_closed_form():
     bj = F.stt_bj(P, xi, MS)
     expect = -bj / (1 + alpha ** 2) * (-u + (xi - alpha) * zhat)
     np.testing.assert_allclose(tq[:, 0, 0, :], expect, rtol=1e-12, atol=1e-12 * np.abs(expect).max())
-    assert bj == pytest.approx(P * F.MU_B / (F.E_CHARGE * MS * (1 + xi * xi)), rel=1e-15)
+    assert bj == pytest.approx(P * F.MU_B / (F.E_CHARGE * MS * (1 + xi * xi)), rel=1e-15, abs=0.0)
 
 
 def test_adiabatic_stt_advects_a_spiral():

@@ -117,7 +117,7 @@ def test_adaptive_run_hits_closed_form():
     p = _macrospin(alpha, B)
     st = llg.Stepper(p, _m0(th0, ph0), h0=1e-13, tol=1e-9)
     st.run_until(2e-10)
-    assert st.t == pytest.approx(2e-10, rel=1e-12)
+    assert st.t == pytest.approx(2e-10, rel=1e-12, abs=0.0)
     np.testing.assert_allclose(st.m, _exact(alpha, B, th0, ph0, st.t), atol=100 * 1e-9)
     assert st.accepted > 10
 
@@ -235,7 +235,7 @@ def test_generic_dormand_prince_equals_the_dedicated_one():
     a = llg.rk_attempt(p, m, 3e-14, llg.TABLEAUS["rkdp"])
     b = llg.rkdp_stages(p, m, 3e-14)
     assert np.max(np.abs(a[0] - b[0])) < 1e-15
-    assert a[2] == pytest.approx(b[2], rel=1e-12)
+    assert a[2] == pytest.approx(b[2], rel=1e-12, abs=0.0)
 
 
 @pytest.mark.parametrize("name", ["rk12", "rk23", "rkck"])
@@ -244,7 +244,7 @@ def test_adaptive_tableaus_hit_the_closed_form(name):
     p = _macrospin(alpha, B)
     st = llg.TableauStepper(p, _m0(th0, 0.0), llg.TABLEAUS[name], h0=1e-13, tol=1e-8)
     st.run_until(1e-10)
-    assert st.t == pytest.approx(1e-10, rel=1e-12)
+    assert st.t == pytest.approx(1e-10, rel=1e-12, abs=0.0)
     np.testing.assert_allclose(st.m, _exact(alpha, B, th0, 0.0, st.t), atol=2e-5)
 
 
@@ -260,7 +260,7 @@ def test_max_dm_step_size_is_the_first_order_variation():
     dm = 0.02
     m1, h = llg.max_dm_step(p, m, llg.MAXDM_TABLEAUS["euler"], dm)
     move = np.sqrt(((h * k1) ** 2).sum(axis=0))
-    assert move.max() == pytest.approx(dm, rel=1e-14)
+    assert move.max() == pytest.approx(dm, rel=1e-14, abs=0.0)
     np.testing.assert_allclose(m1, llg.normalize(m + h * k1), rtol=0, atol=1e-15)
     # the cap wins when it is smaller
     _, hc = llg.max_dm_step(p, m, llg.MAXDM_TABLEAUS["euler"], dm, h_cap=0.5 * h)
@@ -310,7 +310,7 @@ def test_dissipation_is_the_energy_rate_along_a_trajectory():
     dEdt = (-3 * E[0] + 4 * E[1] - E[2]) / (2 * h)
     D = F.dissipation(m0, p.heff(m0), p.Ms, p.V, p.alpha)
     assert D < 0
-    assert dEdt == pytest.approx(D, rel=1e-4)
+    assert dEdt == pytest.approx(D, rel=1e-4, abs=0.0)
     # no damping, no dissipation
     p0 = llg.Problem((8, 6, 1), CELL, MS, 1.3e-11, 0.0, Ku=2e4, u=(0.2, 0.4, 1.0), B=(0.01, -0.02, 0.03))
     assert F.dissipation(m0, p0.heff(m0), p0.Ms, p0.V, 0.0) == 0.0
