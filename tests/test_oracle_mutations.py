@@ -300,3 +300,71 @@ def test_heun_corrector_reusing_the_predictor_slope(monkeypatch):
 def test_dissipation_with_flipped_sign(monkeypatch):
     _wrap(monkeypatch, F, "dissipation", lambda f: lambda *a, **k: -f(*a, **k))
     _caught(TL.test_dissipation_is_the_energy_rate_along_a_trajectory)
+
+
+# --------------------------------------- the rest of the Runge-Kutta family (Sec. 2.2)
+
+def _with_tableau(monkeypatch, name, **fields):
+    t = llg.TABLEAUS[name]
+    kw = dict(a=t.a, b=t.b, bstar=t.bstar, fsal=t.fsal, q=t.q)
+    kw.update(fields)
+    monkeypatch.setitem(llg.TABLEAUS, name, llg.Tableau(name, **kw))
+
+
+def test_rk4_with_interior_and_end_weights_swapped(monkeypatch):
+    _with_tableau(monkeypatch, "rk4", b=(1 / 3, 1 / 6, 1 / 6, 1 / 3))      # still sums to 1
+    _caught(TL.test_tableau_convergence_orders, "rk4", 4, [8e-12, 4e-12])
+
+
+def test_rk3_with_a_wrong_third_stage(monkeypatch):
+    _with_tableau(monkeypatch, "rk3", a=((), (1 / 2,), (0.0, 1.0)))         # c3 = 1 kept, a31 dropped
+    _caught(TL.test_tableau_convergence_orders, "rk3", 3, [4e-12, 2e-12])
+
+
+@pytest.mark.parametrize("name,q", [("rk23", 3), ("rkck", 5)])
+def test_embedded_weights_perturbed(monkeypatch, name, q):
+    bs = list(llg.TABLEAUS[name].bstar)
+    bs[0] *= 1.0 + 1e-2
+    _with_tableau(monkeypatch, name, bstar=tuple(bs))
+    _caught(TL.test_embedded_error_orders, name, q)
+
+
+def test_max_variation_rule_on_the_mean_speed(monkeypatch):
+    def step(p, m, tab, dm_max, h_cap=None):
+        k1 = p.rhs(m)
+        h = dm_max / float(np.sqrt((k1 * k1).sum(axis=0)).mean())        # mean instead of max
+        if h_cap:
+            h = min(h, h_cap)
+        return llg.rk_attempt(p, m, h, tab, k1)[0], h
+    monkeypatch.setattr(llg, "max_dm_step", step)
+    _caught(TL.test_max_dm_step_size_is_the_first_order_variation)
+
+
+def test_max_variation_rule_ignoring_the_cap(monkeypatch):
+    _wrap(monkeypatch, llg, "max_dm_step", lambda f: lambda p, m, tab, dm_max, h_cap=None: f(p, m, tab, dm_max))
+    _caught(TL.test_max_dm_step_size_is_the_first_order_variation)
+
+
+def test_heun_drawing_new_noise_for_the_corrector(monkeypatch):
+    def heun(p, m, dt, step=0):
+        k1 = p.rhs(m, step, dt)
+        k2 = p.rhs(m + dt * k1, step + (1 << 40), dt)         # an independent eta
+        return llg.normalize(m + 0.5 * dt * (k1 + k2))
+    monkeypatch.setattr(llg, "heun_step", heun)
+    _caught(TL.test_langevin_statistics_of_thermal_macrospins)
+
+
+# ------------------------------------------------ FFT sizes and periodic images (Sec. 3.3)
+
+def test_fft_sizes_rounded_to_powers_of_two(monkeypatch):
+    monkeypatch.setattr(demag, "_good_size", lambda n: 1 << max(0, (n - 1).bit_length()))
+    _caught(TD.test_padded_length_rule)
+
+
+def test_periodic_kernel_with_one_image_fewer(monkeypatch):
+    def outer(f):
+        def offsets(n, L, periodic, images):
+            return f(n, L, periodic, images - 1 if periodic else images)
+        return offsets
+    _wrap(monkeypatch, demag, "_axis_offsets", outer)
+    _caught(TD.test_fft_matches_direct_sum_periodic, (4, 3, 1), (True, False, False))
