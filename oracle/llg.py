@@ -6,7 +6,7 @@ maximum tolerable error per step).  Dividing Eq. (1) by Ms (M = Ms m):
 
     dm/dt = -gamma0/(1+alpha^2) [ m x H + alpha m x (m x H) ].
 
-Readings where the paper is silent (all listed in the design doc):
+Readings where the paper is silent:
 * RKDP tableau: Dormand & Prince (1980), J. Comput. Appl. Math. 6:19, FSAL,
   6 new evaluations per step.
 * step error  err = max_i | h sum_j (b_j - b*_j) k_j,i |  (Euclidean norm per
