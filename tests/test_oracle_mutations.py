@@ -182,9 +182,10 @@ def test_newell_f_with_a_flipped_term(monkeypatch):
         return f_bad
     _wrap(monkeypatch, newell, "newell_f", outer)
     # the flipped term cancels in the trace, so by symmetry the cube's self
-    # term stays 1/3; the point-dipole quadrature, an independent formula,
-    # sees it
+    # term stays 1/3; the point-dipole quadrature and Aharoni's prism factors,
+    # both independent formulas, see it
     _caught(TN.test_closed_form_and_quadrature_agree, (1.0, 1.0, 1.0))
+    _caught(TN.test_self_term_is_the_aharoni_prism_factor, (1.0, 2.0, 3.0))
 
 
 def test_newell_g_without_its_last_term(monkeypatch):

@@ -11,7 +11,10 @@ Closed forms and invariants, not the formula re-typed:
 * whole-prism identity: summing N over all cell pairs of a box of cells gives
   the self-term of the whole box (superposition), which ties every offset of
   the tensor - near and far - to one closed-form number;
-* thin-film and needle limits of the self-term.
+* thin-film and needle limits of the self-term;
+* the self-term equals Aharoni's closed-form demagnetising factors of a
+  rectangular prism (J. Appl. Phys. 83, 3432, 1998), an expression derived
+  independently of Newell's f and g.
 """
 
 import itertools
@@ -116,6 +119,47 @@ def test_whole_prism_identity(n, cell):
     gaps = _prism_identity_gap(n, cell)
     for c, g in gaps.items():
         assert g < 1e-11, (c, g)
+
+
+def _aharoni_dz(A, B, C):
+    """Demagnetising factor along the C side of a uniformly magnetised
+    rectangular prism with sides A, B, C: A. Aharoni, J. Appl. Phys. 83, 3432
+    (1998), Eq. 1, in terms of the half-sides a, b, c.  A closed form derived
+    independently of Newell's cell-pair functions f and g."""
+    a, b, c = A / 2, B / 2, C / 2
+    abc = np.sqrt(a * a + b * b + c * c)
+    ab, bc, ac = np.sqrt(a * a + b * b), np.sqrt(b * b + c * c), np.sqrt(a * a + c * c)
+    t = ((b * b - c * c) / (2 * b * c) * np.log((abc - a) / (abc + a))
+         + (a * a - c * c) / (2 * a * c) * np.log((abc - b) / (abc + b))
+         + b / (2 * c) * np.log((ab + a) / (ab - a))
+         + a / (2 * c) * np.log((ab + b) / (ab - b))
+         + c / (2 * a) * np.log((bc - b) / (bc + b))
+         + c / (2 * b) * np.log((ac - a) / (ac + a))
+         + 2 * np.arctan(a * b / (c * abc))
+         + (a ** 3 + b ** 3 - 2 * c ** 3) / (3 * a * b * c)
+         + (a * a + b * b - 2 * c * c) / (3 * a * b * c) * abc
+         + c / (a * b) * (ac + bc)
+         - (ab ** 3 + bc ** 3 + ac ** 3) / (3 * a * b * c))
+    return t / np.pi
+
+
+def test_aharoni_formula_itself():
+    # the restated formula before it serves as a pin: cube 1/3, trace 1
+    assert _aharoni_dz(1.0, 1.0, 1.0) == pytest.approx(1.0 / 3.0, rel=1e-14, abs=0.0)
+    for A, B, C in [(1.0, 2.0, 3.0), (10.0, 1.0, 0.5), (3.0, 7.0, 2.0)]:
+        assert _aharoni_dz(B, C, A) + _aharoni_dz(C, A, B) + _aharoni_dz(A, B, C) == pytest.approx(1.0, abs=1e-13)
+
+
+@pytest.mark.parametrize("sides", [(1.0, 2.0, 3.0), (4.0, 4.0, 2.0), (10.0, 1.0, 0.5), (3.0, 7.0, 2.0),
+                                   (100.0, 100.0, 1.0), (1.0, 1.0, 100.0)])
+def test_self_term_is_the_aharoni_prism_factor(sides):
+    # the cell self-term of Eq. 2 is the demagnetising factor of the cell
+    # itself, so every diagonal entry must equal Aharoni's closed form
+    A, B, C = sides
+    t = nw.newell_tensor(0.0, 0.0, 0.0, A, B, C)
+    assert abs(float(t["xx"]) - _aharoni_dz(B, C, A)) <= 1e-12
+    assert abs(float(t["yy"]) - _aharoni_dz(C, A, B)) <= 1e-12
+    assert abs(float(t["zz"]) - _aharoni_dz(A, B, C)) <= 1e-12
 
 
 def test_thin_film_and_needle_limits():
