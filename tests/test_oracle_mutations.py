@@ -198,6 +198,19 @@ def test_newell_g_without_its_last_term(monkeypatch):
     _caught(TN.test_closed_form_and_quadrature_agree, (1.0, 1.0, 1.0))
 
 
+def test_newell_g_with_a_flipped_arctangent_term(monkeypatch):
+    def outer(g):
+        def g_bad(x, y, z):
+            x_, y_, z_ = np.broadcast_arrays(*(np.asarray(v, float) for v in (x, y, z)))
+            R = np.sqrt(x_ * x_ + y_ * y_ + z_ * z_)
+            with np.errstate(divide="ignore", invalid="ignore"):
+                t = np.where(z_ * y_ * y_ != 0, z_ * y_ * y_ * np.arctan(x_ * z_ / (y_ * R)), 0.0)
+            return g(x, y, z) + t              # the sign of the z y^2/2 arctangent term flipped
+        return g_bad
+    _wrap(monkeypatch, newell, "newell_g", outer)
+    _caught(TN.test_near_field_matches_fine_quadrature, (1.0, 1.0, 1.0), [(2, 1, 1), (2, 2, 2)], 16)
+
+
 def test_newell_sum_with_a_wrong_centre_weight(monkeypatch):
     monkeypatch.setitem(newell._W, 0, 1.0)
     _caught(TN.test_offsite_trace_is_zero, (4.0, 4.0, 2.0))      # Laplace: the field is divergence-free
