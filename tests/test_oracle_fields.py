@@ -265,6 +265,21 @@ def test_stt_on_a_spiral_has_the_closed_form():
     assert bj == pytest.approx(P * F.MU_B / (F.E_CHARGE * MS * (1 + xi * xi)), rel=1e-15, abs=0.0)
 
 
+def test_current_derivative_on_an_open_three_cell_chain():
+    # central differences inside; at a free end the missing neighbour is the
+    # cell itself, so the end cells take half the one-sided difference
+    d, jx = 2e-9, 3e11
+    m = np.zeros((3, 1, 1, 3))
+    m[:, 0, 0, 0] = (1, 0, 0)
+    m[:, 0, 0, 1] = (0, 1, 0)
+    m[:, 0, 0, 2] = (0, 0, 1)
+    u = F.current_derivative(m, (jx, 0.0, 0.0), (d, 1e-9, 1e-9))
+    c = jx / (2 * d)
+    np.testing.assert_allclose(u[:, 0, 0, 0], c * np.array([-1, 1, 0]), rtol=1e-14)     # (m1 - m0)
+    np.testing.assert_allclose(u[:, 0, 0, 1], c * np.array([-1, 0, 1]), rtol=1e-14)     # (m2 - m0)
+    np.testing.assert_allclose(u[:, 0, 0, 2], c * np.array([0, -1, 1]), rtol=1e-14)     # (m2 - m1)
+
+
 def test_adiabatic_stt_advects_a_spiral():
     # xi = alpha and no field: dm/dt = b_j/(1+alpha^2) (j.grad)m, a rigid rotation of the
     # spiral about z at rate b_j j sin(kd)/d/(1+alpha^2) - a translation of the texture

@@ -153,6 +153,26 @@ def test_stt_with_the_current_derivative_reversed(monkeypatch):
     _caught(TF.test_stt_on_a_spiral_has_the_closed_form)
 
 
+def test_stt_reading_missing_neighbours_as_zero(monkeypatch):
+    def derivative(m, j, cell, pbc=(False, False, False)):
+        m = np.asarray(m, float)
+        u = np.zeros_like(m)
+        for axis, jc, d, per in ((3, j[0], cell[0], pbc[0]), (2, j[1], cell[1], pbc[1]), (1, j[2], cell[2], pbc[2])):
+            if jc == 0.0:
+                continue
+            n = m.shape[axis]
+            up, dn = np.roll(m, -1, axis=axis), np.roll(m, 1, axis=axis)
+            if not per:
+                last, first = [slice(None)] * 4, [slice(None)] * 4
+                last[axis], first[axis] = n - 1, 0
+                up[tuple(last)] = 0.0
+                dn[tuple(first)] = 0.0
+            u += jc * (up - dn) / (2.0 * d)
+        return u
+    monkeypatch.setattr(F, "current_derivative", derivative)
+    _caught(TF.test_current_derivative_on_an_open_three_cell_chain)
+
+
 def test_stt_prefactor_without_one_plus_xi_squared(monkeypatch):
     monkeypatch.setattr(F, "stt_bj", lambda P, xi, Ms: P * F.MU_B / (F.E_CHARGE * Ms))
     _caught(TF.test_stt_on_a_spiral_has_the_closed_form)
