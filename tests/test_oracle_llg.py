@@ -131,6 +131,22 @@ def _random_film(alpha, seed=0, shape=(16, 8, 1), B=(0, 0, 0.01)):
     return p, m
 
 
+def test_controller_special_cases():
+    # the step-size rule read for Sec. 2.2 (the paper gives none):
+    # f = 0.9 (tol/err)^(1/q) clamped to [0.2, 5], at most 1 right after a reject
+    tol = 1e-6
+    f = llg.controller_factor
+    assert f(tol, tol, False) == pytest.approx(0.9, rel=1e-15, abs=0.0)
+    assert f(32 * tol, tol, False) == pytest.approx(0.45, rel=1e-15, abs=0.0)    # q = 5: 2^5 -> 1/2
+    assert f(0.0, tol, False) == 5.0 and f(1e-30, tol, False) == 5.0
+    assert f(1e6 * tol, tol, False) == 0.2
+    assert f(1e-9 * tol, tol, True) == 1.0 and f(32 * tol, tol, True) == pytest.approx(0.45, rel=1e-15, abs=0.0)
+    st = llg.TableauStepper(_macrospin(0.1), _m0(1.0, 0.0), llg.TABLEAUS["rk23"], tol=tol)
+    assert st._factor(8 * tol, False) == pytest.approx(0.45, rel=1e-15, abs=0.0)                 # q = 3
+    st = llg.TableauStepper(_macrospin(0.1), _m0(1.0, 0.0), llg.TABLEAUS["rk12"], tol=tol)
+    assert st._factor(4 * tol, False) == pytest.approx(0.45, rel=1e-15, abs=0.0)                 # q = 2
+
+
 def test_energy_never_increases_under_damping():
     p, m = _random_film(0.5)
     st = llg.Stepper(p, m, h0=1e-14, tol=1e-6)

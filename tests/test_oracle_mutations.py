@@ -402,3 +402,17 @@ def test_periodic_kernel_with_one_image_fewer(monkeypatch):
         return offsets
     _wrap(monkeypatch, demag, "_axis_offsets", outer)
     _caught(TD.test_fft_matches_direct_sum_periodic, (4, 3, 1), (True, False, False))
+
+
+def test_controller_with_a_fourth_root(monkeypatch):
+    def factor(err, tol, after_reject):
+        f = 5.0 if err == 0.0 else 0.9 * (tol / err) ** 0.25
+        f = min(max(f, 0.2), 5.0)
+        return min(f, 1.0) if after_reject else f
+    monkeypatch.setattr(llg, "controller_factor", factor)
+    _caught(TL.test_controller_special_cases)
+
+
+def test_controller_growing_right_after_a_reject(monkeypatch):
+    _wrap(monkeypatch, llg, "controller_factor", lambda f: lambda err, tol, after_reject: f(err, tol, False))
+    _caught(TL.test_controller_special_cases)
