@@ -416,3 +416,27 @@ def test_controller_with_a_fourth_root(monkeypatch):
 def test_controller_growing_right_after_a_reject(monkeypatch):
     _wrap(monkeypatch, llg, "controller_factor", lambda f: lambda err, tol, after_reject: f(err, tol, False))
     _caught(TL.test_controller_special_cases)
+
+
+def test_dormand_prince_normalising_every_stage(monkeypatch):
+    # a legitimate variant, but not the reading taken (only the candidate
+    # m_{n+1} is renormalised): the generic tableau code, written separately,
+    # disagrees with it
+    def stages(p, m, h, k1=None):
+        k = [p.rhs(m) if k1 is None else k1]
+        for s in range(1, 6):
+            ms = m.copy()
+            for j, a in enumerate(llg.DP_A[s]):
+                if a != 0.0:
+                    ms = ms + h * a * k[j]
+            k.append(p.rhs(llg.normalize(ms)))
+        mn = m.copy()
+        for j in range(6):
+            if llg.DP_B[j] != 0.0:
+                mn = mn + h * llg.DP_B[j] * k[j]
+        mn = llg.normalize(mn)
+        k.append(p.rhs(mn))
+        e = sum(h * (llg.DP_B[j] - llg.DP_BSTAR[j]) * k[j] for j in range(7))
+        return mn, k, float(np.sqrt((e * e).sum(axis=0)).max())
+    monkeypatch.setattr(llg, "rkdp_stages", stages)
+    _caught(TL.test_generic_dormand_prince_equals_the_dedicated_one)
