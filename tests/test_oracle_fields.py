@@ -163,9 +163,17 @@ def test_gaussian_moments():
     assert np.all(np.abs(x.var(axis=1) - 1.0) < 5 * np.sqrt(2.0 / n))
     c = np.corrcoef(x)
     assert np.all(np.abs(c[np.triu_indices(3, 1)]) < 5 / np.sqrt(n))
-    # different step or seed -> different numbers
+    # different step or seed -> different numbers (the step's high word counts too)
     assert not np.allclose(eta, philox.thermal_eta((3, 1, 256, 256), seed=1234, step=8))
     assert not np.allclose(eta, philox.thermal_eta((3, 1, 256, 256), seed=1235, step=7))
+    assert not np.allclose(eta, philox.thermal_eta((3, 1, 256, 256), seed=1234, step=7 + (1 << 32)))
+    # uncorrelated in space and time (Eq. 6): x and y neighbours, the next step
+    e = eta.reshape(3, 256, 256)
+    nxt = philox.thermal_eta((3, 1, 256, 256), seed=1234, step=8).reshape(3, 256, 256)
+    for a, b in ((e[:, :, 1:], e[:, :, :-1]), (e[:, 1:, :], e[:, :-1, :]), (e, nxt)):
+        for c in range(3):
+            r = np.corrcoef(a[c].ravel(), b[c].ravel())[0, 1]
+            assert abs(r) < 5 / np.sqrt(a[c].size), r
 
 
 def test_uniform_open_interval_exact_in_binary32():

@@ -185,6 +185,35 @@ def test_thermal_variance_without_the_factor_two(monkeypatch):
     _caught(TL.test_langevin_statistics_of_thermal_macrospins)
 
 
+def _eta(cell_of=lambda c: c, high_word=True):
+    def eta(shape, seed, step):
+        _, nz, ny, nx = shape
+        cell = cell_of(np.arange(nz * ny * nx, dtype=np.uint64))
+        hi = (int(step) >> 32) & 0xFFFFFFFF if high_word else 0
+        w = philox.philox4x32_10(cell, int(step) & 0xFFFFFFFF, hi, 0,
+                                 int(seed) & 0xFFFFFFFF, (int(seed) >> 32) & 0xFFFFFFFF)
+        u = [philox.uniform_open(x) for x in w]
+        r01, r23 = np.sqrt(-2.0 * np.log(u[0])), np.sqrt(-2.0 * np.log(u[2]))
+        return np.stack([r01 * np.cos(2 * np.pi * u[1]), r01 * np.sin(2 * np.pi * u[1]),
+                         r23 * np.cos(2 * np.pi * u[3])]).reshape(3, nz, ny, nx)
+    return eta
+
+
+def test_unplanted_noise_variant_is_the_oracle():
+    np.testing.assert_array_equal(_eta()((3, 2, 5, 7), 99, 3 + (1 << 33)),
+                                  philox.thermal_eta((3, 2, 5, 7), 99, 3 + (1 << 33)))
+
+
+def test_noise_shared_by_neighbouring_cells(monkeypatch):
+    monkeypatch.setattr(philox, "thermal_eta", _eta(cell_of=lambda c: c // np.uint64(2)))
+    _caught(TF.test_gaussian_moments)
+
+
+def test_noise_ignoring_the_high_word_of_the_step(monkeypatch):
+    monkeypatch.setattr(philox, "thermal_eta", _eta(high_word=False))
+    _caught(TF.test_gaussian_moments)
+
+
 @pytest.mark.parametrize("name,value", [("_W1", 0xBB67AE86), ("_M0", 0xCD9E8D57)])
 def test_philox_with_a_wrong_constant(monkeypatch, name, value):
     monkeypatch.setattr(philox, name, np.uint64(value))
