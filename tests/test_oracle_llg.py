@@ -10,7 +10,8 @@ gamma' = gamma0/(1+alpha^2):
   frequency gamma0 (H + H_K) as theta0 -> 0;
 * convergence orders 1 (Euler), 2 (Heun), 5 (Dormand-Prince) and order 5 of
   the embedded error estimate;
-* energy does not increase under damping; relaxation reaches the torque bound;
+* energy does not increase under damping; relaxation reaches the torque bound,
+  and for a single cell it lands on the Stoner-Wohlfarth equilibrium angle;
 * Langevin: an ensemble of uncoupled thermal macrospins in a field has
   <cos theta> = coth x - 1/x, x = mu0 Ms V H / (kB T), which fixes the variance
   of Eq. 6 and the noise interpretation of the Heun scheme.
@@ -185,6 +186,25 @@ def test_relax_reaches_torque_bound():
     assert p.torque(mr) < 1e-4
     assert p.energy(mr) < E0
     assert steps > 0
+
+
+@pytest.mark.parametrize("psi_deg,B", [(30.0, 0.05), (60.0, 0.02), (80.0, 0.1), (45.0, 0.2)])
+def test_relax_reaches_the_stoner_wohlfarth_angle(psi_deg, B):
+    # one cubic cell (isotropic self-field, no exchange partner) with a uniaxial
+    # axis along z and a field at psi from it: the relaxed state lies in the
+    # x-z plane at the angle theta with Ku sin(2 theta) = mu0 Ms H sin(psi - theta),
+    # found here by bracketing (scipy), independently of the oracle's dynamics
+    from scipy.optimize import brentq
+    Ku = 5e4
+    psi = np.deg2rad(psi_deg)
+    p = llg.Problem((1, 1, 1), CELL, MS, 1.3e-11, 1.0, Ku=Ku, u=(0, 0, 1),
+                    B=(B * np.sin(psi), 0.0, B * np.cos(psi)))
+    H = B / F.MU0
+    theta = brentq(lambda th: Ku * np.sin(2 * th) + F.MU0 * MS * H * np.sin(th - psi), 0.0, psi)
+    mr, steps, tq = llg.relax(p, _m0(psi, 0.0), torque_tol=1e-9, tol=1e-8)
+    assert tq < 1e-9 and steps > 0
+    assert abs(np.arctan2(mr[0].item(), mr[2].item()) - theta) < 1e-7
+    assert abs(mr[1].item()) < 1e-7
 
 
 def test_rkdp_refuses_thermal_noise():
