@@ -4,6 +4,8 @@
   is an exact eigenvector of the discrete Laplacian with eigenvalue
   -(2 - 2 cos k d)/d^2; at a free boundary a missing neighbour adds nothing
   (checked on a three-cell chain worked by hand);
+* a Bloch wall theta = 2 atan(exp(x/D)), D = sqrt(A/K), is an equilibrium of
+  exchange + anisotropy up to a residual torque that falls like (d/D)^2;
 * exchange energy equals the bond sum A V sum_bonds |m_i - m_j|^2 / d^2;
 * anisotropy: |H_an| = 2Ku/(mu0 Ms) cos(theta) along u; energy -Ku V cos^2;
   the same per cell with a different easy axis in every cell;
@@ -55,6 +57,28 @@ def test_free_boundary_three_cell_chain():
     np.testing.assert_allclose(H[:, 0, 0, 0], c * np.array([-1, 1, 0]), rtol=1e-14)     # only right nbr
     np.testing.assert_allclose(H[:, 0, 0, 1], c * np.array([1, -2, 1]), rtol=1e-14)
     np.testing.assert_allclose(H[:, 0, 0, 2], c * np.array([0, 1, -1]), rtol=1e-14)     # only left nbr
+
+
+def test_bloch_wall_is_an_equilibrium_to_second_order():
+    # the 180-degree wall theta(x) = 2 atan(exp(x/D)), D = sqrt(A/K), balances
+    # exchange (Eq. 3) and uniaxial anisotropy (Eq. 4) exactly in the
+    # continuum; on the lattice the residual torque falls like (d/D)^2
+    A, K = 1.3e-11, 5e5
+    D = np.sqrt(A / K)
+    HK = 2 * K / (F.MU0 * MS)
+    res = []
+    for frac in (10, 20, 40):
+        d = D / frac
+        n = 40 * frac + 1
+        x = (np.arange(n) - n // 2) * d
+        th = 2 * np.arctan(np.exp(x / D))
+        m = np.zeros((3, 1, 1, n))
+        m[0, 0, 0], m[2, 0, 0] = np.sin(th), np.cos(th)
+        H = F.exchange_field(m, MS, A, (d, d, d)) + F.anisotropy_field(m, MS, K, (0.0, 0.0, 1.0))
+        res.append(float(np.linalg.norm(np.cross(m, H, axis=0), axis=0).max()) / HK)
+        assert res[-1] <= 0.3 / frac ** 2
+    assert np.log2(res[0] / res[1]) == pytest.approx(2.0, abs=0.05)
+    assert np.log2(res[1] / res[2]) == pytest.approx(2.0, abs=0.05)
 
 
 def test_exchange_energy_equals_bond_sum():

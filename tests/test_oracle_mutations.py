@@ -72,6 +72,11 @@ def test_exchange_with_flipped_sign(monkeypatch):
     _caught(TF.test_spin_wave_eigenvalue, 1)
 
 
+def test_exchange_without_its_factor_two(monkeypatch):
+    _wrap(monkeypatch, F, "exchange_field", lambda f: lambda *a, **k: 0.5 * f(*a, **k))
+    _caught(TF.test_bloch_wall_is_an_equilibrium_to_second_order)
+
+
 def test_exchange_without_the_y_axis(monkeypatch):
     monkeypatch.setattr(F, "exchange_field", _exchange(skip_axis=2))
     _caught(TF.test_exchange_energy_equals_bond_sum)
