@@ -5,6 +5,9 @@ and exerts no torque; no exchange partner) with H = B/mu0 along z and
 gamma' = gamma0/(1+alpha^2):
     phi(t) = phi0 + gamma' H t,   cos theta(t) = tanh(alpha gamma' H t + atanh cos theta0).
 * Larmor: alpha = 0 precession at gamma0 H;
+* Kittel: a single flat cell precesses about an in-plane field at
+  gamma0 sqrt((H + (Nyy - Nxx) Ms)(H + (Nzz - Nxx) Ms)), its N from Aharoni's
+  prism formula;
 * uniaxial easy axis along the field (alpha = 0): precession at
   gamma0 (H + 2Ku/(mu0 Ms) cos theta0), which is Kittel's small-angle FMR
   frequency gamma0 (H + H_K) as theta0 -> 0;
@@ -80,6 +83,31 @@ def test_uniaxial_precession_frequency():
     n = 600
     m = llg.rkdp_fixed(p, _m0(th0, 0.0), t / n, n)
     np.testing.assert_allclose(m, _m0(th0, 0.0), atol=1e-9)
+
+
+def test_flat_cell_precesses_at_the_kittel_frequency():
+    # one 4 x 4 x 1 nm cell: its self-field (Eq. 2) is -N.M with the prism's
+    # demagnetising factors, which Aharoni's closed form gives independently of
+    # the oracle; small-angle precession about an in-plane field H along x then
+    # has Kittel's frequency  w = gamma0 sqrt((H + (Nyy - Nxx) Ms)(H + (Nzz - Nxx) Ms))
+    from closed_forms import aharoni_dz
+    cell = (4e-9, 4e-9, 1e-9)
+    Nxx, Nyy, Nzz = aharoni_dz(cell[1], cell[2], cell[0]), aharoni_dz(cell[2], cell[0], cell[1]), aharoni_dz(*cell)
+    B = 0.05
+    H = B / F.MU0
+    T = 2 * np.pi / (F.GAMMA0 * np.sqrt((H + (Nyy - Nxx) * MS) * (H + (Nzz - Nxx) * MS)))
+    p = llg.Problem((1, 1, 1), cell, MS, 1.3e-11, 0.0, B=(B, 0.0, 0.0))
+    m = _m0(np.pi / 2 - 1e-3, 0.0)                  # 1 mrad off the field, towards +z
+    n = 400
+    h = T / n
+    t, ys = [], []
+    for i in range(3 * n + 5):
+        t.append(i * h)
+        ys.append(m[1].item())
+        m = llg.rkdp_fixed(p, m, h, 1)
+    cross = [t[i] - ys[i] * h / (ys[i + 1] - ys[i]) for i in range(len(ys) - 1) if ys[i] > 0 >= ys[i + 1]]
+    assert len(cross) >= 2
+    assert np.mean(np.diff(cross)) == pytest.approx(T, rel=1e-6, abs=0.0)
 
 
 def _order(stepper, hs, T, alpha=0.1, B=0.05):

@@ -308,6 +308,7 @@ def test_convolution_with_transposed_off_diagonal_components(monkeypatch):
 def test_demag_field_without_the_minus_sign(monkeypatch):
     _wrap(monkeypatch, demag, "demag_field_fft", lambda f: lambda *a, **k: -f(*a, **k))
     _caught(TD.test_uniform_body_mean_field, (16, 8, 1), (4.0, 4.0, 2.0), 0)
+    _caught(TL.test_flat_cell_precesses_at_the_kittel_frequency)
 
 
 def test_padding_shorter_than_2n_minus_1_is_refused(monkeypatch):
