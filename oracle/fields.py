@@ -28,7 +28,10 @@ variational derivative is the field above):
 
 m: (3, nz, ny, nx) float64, unit vectors.  Fields in A/m, energy in J.
 Pins: tests/test_oracle_fields.py (uniform state, spin-wave eigenvalue,
-closed-form anisotropy, energy = sum of bond energies, Langevin statistics).
+free-boundary chains for exchange and the current derivative, the Bloch wall
+as an equilibrium to second order, closed-form anisotropy, energy = sum of
+bond energies, cubic field = minus the energy gradient, the spin-transfer
+torque on a spiral) and tests/test_oracle_llg.py (Langevin statistics).
 """
 
 import numpy as np

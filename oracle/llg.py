@@ -24,8 +24,10 @@ Readings where the paper is silent:
   the step itself is the method's (max_dm_step).
 
 Pins: tests/test_oracle_llg.py (macrospin precession and damping closed forms,
-Larmor/Kittel frequencies, convergence orders 1/2/5, |m| conservation, energy
-decay, Langevin statistics of the thermal macrospin).
+Larmor/Kittel frequencies, convergence orders 1/2/5 and of every tableau,
+embedded error orders, the step controller's special cases, |m| conservation,
+energy decay, the Stoner-Wohlfarth angle reached by relaxation, Langevin
+statistics of the thermal macrospin, the dissipation as the energy rate).
 """
 
 import numpy as np

@@ -24,7 +24,11 @@ nodes on [-d_a, 0] and [0, d_a].
 
 Pins (tests/test_oracle_newell.py): cube self-term 1/3, self trace 1, off-site
 trace 0, parity, far field -> point dipole, Newell == quadrature where both are
-accurate, whole-prism identity, 50-digit mpmath evaluation.
+accurate (also 2-3.5 cells apart with more nodes, which pins the off-diagonal
+entries in the near field), whole-prism identity, the self-term against
+Aharoni's closed-form prism factors, 50-digit mpmath evaluation; the
+self-term in the dynamics by the Kittel precession of a flat cell
+(tests/test_oracle_llg.py).
 
 All lengths may be given in any unit (N is dimensionless and scale-free).
 """
