@@ -13,7 +13,8 @@ gamma' = gamma0/(1+alpha^2):
   frequency gamma0 (H + H_K) as theta0 -> 0;
 * convergence orders 1 (Euler), 2 (Heun), 5 (Dormand-Prince) and order 5 of
   the embedded error estimate;
-* energy does not increase under damping; relaxation reaches the torque bound,
+* energy is conserved without damping up to the integrator's O(h^5) drift
+  (the field is the exact energy gradient); energy does not increase under damping; relaxation reaches the torque bound,
   and for a single cell it lands on the Stoner-Wohlfarth equilibrium angle;
 * Langevin: an ensemble of uncoupled thermal macrospins in a field has
   <cos theta> = coth x - 1/x, x = mu0 Ms V H / (kB T), which fixes the variance
@@ -187,6 +188,21 @@ def test_energy_never_increases_under_damping():
     scale = abs(E[0])
     assert np.all(np.diff(E) <= 1e-6 * scale)
     assert E[-1] < E[0]
+
+
+def test_undamped_energy_drift_falls_with_the_method_order():
+    # with alpha = 0, dm/dt is perpendicular to H_eff, and H_eff is minus the
+    # energy gradient (a symmetric magnetostatic kernel, exchange, anisotropy,
+    # Zeeman), so the energy is conserved; a Dormand-Prince run drifts only by
+    # its local error, O(h^5) over a fixed time
+    from paper_1102_3069_gb300 import inputs
+    shape = (8, 6, 2)
+    p = llg.Problem(shape, (4e-9, 3e-9, 2e-9), MS, 1.3e-11, 0.0, Ku=2e4, u=(0.3, 0.4, 1.0), B=(0.01, -0.02, 0.03))
+    m0 = llg.normalize(inputs.smooth_tilt(shape).astype(np.float64))
+    E0 = p.energy(m0)
+    drift = [abs(p.energy(llg.rkdp_fixed(p, m0, h, int(round(2e-12 / h)))) - E0) / abs(E0) for h in (4e-14, 2e-14)]
+    assert drift[1] < 1e-10
+    assert np.log2(drift[0] / drift[1]) == pytest.approx(5.0, abs=0.3)
 
 
 def test_candidate_norm_error_is_of_order_tol():

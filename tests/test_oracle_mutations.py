@@ -305,6 +305,36 @@ def test_convolution_with_transposed_off_diagonal_components(monkeypatch):
     _caught(TD.test_fft_matches_direct_sum_open, (5, 3, 2), (4.0, 4.0, 2.0))
 
 
+def _field_fft(yx_sign=1.0):
+    """Stages (i)-(iii) of the convolution with the sign of N_xy in the y row as a knob."""
+    def field_fft(m, Ms, Khat, L):
+        _, nz, ny, nx = m.shape
+        Lx, Ly, Lz = L
+        M = np.zeros((3, Lz, Ly, Lx))
+        M[:, :nz, :ny, :nx] = Ms * m
+        Mh = [np.fft.rfftn(M[c], axes=(0, 1, 2)) for c in range(3)]
+        K = Khat
+        Hh = [-(K["xx"] * Mh[0] + K["xy"] * Mh[1] + K["xz"] * Mh[2]),
+              -(yx_sign * K["xy"] * Mh[0] + K["yy"] * Mh[1] + K["yz"] * Mh[2]),
+              -(K["xz"] * Mh[0] + K["yz"] * Mh[1] + K["zz"] * Mh[2])]
+        H = np.stack([np.fft.irfftn(Hh[c], s=(Lz, Ly, Lx), axes=(0, 1, 2)) for c in range(3)])
+        return H[:, :nz, :ny, :nx].copy()
+    return field_fft
+
+
+def test_unplanted_convolution_variant_is_the_oracle():
+    d = demag.Demag((5, 4, 3), (4.0, 3.0, 2.0))
+    m = np.random.default_rng(4).standard_normal((3, 3, 4, 5))
+    np.testing.assert_array_equal(_field_fft()(m, 2.0, d.Khat, d.L), demag.demag_field_fft(m, 2.0, d.Khat, d.L))
+
+
+def test_demag_product_with_an_asymmetric_row(monkeypatch):
+    # N_xy enters the y row with the wrong sign: the field is no longer the
+    # gradient of an energy, so an undamped run stops conserving it
+    monkeypatch.setattr(demag, "demag_field_fft", _field_fft(yx_sign=-1.0))
+    _caught(TL.test_undamped_energy_drift_falls_with_the_method_order)
+
+
 def test_demag_field_without_the_minus_sign(monkeypatch):
     _wrap(monkeypatch, demag, "demag_field_fft", lambda f: lambda *a, **k: -f(*a, **k))
     _caught(TD.test_uniform_body_mean_field, (16, 8, 1), (4.0, 4.0, 2.0), 0)
