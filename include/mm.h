@@ -60,7 +60,8 @@ typedef struct mm_stats {
     double t;               /* simulated time, s                                    */
     double dt;              /* next proposed step (RKDP) or last fixed step, s      */
     double last_err;        /* last step-error estimate (dimensionless, |dm|)       */
-    double max_torque;      /* max_i |m_i x H_i|/Ms at the last accepted state      */
+    double max_torque;      /* max_i |m_i x H_i|/Ms at the last state judged by the */
+                            /* torque bound (see mm_advance)                        */
     double energy;          /* last energy computed by mm_eval_heff, J              */
     int status;             /* device-side status: 0 or a negative mm_status        */
     int done;               /* 1 when t_end / torque target reached or on failure   */
@@ -232,10 +233,19 @@ int mm_store(mm_ctx* ctx, float* m);
  * [0.2, 5].  tol < 0 selects fixed steps of dt_s for an adaptive method (the
  * error estimate is still computed and reported).  The thermal field (T > 0)
  * needs a fixed-step method with a fixed dt (MM_EULER, MM_HEUN, MM_RK3 or
- * MM_RK4; one noise draw per step shared by its stages).  t_end_s > 0 stops the
- * run exactly at t_end_s (the last step is shortened); torque_tol > 0 stops
- * it once max |m x H|/Ms < torque_tol (relaxation).  Once stopped, queued
- * steps do no work.
+ * MM_RK4; one noise draw per step shared by its stages).  t_end_s > 0 stops
+ * the run at t_end_s: the Runge-Kutta tableaus (MM_RK3 and above) shorten their
+ * last step to end exactly there (with the noise amplitude of the full dt);
+ * MM_EULER and MM_HEUN keep their dt and stop at the first step that reaches
+ * or passes t_end_s (they may overshoot it by less than one dt).
+ * torque_tol > 0 stops the run at the first state where
+ * max |m x H|/Ms < torque_tol (relaxation), judged where the method evaluates
+ * the field at an accepted state: the last stage of MM_RKDP and MM_RK23 (first
+ * same as last) judges the new state; MM_EULER, MM_HEUN and the other
+ * tableaus judge the state a step starts from, and then keep that state
+ * without taking the step.  mm_stats.max_torque is the torque of the state so
+ * judged last (for the latter methods: the state the last step started from).
+ * Once stopped, queued steps do no work.
  */
 int mm_advance(mm_ctx* ctx, int method, long nsteps, double dt_s, double tol,
                double t_end_s, double torque_tol);

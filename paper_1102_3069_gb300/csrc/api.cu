@@ -829,7 +829,9 @@ int mm_advance(mm_ctx* ctx, int method, long nsteps, double dt_s, double tol, do
             }
         }
     }
-    if (nsteps > 0) ctx->spec = (is_rk || maxdm) ? mm_ctx::SPEC_NONE : mm_ctx::SPEC_MCUR;
+    // Euler/Heun leave the spectrum of the state slot in place, unless a torque
+    // stop kept m_n after its pass had transformed the rejected new state
+    if (nsteps > 0) ctx->spec = (is_rk || maxdm || torque_tol > 0.0) ? mm_ctx::SPEC_NONE : mm_ctx::SPEC_MCUR;
     if (is_rk && !rk.fsal) ctx->k1_valid = false;
     return MM_OK;
 }

@@ -617,6 +617,11 @@ __device__ void finalize(const HotParams& p, const LaunchArgs& a) {
             break;
         case LM_RKFINAL: {
             st->last_err = err;
+            // a tableau whose last stage is not the new state evaluates the
+            // field at a stage point: its torque says nothing about m_{n+1}.
+            // The next step's k1 pass (at the accepted state) takes the
+            // torque decision instead.
+            const bool tq_here = p.rk_fsal != 0;
             if (bad || !isfinite(err)) { st->status = -5; st->done = 1; break; }
             const double q = c_rkq[p.rk];
             const bool fixed = st->fixed_h || q == 0.0;
@@ -630,7 +635,7 @@ __device__ void finalize(const HotParams& p, const LaunchArgs& a) {
                 st->cur ^= 1;
                 st->accepted += 1;
                 st->step_index += 1;
-                st->max_torque = tq;
+                if (tq_here) st->max_torque = tq;
                 st->after_reject = 0;
             } else {
                 f = fmin(f, 1.0);
@@ -643,13 +648,18 @@ __device__ void finalize(const HotParams& p, const LaunchArgs& a) {
                 if (left <= 1e-12 * st->t_end) st->done = 1;
                 else st->h = fmin(st->h, left);
             }
-            if (accept && st->torque_tol > 0.0 && tq < st->torque_tol) st->done = 1;
+            if (tq_here && accept && st->torque_tol > 0.0 && tq < st->torque_tol) st->done = 1;
             if (!st->done && st->h < st->h_min) { st->status = -4; st->done = 1; }
             break;
         }
         case LM_EULER:
         case LM_HEUN2:
             if (bad) { st->status = -5; st->done = 1; break; }
+            // tq = max |m x h| at m_n (the Euler pass, or Heun's first stage).
+            // Below the bound the run stops at m_n: the new state just written
+            // to the other slot is not taken, and time does not advance.
+            st->max_torque = tq;
+            if (st->torque_tol > 0.0 && tq < st->torque_tol) { st->done = 1; break; }
             st->t += p.dt_d;
             st->cur ^= 1;
             st->step_index += 1;
@@ -666,12 +676,15 @@ __device__ void finalize(const HotParams& p, const LaunchArgs& a) {
 // EV = false: a pass that never runs in evaluation mode (no energy sums).
 template <bool EV = true>
 __device__ void reduce_and_finish(const HotParams& p, const LaunchArgs& a, Partials pt, int nblk) {
-    if (a.mode == LM_RK || a.mode == LM_HEUN1) {
+    if (a.mode == LM_RK) {
         // intermediate stages reduce nothing but the non-finite flag, which the
         // step's last pass reads: one vote per warp, an atomic only when set
         if (__any_sync(0xffffffffu, pt.bad) && (threadIdx.x & 31) == 0) atomicOr(&p.st->bad, 1u);
         return;
     }
+    // Heun's first stage evaluates m_n: it reduces the torque there (one atomic
+    // per block) for the second stage's last block, which stops the run on it
+    const bool last_pass = a.mode != LM_HEUN1;
     __shared__ float r_err[32], r_tq[32];
     __shared__ double r_e[32], r_t[32];
     __shared__ unsigned r_bad[32];
@@ -708,9 +721,12 @@ __device__ void reduce_and_finish(const HotParams& p, const LaunchArgs& a, Parti
             atomicAdd(&st->tsq_acc, pt.tsq);
         }
         if (pt.bad) atomicOr(&st->bad, 1u);
-        __threadfence();
-        const unsigned prev = atomicAdd(&st->blocks_done, 1u);
-        s_last = (prev == (unsigned)nblk - 1u);
+        s_last = 0;
+        if (last_pass) {
+            __threadfence();
+            const unsigned prev = atomicAdd(&st->blocks_done, 1u);
+            s_last = (prev == (unsigned)nblk - 1u);
+        }
     }
     __syncthreads();
     if (s_last && threadIdx.x == 0) {
@@ -914,6 +930,7 @@ __device__ __forceinline__ f3 update_cell(const HotParams& p, const LaunchArgs& 
         case LM_EULER: {
             next = normalized(axpy(sc.c[0], k, m));
             st3(p.ms[1 - cur], cell, n, next);
+            pt.torque = fmaxf(pt.torque, tq);           // at m_n
             pt.bad |= !finite3(next);
             break;
         }
@@ -921,6 +938,7 @@ __device__ __forceinline__ f3 update_cell(const HotParams& p, const LaunchArgs& 
             st3(p.ks[cur], cell, n, k);
             next = axpy(sc.c[0], k, m);
             st3(p.mstage[0], cell, n, next);
+            pt.torque = fmaxf(pt.torque, tq);           // at m_n
             pt.bad |= !finite3(k);
             break;
         }
