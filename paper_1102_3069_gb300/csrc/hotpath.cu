@@ -231,25 +231,39 @@ __global__ void __launch_bounds__(XS<LOGP>::NT, XS<LOGP>::MINB) k_xfwd(HotParams
     float* wout = p.mstage[0];
     const Coef c21 = comb ? split(st->h * c_rka[p.rk][2][1]) : Coef{0.f, 0.f};
     const int NX = p.nx, NY = p.ny;
-    for (int idx = threadIdx.x; idx < S::NL * S::P; idx += S::NT) {
-        const int l = idx >> LOGP, x = idx & (S::P - 1);
-        const int c = (2 * l) / S::TY, ty = 2 * l - c * S::TY;
-        const int y = y0 + ty;
-        float2 v = make_float2(0.f, 0.f);
-        if (x < NX) {
-            const long long i0 = (long long)c * n + ((long long)z * NY + y) * NX + x;
-            if (y < NY) {
-                float u = src[i0];
-                if (comb) { u = fmaf(c21.lo, k1[i0], fmaf(c21.hi, k1[i0], u)); wout[i0] = u; }
-                v.x = u;
-            }
-            if (y + 1 < NY) {
-                float u = src[i0 + NX];
-                if (comb) { u = fmaf(c21.lo, k1[i0 + NX], fmaf(c21.hi, k1[i0 + NX], u)); wout[i0 + NX] = u; }
-                v.y = u;
+    // loads of CH items in flight at once, then their combination and stores
+    constexpr int NIT = (S::NL * S::P + S::NT - 1) / S::NT;
+    constexpr int CH = NIT < 8 ? NIT : 8;
+    for (int it0 = 0; it0 < NIT; it0 += CH) {
+        float u0[CH], u1[CH], g0[CH], g1[CH];
+#pragma unroll
+        for (int q = 0; q < CH; ++q) {
+            const int idx = threadIdx.x + (it0 + q) * S::NT;
+            const int l = idx >> LOGP, x = idx & (S::P - 1);
+            const int c = (2 * l) / S::TY, ty = 2 * l - c * S::TY;
+            const int y = y0 + ty;
+            u0[q] = u1[q] = g0[q] = g1[q] = 0.f;
+            if (idx < S::NL * S::P && x < NX) {
+                const long long i0 = (long long)c * n + ((long long)z * NY + y) * NX + x;
+                if (y < NY) { u0[q] = src[i0]; if (comb) g0[q] = k1[i0]; }
+                if (y + 1 < NY) { u1[q] = src[i0 + NX]; if (comb) g1[q] = k1[i0 + NX]; }
             }
         }
-        sm[l * S::LS + pad(x)] = v;
+#pragma unroll
+        for (int q = 0; q < CH; ++q) {
+            const int idx = threadIdx.x + (it0 + q) * S::NT;
+            if (idx >= S::NL * S::P) continue;
+            const int l = idx >> LOGP, x = idx & (S::P - 1);
+            const int c = (2 * l) / S::TY, ty = 2 * l - c * S::TY;
+            const int y = y0 + ty;
+            float2 v = make_float2(u0[q], u1[q]);
+            if (comb && x < NX) {
+                const long long i0 = (long long)c * n + ((long long)z * NY + y) * NX + x;
+                if (y < NY) { v.x = fmaf(c21.lo, g0[q], fmaf(c21.hi, g0[q], v.x)); wout[i0] = v.x; }
+                if (y + 1 < NY) { v.y = fmaf(c21.lo, g1[q], fmaf(c21.hi, g1[q], v.y)); wout[i0 + NX] = v.y; }
+            }
+            sm[l * S::LS + pad(x)] = v;
+        }
     }
     __syncthreads();
     fft_lines<LOGP, S::NL, false>(sm, p.tw);
@@ -1030,14 +1044,31 @@ __global__ void __launch_bounds__(XS<LOGP>::NT, XS<LOGP>::MINB) k_xinv_local(Hot
         s_cur = st->cur;
         s_tstep = (a.mode == LM_EVAL) ? p.thermal_step : st->step_index;
     }
-    for (int idx = threadIdx.x; idx < S::NL * S::HX; idx += S::NT) {
-        const int l = idx / S::HX, k = idx - l * S::HX;
-        const int c = (2 * l) / S::TY, ty = 2 * l - c * S::TY;
-        const float4 v = *reinterpret_cast<const float4*>(
-            p.s1 + ((long long)(c * S::HX + k) * p.nz + z) * p.nyp + y0 + ty);
-        // Z = A + iB with A = (v.x, v.y), B = (v.z, v.w); Z[-k] = conj(A) + i conj(B)
-        sm[l * S::LS + pad(k)] = make_float2(v.x - v.w, v.y + v.z);
-        if (k > 0 && 2 * k < S::P) sm[l * S::LS + pad(S::P - k)] = make_float2(v.x + v.w, v.z - v.y);
+    {
+        // every load of the block's spectrum in flight at once, then the unpack
+        constexpr int NLD = (S::NL * S::HX + S::NT - 1) / S::NT;
+        float4 vv[NLD];
+#pragma unroll
+        for (int it = 0; it < NLD; ++it) {
+            const int idx = threadIdx.x + it * S::NT;
+            if (idx < S::NL * S::HX) {
+                const int l = idx / S::HX, k = idx - l * S::HX;
+                const int c = (2 * l) / S::TY, ty = 2 * l - c * S::TY;
+                vv[it] = *reinterpret_cast<const float4*>(
+                    p.s1 + ((long long)(c * S::HX + k) * p.nz + z) * p.nyp + y0 + ty);
+            }
+        }
+#pragma unroll
+        for (int it = 0; it < NLD; ++it) {
+            const int idx = threadIdx.x + it * S::NT;
+            if (idx < S::NL * S::HX) {
+                const int l = idx / S::HX, k = idx - l * S::HX;
+                const float4 v = vv[it];
+                // Z = A + iB with A = (v.x, v.y), B = (v.z, v.w); Z[-k] = conj(A) + i conj(B)
+                sm[l * S::LS + pad(k)] = make_float2(v.x - v.w, v.y + v.z);
+                if (k > 0 && 2 * k < S::P) sm[l * S::LS + pad(S::P - k)] = make_float2(v.x + v.w, v.z - v.y);
+            }
+        }
     }
     __syncthreads();
     fft_lines<LOGP, S::NL, true>(sm, p.tw);
