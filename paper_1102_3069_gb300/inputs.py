@@ -168,3 +168,56 @@ def relax_films(n, seed=0, size=128, alpha=1.0):
         out.append(dict(shape=(size, size, 1), cell=(4e-9, 4e-9, 3e-9), pbc=(0, 0, 0), material=mat,
                         m_seed=seed * 100003 + 50000 + i))
     return out
+
+
+# ---- learned warm start (Fourier neural operator on 128 x 128 films) -------
+
+FNO_N, FNO_WIDTH, FNO_MODES, FNO_CIN, FNO_CHID, FNO_COUT = 128, 32, 16, 16, 128, 3
+
+
+def fno_features(samples):
+    """Input fields (B, 16, 128, 128) float32 of the warm-start operator for
+    relaxation samples (``relax_films``): channel 0 Ms/1e6, 1 Ku/5e4, 2-3 the
+    in-plane easy axis, 4-5 the in-plane applied field / 0.08 T, 6 (x+1/2)/128,
+    7 (y+1/2)/128; channels 8-15 zero."""
+    n = FNO_N
+    x = np.zeros((len(samples), FNO_CIN, n, n), dtype=np.float32)
+    xs = ((np.arange(n) + 0.5) / n).astype(np.float32)
+    for b, s in enumerate(samples):
+        m = s["material"]
+        vals = [m["Ms"] / 1e6, m["Ku"] / 5e4, m["easy_axis"][0], m["easy_axis"][1], m["B"][0] / 0.08,
+                m["B"][1] / 0.08]
+        for ch, v in enumerate(vals):
+            x[b, ch] = v
+        x[b, 6] = xs[None, :]
+        x[b, 7] = xs[:, None]
+    return x
+
+
+def fno_init(seed=0):
+    """Initial weights of the warm-start operator (float64 numpy arrays):
+    uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) for the point-wise maps and their
+    biases, and spectral weights (1/(32*32)) * U[0,1) for the real and the
+    imaginary part (the usual FNO initialisation).  Spectral weights are
+    indexed [mode, out, in], mode = kx*32 + (index of ky in 0..15, 112..127)."""
+    g = rng(seed + 6000)
+    W, C, H, O = FNO_WIDTH, FNO_CIN, FNO_CHID, FNO_COUT
+    nm = FNO_MODES * 2 * FNO_MODES
+
+    def lin(o, i):
+        a = 1.0 / np.sqrt(i)
+        return g.uniform(-a, a, (o, i)), g.uniform(-a, a, o)
+
+    p = {}
+    p["lift_w"], p["lift_b"] = lin(W, 8)
+    p["lift_w"] = np.concatenate([p["lift_w"], np.zeros((W, C - 8))], axis=1)
+    sc = 1.0 / (W * W)
+    p["spec_w"] = [sc * (g.random((nm, W, W)) + 1j * g.random((nm, W, W))) for _ in range(4)]
+    p["pw_w"], p["pw_b"] = [], []
+    for _ in range(4):
+        w, b = lin(W, W)
+        p["pw_w"].append(w)
+        p["pw_b"].append(b)
+    p["proj1_w"], p["proj1_b"] = lin(H, W)
+    p["proj2_w"], p["proj2_b"] = lin(O, H)
+    return p
