@@ -571,6 +571,130 @@ def run_relax(args):
     }
 
 
+def _relax_films(films, m_start, stream, tq_tol, err_tol, max_steps):
+    """Relax the films from the given start states together (mm_batch_relax);
+    returns (relaxed states, wall seconds of the relaxation, steps, torques, converged)."""
+    import torch
+
+    from paper_1102_3069_gb300 import binding as B
+    with torch.cuda.stream(stream):
+        sol = [B.Solver(f["shape"], f["cell"], pbc=f["pbc"], stream=stream.cuda_stream, tensor=False,
+                        **f["material"]) for f in films]
+        bt = B.Batch(sol, stream.cuda_stream)
+        ms = [m.clone() for m in m_start]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, steps, tq, conv = B.mm_batch_relax(bt.b, ms, tq_tol, err_tol, max_steps)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+    del bt, sol
+    return ms, t, steps, tq, conv
+
+
+def run_warmstart(args):
+    """Learned warm start of the relaxation (128 x 128 x 1 films, 4 x 4 x 3 nm,
+    random material, in-plane easy axis and field, alpha 1): the solver relaxes
+    n_train films from random unit vectors to max |m x H|/Ms < 1e-4 (the
+    training set), the Fourier neural operator learns relaxed m from the film's
+    parameters (Adam, bf16 tensor-core kernels), and on held-out films the
+    time to relax from its prediction (inference included) is compared with
+    the time from random unit vectors."""
+    import numpy as np
+    import torch
+
+    from paper_1102_3069_gb300 import binding as B
+    from paper_1102_3069_gb300 import inputs
+
+    n_train, n_eval, bs = args.warmstart, args.warmstart_eval, 32
+    epochs, lr0 = args.warmstart_epochs, 1e-3
+    tq_tol, err_tol, max_steps = 1e-4, 1e-6, args.relax_max_steps
+    stream = torch.cuda.Stream()
+    # training set: relaxed states from the solver itself
+    t0 = time.perf_counter()
+    train = inputs.relax_films(n_train, seed=100)
+    Y = torch.empty((n_train, 3, 128, 128), dtype=torch.float32, device="cuda")
+    chunk = 256
+    gen_steps = []
+    for i in range(0, n_train, chunk):
+        films = train[i:i + chunk]
+        m0 = [torch.from_numpy(inputs.random_unit(f["shape"], f["m_seed"])).cuda() for f in films]
+        ms, _, steps, _, _ = _relax_films(films, m0, stream, tq_tol, err_tol, max_steps)
+        for j, m in enumerate(ms):
+            Y[i + j] = m.view(3, 128, 128)
+        gen_steps += steps
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    X = torch.from_numpy(inputs.fno_features(train)).cuda()
+    # training
+    net = B.Fno(bs, stream.cuda_stream)
+    net.set_params(inputs.fno_init(0))
+    g = np.random.default_rng(0)
+    nb = n_train // bs
+    total = epochs * nb
+    losses = []
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        it = 0
+        for ep in range(epochs):
+            perm = torch.from_numpy(g.permutation(n_train)).cuda()
+            ep_loss = []
+            for k in range(nb):
+                idx = perm[k * bs:(k + 1) * bs]
+                xb, yb = X[idx].contiguous(), Y[idx].contiguous()
+                lr = lr0 * 0.5 * (1.0 + np.cos(np.pi * it / total))
+                want = k == nb - 1 or k % 16 == 0
+                l = B.mm_fno_train_step(net.f, xb, yb, bs, lr, want_loss=want)
+                if want:
+                    ep_loss.append(l)
+                it += 1
+            losses.append(float(np.mean(ep_loss)))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    # held-out films: plain relaxation against the warm start
+    evalf = inputs.relax_films(n_eval, seed=7)
+    m_rand = [torch.from_numpy(inputs.random_unit(f["shape"], f["m_seed"])).cuda() for f in evalf]
+    _, t_plain, steps_plain, tq_plain, conv_plain = _relax_films(evalf, m_rand, stream, tq_tol, err_tol, max_steps)
+    nev8 = (n_eval + 7) // 8 * 8
+    xe = np.zeros((nev8, 16, 128, 128), dtype=np.float32)
+    xe[:n_eval] = inputs.fno_features(evalf)
+    pred = torch.empty((nev8, 3, 128, 128), dtype=torch.float32, device="cuda")
+    evnet = B.Fno(nev8, stream.cuda_stream)
+    evnet.set_params(net.get_params())
+    xed = torch.from_numpy(xe).cuda()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        B.mm_fno_predict(evnet.f, xed, nev8, pred)
+    torch.cuda.synchronize()
+    t_inf = time.perf_counter() - t2
+    m_warm = [pred[i].reshape(-1).contiguous() for i in range(n_eval)]
+    ms_w, t_warm, steps_warm, tq_warm, conv_warm = _relax_films(evalf, m_warm, stream, tq_tol, err_tol, max_steps)
+    # the prediction's own error: distance to the state the solver then reached
+    err = [float(torch.sqrt(((m_warm[i].view(3, -1) - ms_w[i].view(3, -1)) ** 2).sum(0)).mean()) for i in range(n_eval)]
+    t_warm_total = t_inf + t_warm
+    return {
+        "metric": "time to relax (torque < 1e-4), learned warm start vs plain", "value": t_warm_total, "unit": "s",
+        "higher_is_better": False, "n_gpus": 1,
+        "plain_s": t_plain, "warm_inference_s": t_inf, "warm_relax_s": t_warm,
+        "speedup": t_plain / t_warm_total,
+        "films": n_eval, "converged_plain": conv_plain, "converged_warm": conv_warm,
+        "steps_median_plain": float(np.median(steps_plain)), "steps_median_warm": float(np.median(steps_warm)),
+        "torque_max_plain": float(max(tq_plain)), "torque_max_warm": float(max(tq_warm)),
+        "prediction_mean_dm": float(np.mean(err)),
+        "training": {"films": n_train, "generation_s": t_gen, "generation_steps_median": float(np.median(gen_steps)),
+                     "epochs": epochs, "batch": bs, "train_s": t_train, "loss_first_epoch": losses[0],
+                     "loss_last_epoch": losses[-1], "optimizer": "Adam lr 1e-3 cosine to 0, betas (0.9, 0.999)"},
+        "dtype": "bf16 operands, fp32 accumulation (operator); f32 solver",
+        "data": "synthetic (seeded material, field, easy axis; training targets relaxed by the solver from random m)",
+        "config": {"workload": f"warmstart_films_128x128_train{n_train}_eval{n_eval}", "grid": [128, 128, 1],
+                   "cell_nm": [4, 4, 3], "alpha": 1.0, "method": "RKDP adaptive, tol 1e-6 per step",
+                   "torque_tol": tq_tol,
+                   "timing": "wall clock around mm_batch_relax of the held-out films (all at once) from random m "
+                             "and from the prediction; the prediction's inference time is added to the latter"},
+    }
+
+
 def run_cufft_comparison(args):
     """The demag convolution of the 1024 x 1024 film through cuFFT (torch.fft:
     zero-padded 2048 x 2048 R2C of the three components, the 3x3 real kernel
@@ -682,6 +806,11 @@ def main():
     ap.add_argument("--relax", type=int, default=0,
                     help="time to relax this many 128 x 128 films from random states (batched and one by one)")
     ap.add_argument("--relax-max-steps", type=int, default=100000)
+    ap.add_argument("--warmstart", type=int, default=0,
+                    help="learned warm start: relax this many training films, train the operator, compare "
+                         "relaxation times on held-out films")
+    ap.add_argument("--warmstart-eval", type=int, default=64)
+    ap.add_argument("--warmstart-epochs", type=int, default=60)
     ap.add_argument("--cufft", action="store_true",
                     help="time the film's demag convolution through cuFFT next to the hand-written passes")
     args = ap.parse_args()
@@ -706,6 +835,9 @@ def main():
         return
     if args.relax > 0:
         print(json.dumps(run_relax(args)))
+        return
+    if args.warmstart > 0:
+        print(json.dumps(run_warmstart(args)))
         return
     if args.cufft:
         print(json.dumps(run_cufft_comparison(args)))

@@ -92,6 +92,21 @@ _SIGS = {
     "mm_batch_tuning": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "mm_batch_last_error": (ctypes.c_char_p, [_vp]),
     "mm_batch_destroy": (None, [_vp]),
+    "mm_fno_create": (_i, [ctypes.POINTER(_vp), _i, _vp]),
+    "mm_fno_workspace_bytes": (_sz, [_vp]),
+    "mm_fno_set_workspace": (_i, [_vp, _vp, _sz]),
+    "mm_fno_param_count": (_sz, []),
+    "mm_fno_set_params": (_i, [_vp, _vp]),
+    "mm_fno_get_params": (_i, [_vp, _vp]),
+    "mm_fno_train_step": (_i, [_vp, _vp, _vp, _i, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                               _dp, _vp]),
+    "mm_fno_predict": (_i, [_vp, _vp, _i, _vp, _vp]),
+    "mm_fno_status": (_i, [_vp]),
+    "mm_fno_last_error": (ctypes.c_char_p, [_vp]),
+    "mm_fno_destroy": (None, [_vp]),
+    "mm_gemm_bf16": (_i, [_vp, ctypes.c_longlong, ctypes.c_longlong, _vp, ctypes.c_longlong, ctypes.c_longlong, _vp,
+                          ctypes.c_longlong, ctypes.c_longlong, _i, _i, _i, _i, ctypes.c_float, _i, _vp]),
+    "mm_gemm_status": (_i, [_vp]),
 }
 
 
@@ -469,6 +484,153 @@ class Solver:
         if self.ctx is not None:
             mm_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- learned warm start (include/mm_fno.h) ----------------------------------
+
+def _fcheck(f, rc):
+    if rc != MM_OK:
+        msg = lib().mm_fno_last_error(f)
+        raise MMError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def mm_fno_create(max_batch, stream=None):
+    f = _vp()
+    rc = lib().mm_fno_create(ctypes.byref(f), int(max_batch), stream)
+    if rc != MM_OK:
+        raise MMError(rc, "mm_fno_create")
+    return f
+
+
+def mm_fno_workspace_bytes(f):
+    return int(lib().mm_fno_workspace_bytes(f))
+
+
+def mm_fno_set_workspace(f, ptr, nbytes):
+    return _fcheck(f, lib().mm_fno_set_workspace(f, _ptr(ptr), int(nbytes)))
+
+
+def mm_fno_param_count():
+    return int(lib().mm_fno_param_count())
+
+
+def mm_fno_set_params(f, params):
+    return _fcheck(f, lib().mm_fno_set_params(f, _ptr(params)))
+
+
+def mm_fno_get_params(f, params):
+    return _fcheck(f, lib().mm_fno_get_params(f, _ptr(params)))
+
+
+def mm_fno_train_step(f, x, target, batch, lr, beta1=0.9, beta2=0.999, eps=1e-8, want_loss=True, grad_out=None):
+    loss = ctypes.c_double(0.0)
+    _fcheck(f, lib().mm_fno_train_step(f, _ptr(x), _ptr(target), int(batch), float(lr), float(beta1), float(beta2),
+                                       float(eps), ctypes.byref(loss) if want_loss else None, _ptr(grad_out)))
+    return loss.value if want_loss else None
+
+
+def mm_fno_predict(f, x, batch, m_out=None, raw_out=None):
+    return _fcheck(f, lib().mm_fno_predict(f, _ptr(x), int(batch), _ptr(m_out), _ptr(raw_out)))
+
+
+def mm_fno_status(f):
+    return lib().mm_fno_status(f)
+
+
+def mm_fno_last_error(f):
+    msg = lib().mm_fno_last_error(f)
+    return msg.decode() if msg else ""
+
+
+def mm_fno_destroy(f):
+    lib().mm_fno_destroy(f)
+
+
+def mm_gemm_bf16(a, lda, a_batch, b, ldb, b_batch, c, ldc, c_batch, m, n, k, batch=1, alpha=1.0, beta=0, stream=None):
+    rc = lib().mm_gemm_bf16(_ptr(a), int(lda), int(a_batch), _ptr(b), int(ldb), int(b_batch), _ptr(c), int(ldc),
+                            int(c_batch), int(m), int(n), int(k), int(batch), float(alpha), int(beta), stream)
+    if rc != MM_OK:
+        raise MMError(rc, "mm_gemm_bf16: bad sizes, strides or alignment")
+    return rc
+
+
+def mm_gemm_status(stream=None):
+    return lib().mm_gemm_status(stream)
+
+
+# Flat parameter vector of include/mm_fno.h <-> the dict form of the seeded
+# initialisation (inputs.fno_init): marshalling only.
+FNO_SHAPES = [("lift_w", (32, 16)), ("lift_b", (32,)), ("spec_w", (4, 2, 512, 32, 32)), ("pw_w", (4, 32, 32)),
+              ("pw_b", (4, 32)), ("proj1_w", (128, 32)), ("proj1_b", (128,)), ("proj2_w", (3, 128)),
+              ("proj2_b", (3,))]
+
+
+def fno_pack(p):
+    """dict (numpy float64, spec_w a list of 4 complex [512][32][32]) -> flat float32 numpy array."""
+    parts = []
+    for name, shape in FNO_SHAPES:
+        v = p[name]
+        if name == "spec_w":
+            v = np.stack([np.stack([np.real(w), np.imag(w)]) for w in v])
+        elif isinstance(v, list):
+            v = np.stack(v)
+        parts.append(np.asarray(v, dtype=np.float32).reshape(-1))
+    return np.concatenate(parts)
+
+
+def fno_unpack(flat):
+    flat = np.asarray(flat, dtype=np.float64)
+    out, off = {}, 0
+    for name, shape in FNO_SHAPES:
+        n = int(np.prod(shape))
+        v = flat[off:off + n].reshape(shape)
+        off += n
+        if name == "spec_w":
+            v = [v[l, 0] + 1j * v[l, 1] for l in range(4)]
+        elif name in ("pw_w", "pw_b"):
+            v = [v[l] for l in range(4)]
+        out[name] = v
+    return out
+
+
+class Fno:
+    """The warm-start operator on the current CUDA device; workspace from torch."""
+
+    def __init__(self, max_batch, stream=None):
+        import torch
+        self.torch = torch
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = stream
+        self.f = mm_fno_create(max_batch, stream)
+        nbytes = mm_fno_workspace_bytes(self.f)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        base = self.workspace.data_ptr()
+        mm_fno_set_workspace(self.f, (base + 255) // 256 * 256, nbytes)
+        self.nparam = mm_fno_param_count()
+
+    def set_params(self, p):
+        flat = p if isinstance(p, np.ndarray) else fno_pack(p)
+        t = self.torch.from_numpy(np.ascontiguousarray(flat, dtype=np.float32)).cuda()
+        mm_fno_set_params(self.f, t)
+        self.torch.cuda.synchronize()
+
+    def get_params(self):
+        t = self.torch.empty(self.nparam, dtype=self.torch.float32, device="cuda")
+        mm_fno_get_params(self.f, t)
+        return t.cpu().numpy()
+
+    def close(self):
+        if getattr(self, "f", None) is not None:
+            mm_fno_destroy(self.f)
+            self.f = None
 
     def __del__(self):
         try:

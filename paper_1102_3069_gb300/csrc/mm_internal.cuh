@@ -185,3 +185,12 @@ struct SetupParams {
 cudaError_t launch_kernel_setup(const SetupParams& p, cudaStream_t s);
 
 }  // namespace mm
+
+namespace mm {
+// tensor-core product (tc_gemm.cu): C[b] = alpha * A[b] B[b]^T (+ C[b] when beta),
+// A [m][k], B [n][k] bf16 row-major (k contiguous), C [m][n] fp32 row-major;
+// strides in elements.  *err gets a non-zero bit when a bounded wait ran out.
+cudaError_t gemm_bf16(const void* a, long long lda, long long a_batch, const void* b, long long ldb,
+                      long long b_batch, float* c, long long ldc, long long c_batch, int m, int n, int k, int batch,
+                      float alpha, int beta, unsigned* err, cudaStream_t s);
+}  // namespace mm
