@@ -237,8 +237,10 @@ def run_gpu(args):
     else:
         method, first_dt, dt_step, tol = B.MM_HEUN, spec["dt"], spec["dt"], 0.0
     stream = torch.cuda.Stream()
+    dft = B.MM_DFT_SPLIT_BF16 if args.dft == "split-bf16" else None
     with torch.cuda.stream(stream):
-        s = B.Solver(w["shape"], w["cell"], pbc=w["pbc"], stream=stream.cuda_stream, **w["material"])
+        s = B.Solver(w["shape"], w["cell"], pbc=w["pbc"], stream=stream.cuda_stream, dft_precision=dft,
+                     **w["material"])
         axes = None
         if w.get("axes") is not None:             # per-cell easy axes (the cube's polycrystal)
             axes = torch.from_numpy(w["axes"]).cuda()
@@ -254,21 +256,27 @@ def run_gpu(args):
         if ws > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
+        # the timed window of `steps` steps is repeated until the clock sampler
+        # has seen at least min_timed_s of load; the median window is reported
+        windows = []                                  # (ms of the window, evals, simulated time)
         with ClockSampler(dev) as clk:
             t_wall0 = time.perf_counter()
-            for k in range(args.steps):
-                flush.fill_(k & 0xFF)                     # evict the previous step from L2
-                ev[k][0].record(stream)
-                B.mm_advance(ctx, method, 1, dt_s=dt_step, tol=tol)
-                ev[k][1].record(stream)
-            torch.cuda.synchronize()
+            while True:
+                sa = B.mm_get_stats(ctx)
+                for k in range(args.steps):
+                    flush.fill_(k & 0xFF)                 # evict the previous step from L2
+                    ev[k][0].record(stream)
+                    B.mm_advance(ctx, method, 1, dt_s=dt_step, tol=tol)
+                    ev[k][1].record(stream)
+                torch.cuda.synchronize()
+                sb = B.mm_get_stats(ctx)
+                windows.append((sum(a.elapsed_time(b) for a, b in ev), sb["evals"] - sa["evals"], sb["t"] - sa["t"]))
+                if time.perf_counter() - t_wall0 >= args.min_timed_s or len(windows) >= 1000:
+                    break
             t_wall = time.perf_counter() - t_wall0
         st1 = B.mm_get_stats(ctx)
-        step_ms = [a.elapsed_time(b) for a, b in ev]
-        gpu_ms = sum(step_ms)
-        evals = st1["evals"] - st0["evals"]
-        sim_t = st1["t"] - st0["t"]
         assert st1["status"] == 0, st1
+        gpu_ms, evals, sim_t = sorted(windows)[len(windows) // 2]
 
         # per-pass durations over a second timed region of the same steps
         passes = B.pass_times(ctx, lambda: B.mm_advance(ctx, method, min(args.steps, 200), dt_s=dt_step, tol=tol))
@@ -309,7 +317,9 @@ def run_gpu(args):
         "config": {"workload": wname, "grid": [nx, ny, nz], "cell_nm": [round(c * 1e9, 3) for c in w["cell"]],
                    "pbc": list(w["pbc"]), "method": spec["desc"], "evals_per_step": spec["evals"],
                    "l2": "flushed between timed steps (256 MB write, outside the events)",
-                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+                   "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "timing": "median of repeated windows of `steps` steps (CUDA events on the launching stream)",
+                   "dft": args.dft},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": _traffic_for(dom), "kernel": dom, "peak_source": peak_kind,
                      "bytes_per_launch": ab[dom], "ms_per_launch": dms},
@@ -317,7 +327,8 @@ def run_gpu(args):
                           "frac": step_bytes / (gpu_ms / args.steps * 1e-3) / 1e9 / hbm},
         "passes": passes,
         "ns_simulated_per_hour": sim_t * 1e9 / (gpu_ms * 1e-3 / 3600.0) if gpu_ms > 0 else None,
-        "clocks": clk.summary(),
+        "clocks": dict(clk.summary(), timed_windows=len(windows), timed_wall_s=t_wall,
+                       window_ms_min=min(x[0] for x in windows), window_ms_max=max(x[0] for x in windows)),
         "gpu_launches": int(sum(v["launches"] for v in passes.values()) / max(1, min(args.steps, 200)) * args.steps),
         "e2e": {"value": ev_total * N / te if te > 0 else None, "unit": UNIT,
                 "h2d_bytes_per_step": 12 * N, "d2h_bytes_per_step": 12 * N,
@@ -394,7 +405,8 @@ def run_table1(args):
     from paper_1102_3069_gb300 import inputs
 
     rows = []
-    sizes = [("N2", n) for n in (32, 64, 128, 256, 512, 1024, 2048)] + [("N3", n) for n in (8, 16, 32, 64, 128)]
+    sizes = ([("N2", n) for n in (32, 64, 128, 256, 512, 700, 992, 1024, 2048)] +
+             [("N3", n) for n in (8, 16, 32, 64, 128)])
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
     for kind, n in sizes:
         w = inputs.workload(f"table1_{kind}_{n}")
@@ -422,6 +434,71 @@ def run_table1(args):
     return {"metric": "Euler step time (Table 1 grids)", "unit": "ms", "rows": rows,
             "config": {"material": "Ms 8e5 A/m, A 1.3e-11 J/m, Ku 5e3 J/m^3 along x, Bz 10 mT, alpha 0.01",
                        "cell_nm": 4, "timing": "median of 50 steps, CUDA events, L2 flushed between steps"}}
+
+
+def _host_cpu():
+    """Core count and CPU model of this host (for the CPU baselines)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() in ("Model name", "Model"):
+                model = ln.split(":", 1)[1].strip()
+                if ln.split(":")[0].strip() == "Model name":
+                    break
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "model": model}
+
+
+def _oracle_euler_worker(args):
+    """One process: oracle Euler steps of a table-1 grid for `seconds` (kernel build untimed)."""
+    name, seconds = args
+    import numpy as np
+
+    from oracle import llg
+    from paper_1102_3069_gb300 import inputs
+    w = inputs.workload(name)
+    mat = w["material"]
+    p = llg.Problem(w["shape"], w["cell"], mat["Ms"], mat["Aex"], mat["alpha"], Ku=mat["Ku"], u=mat["easy_axis"],
+                    B=mat["B"])
+    m = w["m"].astype(np.float64)
+    t0 = time.perf_counter()
+    k = 0
+    while time.perf_counter() - t0 < seconds or k < 2:
+        m = llg.euler_step(p, m, 1e-14)
+        k += 1
+    return k, time.perf_counter() - t0, int(np.prod(w["shape"]))
+
+
+def run_cpu_sweep(args):
+    """The FP64 oracle timed on this host: Euler steps of the Table-1 grids on one
+    thread (the paper's CPU column is one core), and the throughput of all host
+    cores running independent oracle processes on the 256^2 grid."""
+    import multiprocessing as mp
+    rows = []
+    grids = [("N2", n) for n in (32, 64, 128, 256, 512)] + [("N3", n) for n in (8, 16, 32)]
+    for kind, n in grids:
+        k, t, cells = _oracle_euler_worker((f"table1_{kind}_{n}", 2.0))
+        rows.append({"grid": f"{n}^{2 if kind == 'N2' else 3}", "cells": cells, "ms_per_euler_step": t / k * 1e3,
+                     "steps": k})
+    host = _host_cpu()
+    ncore = host["nproc"] or 1
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(ncore) as pool:
+        res = pool.map(_oracle_euler_worker, [("table1_N2_256", 10.0)] * ncore)
+    wall = time.perf_counter() - t0
+    evals = sum(k * c for k, _, c in res)
+    per = [k * c / t for k, t, c in res]
+    return {"metric": "oracle Euler step time (Table 1 grids), one thread", "unit": "ms", "rows": rows,
+            "all_cores": {"grid": "256^2", "processes": ncore, "cell_evals_per_s": sum(per),
+                          "cell_evals_per_s_one_process": per[0], "wall_s_including_kernel_builds": wall,
+                          "evals": evals},
+            "host": host,
+            "config": {"oracle": "numpy float64 (FFT convolution, one thread per process)",
+                       "timing": "wall clock per Euler step after the kernel build; all cores: one spawn process "
+                                 "per core, each 10 s of steps"}}
 
 
 def run_ensemble(args):
@@ -695,6 +772,76 @@ def run_warmstart(args):
     }
 
 
+def run_relax_ensemble(args):
+    """Time to relax an ensemble of independent samples of uneven sizes (grids
+    32..256 x 32..256 x 1..4 of 4 nm cells, random material, easy axis and
+    field) from random unit vectors to max |m x H|/Ms < 1e-4, all samples in
+    one batch (mm_batch_relax: per-sample step control, finished samples leave
+    the batched launches)."""
+    import numpy as np
+    import torch
+
+    from paper_1102_3069_gb300 import binding as B
+    from paper_1102_3069_gb300 import inputs
+
+    samples = inputs.ensemble(args.relax_ensemble, alpha=args.relax_alpha)
+    tq_tol, err_tol, max_steps = 1e-4, 1e-6, args.relax_max_steps
+    stream = torch.cuda.Stream()
+    m0 = [torch.from_numpy(inputs.random_unit(x["shape"], x["m_seed"])).cuda() for x in samples]
+    t0 = time.perf_counter()
+    ms, t, steps, tq, conv = _relax_films(samples, m0, stream, tq_tol, err_tol, max_steps)
+    setup_and_relax = time.perf_counter() - t0
+    cells = [int(np.prod(x["shape"])) for x in samples]
+    return {"metric": "time to relax the ensemble (torque < 1e-4)", "value": t, "unit": "s",
+            "higher_is_better": False, "n_gpus": 1, "samples": len(samples), "converged": conv,
+            "cells_total": sum(cells), "steps_median": float(np.median(steps)), "steps_max": int(max(steps)),
+            "torque_max": float(max(tq)), "setup_plus_relax_s": setup_and_relax,
+            "data": "synthetic (seeded per-sample geometry, material, field and random unit m)",
+            "config": {"workload": f"ensemble_{len(samples)}_relax", "alpha": args.relax_alpha,
+                       "grids": "nx, ny U{32..256}, nz U{1..4}, 4 nm cells, open boundaries",
+                       "method": "RKDP adaptive per sample, tol 1e-6 per step", "torque_tol": tq_tol,
+                       "max_steps": max_steps,
+                       "timing": "wall clock around mm_batch_relax (host polls every 64 steps)"}}
+
+
+def run_gemm(args):
+    """The library's tensor-core product (tcgen05) alone: C = A B^T, bf16
+    operands, fp32 accumulation, timed with CUDA events against the measured
+    bf16 tensor peak."""
+    import torch
+
+    from paper_1102_3069_gb300 import binding as B
+    m, n, k = args.gemm
+    g = torch.Generator(device="cuda").manual_seed(0)
+    a = torch.randn((m, k), device="cuda", generator=g).to(torch.bfloat16)
+    b = torch.randn((n, k), device="cuda", generator=g).to(torch.bfloat16)
+    c = torch.empty((m, n), device="cuda", dtype=torch.float32)
+    stream = torch.cuda.current_stream().cuda_stream
+    for _ in range(3):
+        B.mm_gemm_bf16(a, k, 0, b, k, 0, c, n, 0, m, n, k, stream=stream)
+    torch.cuda.synchronize()
+    reps = 20
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        B.mm_gemm_bf16(a, k, 0, b, k, 0, c, n, 0, m, n, k, stream=stream)
+    e1.record()
+    torch.cuda.synchronize()
+    assert B.mm_gemm_status(stream) == B.MM_OK
+    ms = e0.elapsed_time(e1) / reps
+    tflops = 2.0 * m * n * k / (ms * 1e-3) / 1e12
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak, kind = float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        peak, kind = 1900.0, "fallback"
+    err = float((c - a.float() @ b.float().T).abs().max() / (a.float() @ b.float().T).abs().max())
+    return {"metric": "tcgen05 bf16 product throughput", "value": tflops, "unit": "TFLOP/s",
+            "shape": [m, n, k], "ms": ms, "max_rel_err_vs_fp32_product": err,
+            "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+                         "frac": tflops / peak, "peak_source": kind + " (bf16 cuBLAS burst)"}}
+
+
 def run_cufft_comparison(args):
     """The demag convolution of the 1024 x 1024 film through cuFFT (torch.fft:
     zero-padded 2048 x 2048 R2C of the three components, the 3x3 real kernel
@@ -801,16 +948,27 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(METHODS))
     ap.add_argument("--table1", action="store_true",
                     help="Euler-step timing sweep of the paper's Table 1 grids (N^2 and N^3, 4 nm cells)")
+    ap.add_argument("--cpu-sweep", action="store_true",
+                    help="the FP64 oracle's Euler steps on the Table-1 grids (one thread) and on all host cores")
     ap.add_argument("--ensemble", type=int, default=0,
                     help="batched Dormand-Prince steps of an ensemble of this many independent samples")
     ap.add_argument("--relax", type=int, default=0,
                     help="time to relax this many 128 x 128 films from random states (batched and one by one)")
     ap.add_argument("--relax-max-steps", type=int, default=100000)
+    ap.add_argument("--relax-ensemble", type=int, default=0,
+                    help="time to relax this many ensemble samples (uneven grids) together")
+    ap.add_argument("--relax-alpha", type=float, default=0.02)
     ap.add_argument("--warmstart", type=int, default=0,
                     help="learned warm start: relax this many training films, train the operator, compare "
                          "relaxation times on held-out films")
     ap.add_argument("--warmstart-eval", type=int, default=64)
     ap.add_argument("--warmstart-epochs", type=int, default=60)
+    ap.add_argument("--min-timed-s", type=float, default=2.0,
+                    help="repeat the timed window of --steps steps until this much wall time has passed")
+    ap.add_argument("--dft", default="fp32", choices=["fp32", "split-bf16"],
+                    help="precision of the 3-D z transforms (split-bf16: tensor-core DFT products)")
+    ap.add_argument("--gemm", type=int, nargs=3, default=None, metavar=("M", "N", "K"),
+                    help="time the tensor-core bf16 product alone")
     ap.add_argument("--cufft", action="store_true",
                     help="time the film's demag convolution through cuFFT next to the hand-written passes")
     args = ap.parse_args()
@@ -830,11 +988,20 @@ def main():
     if args.table1:
         print(json.dumps(run_table1(args)))
         return
+    if args.cpu_sweep:
+        print(json.dumps(run_cpu_sweep(args)))
+        return
     if args.ensemble > 0:
         print(json.dumps(run_ensemble(args)))
         return
     if args.relax > 0:
         print(json.dumps(run_relax(args)))
+        return
+    if args.gemm:
+        print(json.dumps(run_gemm(args)))
+        return
+    if args.relax_ensemble > 0:
+        print(json.dumps(run_relax_ensemble(args)))
         return
     if args.warmstart > 0:
         print(json.dumps(run_warmstart(args)))

@@ -158,6 +158,25 @@ enum { MM_LAYOUT_AUTO = 0, MM_LAYOUT_FUSED = 1, MM_LAYOUT_SPLIT = 2 };
 int mm_set_pass_layout(mm_ctx* ctx, int layout);
 
 /*
+ * Precision of the z transforms of 3-D grids (Sec. 3.3 computes the whole
+ * convolution in single precision; this is a variant with no counterpart in
+ * the paper).  MM_DFT_FP32 (default): the FP32 column pass.  MM_DFT_SPLIT_BF16:
+ * the z transforms (stages i and iii of Sec. 3.2 along z) run as dense DFT
+ * matrix products on the tensor cores with bf16 operands split as
+ * hi + lo (three products per transform, fp32 accumulation) and the kernel
+ * product in fp32 between them.  Its H_eff error against the FP64 oracle,
+ * measured on a 32^3 periodic crop, is 1.1e-7 relative (the FP32 pass: 6.2e-8);
+ * it is ~17x slower than the FP32 pass on the 256 x 256 x 64 cube and serves
+ * precision studies.
+ * Only single-context evaluations and steps use it (mm_eval_heff_static and
+ * batches keep the FP32 pass).  Call before mm_set_workspace (the variant
+ * needs workspace of its own: mm_workspace_bytes grows); MM_ESTATE after it,
+ * MM_EINVAL for 2-D grids or a padded z length below 4.
+ */
+enum { MM_DFT_FP32 = 0, MM_DFT_SPLIT_BF16 = 1 };
+int mm_set_dft_precision(mm_ctx* ctx, int mode);
+
+/*
  * Spin-transfer torque of Zhang and Li (Sec. 2.1.4, Eq. 7), a torque added to
  * dm/dt (not a field):
  *   dm/dt += -b_j/(1+alpha^2) [ m x (m x (j.grad)m) + (xi - alpha) m x (j.grad)m ],

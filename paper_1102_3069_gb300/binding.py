@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libmm.so")
 MM_OK, MM_EINVAL, MM_ENOMEM, MM_ECUDA = 0, -1, -2, -3
 MM_ENOTCONVERGED, MM_ENONFINITE, MM_ETIMEOUT, MM_ESTATE = -4, -5, -6, -7
 MM_EULER, MM_HEUN, MM_RK3, MM_RK4, MM_RKDP, MM_RKCK, MM_RK12, MM_RK23 = 1, 2, 3, 4, 5, 6, 12, 23
+MM_DFT_FP32, MM_DFT_SPLIT_BF16 = 0, 1
 
 STATUS_NAMES = {0: "MM_OK", -1: "MM_EINVAL", -2: "MM_ENOMEM", -3: "MM_ECUDA", -4: "MM_ENOTCONVERGED",
                 -5: "MM_ENONFINITE", -6: "MM_ETIMEOUT", -7: "MM_ESTATE"}
@@ -59,6 +60,7 @@ _SIGS = {
     "mm_set_anisotropy_axes": (_i, [_vp, _vp]),
     "mm_set_max_dm": (_i, [_vp, _d]),
     "mm_set_pass_layout": (_i, [_vp, _i]),
+    "mm_set_dft_precision": (_i, [_vp, _i]),
     "mm_set_cubic_anisotropy": (_i, [_vp, _d, _d, _dp, _dp]),
     "mm_set_stt": (_i, [_vp, _d, _d, _dp]),
     "mm_demag_kernel": (_i, [_vp, _dp]),
@@ -206,6 +208,10 @@ MM_LAYOUT_AUTO, MM_LAYOUT_FUSED, MM_LAYOUT_SPLIT = 0, 1, 2
 
 def mm_set_pass_layout(ctx, layout):
     return _check(ctx, lib().mm_set_pass_layout(ctx, int(layout)))
+
+
+def mm_set_dft_precision(ctx, mode):
+    return _check(ctx, lib().mm_set_dft_precision(ctx, int(mode)))
 
 
 def mm_set_max_dm(ctx, max_dm):
@@ -446,7 +452,8 @@ class Solver:
     mm_set_material.  ``demag=False`` disables the magnetostatic term.
     """
 
-    def __init__(self, shape, cell, pbc=(0, 0, 0), images=10, demag=True, stream=None, tensor=True, **material):
+    def __init__(self, shape, cell, pbc=(0, 0, 0), images=10, demag=True, stream=None, tensor=True,
+                 dft_precision=None, **material):
         import torch
         self.torch = torch
         self.shape = tuple(int(v) for v in shape)
@@ -455,6 +462,8 @@ class Solver:
             stream = torch.cuda.current_stream().cuda_stream
         self.stream = stream
         self.ctx = mm_init_geometry(*self.shape, *self.cell, pbc, images, stream)
+        if dft_precision is not None:
+            mm_set_dft_precision(self.ctx, dft_precision)
         nbytes = mm_workspace_bytes(self.ctx)
         self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
         base = self.workspace.data_ptr()

@@ -98,6 +98,8 @@ struct mm_ctx {
     bool last_maxdm = false;        // the last run chose its steps by the maximum variation of m
     double max_dm = 0.0;            // mm_set_max_dm (0: fixed dt)
     int layout = MM_LAYOUT_AUTO;    // mm_set_pass_layout
+    int dft_prec = MM_DFT_FP32;     // mm_set_dft_precision
+    size_t off_zs = 0, sz_zs = 0, zs_sizes[7] = {0, 0, 0, 0, 0, 0, 0};
     // what the x spectrum in the workspace currently holds: nothing usable, the
     // transform of m_n (ms[cur]) or of the Dormand-Prince stage-2 input m_2
     enum { SPEC_NONE, SPEC_MCUR, SPEC_M2 } spec = SPEC_NONE;
@@ -155,6 +157,10 @@ void layout(mm_ctx* c) {
     c->off_s1 = off; off += align256(c->sz_s1);
     c->off_s2 = off; off += align256(c->sz_s2);
     c->off_union = off; off += (c->sz_rk > c->sz_setup ? c->sz_rk : c->sz_setup);
+    c->sz_zs = c->dft_prec == MM_DFT_SPLIT_BF16
+                   ? mm::zsplit_bytes(c->nx, c->ny, c->nz, c->hx, c->py, c->pz, c->nzp, c->zs_sizes)
+                   : 0;
+    c->off_zs = off; off += align256(c->sz_zs);
     c->total = off;
 }
 
@@ -233,6 +239,24 @@ mm::HotParams hot_params(mm_ctx* c, double dt_internal, bool thermal) {
     for (int j = 2; j <= 6; ++j) p.kb[j] = rk_array(c, 2 + j);    // 4..8
     p.mstage[0] = rk_array(c, 9); p.mstage[1] = rk_array(c, 10);
     p.hbuf = rk_array(c, 11);
+    if (c->dft_prec == MM_DFT_SPLIT_BF16) {
+        // [A hi | A lo | X | Y hi | Y lo | O | F hi | F lo | G hi | G lo | error word]
+        const size_t* z = c->zs_sizes;
+        char* b = c->ws + c->off_zs;
+        p.zsplit = 1;
+        p.zs_kp = 2 * c->nzp;
+        p.zs_a_hi = b; b += z[0];
+        p.zs_a_lo = b; b += z[0];
+        p.zs_x = reinterpret_cast<float*>(b); b += z[1];
+        p.zs_y_hi = b; b += z[2];
+        p.zs_y_lo = b; b += z[2];
+        p.zs_o = reinterpret_cast<float*>(b); b += z[3];
+        p.zs_f_hi = b; b += z[4];
+        p.zs_f_lo = b; b += z[4];
+        p.zs_g_hi = b; b += z[4];
+        p.zs_g_lo = b; b += z[4];
+        p.zs_err = reinterpret_cast<unsigned*>(b);
+    }
     return p;
 }
 
@@ -479,6 +503,10 @@ int mm_set_workspace(mm_ctx* ctx, void* dev_ptr, size_t bytes) {
     CK(cudaMemcpyAsync(ctx->ws + ctx->off_tw, ctx->tw_host.data(), mmfft::TWN * sizeof(float2),
                        cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemsetAsync(ctx->ws + ctx->off_st, 0, sizeof(mm::DevState), ctx->stream));
+    if (ctx->dft_prec == MM_DFT_SPLIT_BF16) {
+        CK(cudaMemsetAsync(ctx->ws + ctx->off_zs, 0, ctx->sz_zs, ctx->stream));
+        CK(mm::zsplit_tables(hot_params(ctx, 0.0, false), ctx->stream));
+    }
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->kernel_ready = false;
     ctx->state_loaded = false;
@@ -571,6 +599,18 @@ int mm_set_anisotropy_axes(mm_ctx* ctx, const float* u) {
     ctx->uaxis = u;
     ctx->k1_valid = false;
     ctx->param_version++;
+    return MM_OK;
+}
+
+int mm_set_dft_precision(mm_ctx* ctx, int mode) {
+    if (!ctx) return MM_EINVAL;
+    if (mode != MM_DFT_FP32 && mode != MM_DFT_SPLIT_BF16)
+        return fail(ctx, MM_EINVAL, "mode must be MM_DFT_FP32 or MM_DFT_SPLIT_BF16");
+    if (ctx->ws) return fail(ctx, MM_ESTATE, "the DFT precision is chosen before mm_set_workspace");
+    if (mode == MM_DFT_SPLIT_BF16 && (ctx->nz < 2 || ctx->pz < 4))
+        return fail(ctx, MM_EINVAL, "the split-BF16 z pass needs a 3-D grid with a padded z length >= 4");
+    ctx->dft_prec = mode;
+    layout(ctx);
     return MM_OK;
 }
 
@@ -1067,6 +1107,7 @@ int mm_eval_heff_static(mm_ctx* ctx, const float* m, float* h_out, float* torque
     for (int i = 0; i < 2; ++i) { p.ms[i] = nullptr; p.ks[i] = nullptr; p.mstage[i] = nullptr; }
     for (int j = 0; j < 8; ++j) p.kb[j] = nullptr;
     p.hbuf = nullptr;
+    p.zsplit = 0;                 // the FP32 z pass: its buffers stay in the static array
     p.m_eval = m;
     p.h_out = h_out;
     p.tq_out = torque_out;

@@ -428,3 +428,134 @@ __device__ __forceinline__ void run(float2* const* a, float2 (*v)[8], int j, boo
 
 }  // namespace r8
 }  // namespace mmfft
+
+// ---------------------------------------------------------------------------
+// The register passes of namespace r8 with V values per thread (V = 8 or 16):
+// a line of 2^LOGP points takes passes of radix V and one trailing radix
+// REM = 2^(LOGP mod log2 V); a pass of radix R < V gives each thread V/R
+// butterflies.  Radix 16 halves the shared-memory exchanges of a 2048-point
+// line against radix 8 (two instead of three per transform).
+namespace mmfft {
+namespace rv {
+
+template <int V>
+struct Lg { static constexpr int value = V == 16 ? 4 : V == 8 ? 3 : V == 4 ? 2 : 1; };
+
+template <int LOGP, int V>
+struct Plan {
+    static constexpr int LG = Lg<V>::value;
+    static constexpr int P = 1 << LOGP;
+    static constexpr int NF = LOGP >= LG ? LOGP / LG : 0;
+    static constexpr int REM = LOGP >= LG ? (1 << (LOGP % LG)) : P;
+    static constexpr int NPASS = LOGP >= LG ? NF + (REM > 1 ? 1 : 0) : (LOGP > 0 ? 1 : 0);
+    static constexpr int NB = LOGP >= LG ? P / V : 1;
+    static constexpr int LS = padded_len(P);
+    static constexpr int NV = LOGP >= LG ? V : P;
+};
+
+template <int LOGP, int V, bool REV>
+__host__ __device__ constexpr int radix_at(int p) {
+    using PL = Plan<LOGP, V>;
+    if (LOGP < PL::LG) return PL::P;
+    if (PL::REM == 1) return V;
+    if (!REV) return p < PL::NF ? V : PL::REM;
+    return p == 0 ? PL::REM : V;
+}
+template <int LOGP, int V, bool REV>
+__host__ __device__ constexpr int ns_at(int p) {
+    int ns = 1;
+    for (int q = 0; q < p; ++q) ns *= radix_at<LOGP, V, REV>(q);
+    return ns;
+}
+template <int LOGP, int V, bool REV, int PI>
+__device__ __forceinline__ int in_pos(int j, int i) {
+    constexpr int R = radix_at<LOGP, V, REV>(PI);
+    const int b = i / R, r = i - b * R;
+    return j + b * Plan<LOGP, V>::NB + r * (Plan<LOGP, V>::P / R);
+}
+template <int LOGP, int V, bool REV, int PI>
+__device__ __forceinline__ int out_pos(int j, int i) {
+    constexpr int R = radix_at<LOGP, V, REV>(PI), NS = ns_at<LOGP, V, REV>(PI);
+    const int b = i / R, r = i - b * R;
+    const int jj = j + b * Plan<LOGP, V>::NB, k = jj & (NS - 1);
+    return (jj - k) * R + k + r * NS;
+}
+
+// w[r] = tw[t1]^r, r = 1..R-1 (conjugated for INV): loads w, w^2, w^4, w^8, products for the rest
+template <int R, bool INV>
+__device__ __forceinline__ void twiddle_powers(float2* w, const float2* __restrict__ tw, int t1) {
+    if constexpr (R >= 2) w[1] = ldtw<INV>(tw, t1);
+    if constexpr (R >= 4) {
+        w[2] = ldtw<INV>(tw, 2 * t1);
+        w[3] = cmul(w[1], w[2]);
+    }
+    if constexpr (R >= 8) {
+        w[4] = ldtw<INV>(tw, 4 * t1);
+        w[5] = cmul(w[1], w[4]);
+        w[6] = cmul(w[2], w[4]);
+        w[7] = cmul(w[3], w[4]);
+    }
+    if constexpr (R >= 16) {
+        w[8] = ldtw<INV>(tw, 8 * t1);
+#pragma unroll
+        for (int r = 1; r < 8; ++r) w[8 + r] = cmul(w[r], w[8]);
+    }
+}
+
+template <int LOGP, int V, bool REV, bool INV, int PI, int NC>
+__device__ __forceinline__ void compute_nc(float2 (*v)[V], int j, const float2* __restrict__ tw) {
+    constexpr int R = radix_at<LOGP, V, REV>(PI), NS = ns_at<LOGP, V, REV>(PI);
+    constexpr int BPT = LOGP >= Plan<LOGP, V>::LG ? V / R : 1;
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+        if constexpr (NS > 1) {
+            const int jj = j + b * Plan<LOGP, V>::NB, k = jj & (NS - 1);
+            float2 w[R > 1 ? R : 2];
+            twiddle_powers<R, INV>(w, tw, k * (TWN / (NS * R)));
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[c][b * R + r] = cmul(v[c][b * R + r], w[r]);
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) dft<R, INV>(v[c] + b * R);
+    }
+}
+template <int LOGP, int V, bool REV, int PI>
+__device__ __forceinline__ void load(const float2* a, float2* v, int j) {
+#pragma unroll
+    for (int i = 0; i < Plan<LOGP, V>::NV; ++i) v[i] = a[pad(in_pos<LOGP, V, REV, PI>(j, i))];
+}
+template <int LOGP, int V, bool REV, int PI>
+__device__ __forceinline__ void store(float2* a, const float2* v, int j) {
+#pragma unroll
+    for (int i = 0; i < Plan<LOGP, V>::NV; ++i) a[pad(out_pos<LOGP, V, REV, PI>(j, i))] = v[i];
+}
+
+// passes PI..NPASS-1 of NC lines (as r8::run)
+template <int LOGP, int V, bool REV, bool INV, int PI, int NC>
+__device__ __forceinline__ void run(float2* const* a, float2 (*v)[V], int j, bool active,
+                                    const float2* __restrict__ tw, bool from_smem) {
+    using PL = Plan<LOGP, V>;
+    if constexpr (PI < PL::NPASS) {
+        if (from_smem) {
+            if (active) {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) load<LOGP, V, REV, PI>(a[c], v[c], j);
+            }
+        }
+        if (active) compute_nc<LOGP, V, REV, INV, PI, NC>(v, j, tw);
+        if constexpr (PI + 1 < PL::NPASS) {
+            __syncthreads();
+            if (active) {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) store<LOGP, V, REV, PI>(a[c], v[c], j);
+            }
+            __syncthreads();
+            run<LOGP, V, REV, INV, PI + 1, NC>(a, v, j, active, tw, true);
+        }
+    }
+}
+
+}  // namespace rv
+}  // namespace mmfft

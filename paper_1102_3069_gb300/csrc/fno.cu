@@ -672,6 +672,7 @@ int mm_fno_set_workspace(mm_fno* f, void* dev_ptr, size_t bytes) {
     if (bytes < f->total) return fail(f, MM_ENOMEM, "workspace smaller than mm_fno_workspace_bytes()");
     f->ws = static_cast<char*>(dev_ptr);
     layout(f, f->ws);
+    FCK(mm::gemm_configure());
     FCK(cudaMemsetAsync(f->ws, 0, f->total, f->stream));
     k_bases<<<4 * 152, 256, 0, f->stream>>>(f->fb_hi, f->fb_lo, f->ib_hi, f->ib_lo);
     FCK(cudaGetLastError());

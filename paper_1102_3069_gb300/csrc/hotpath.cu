@@ -399,6 +399,73 @@ kb_colconv(const HotParams* __restrict__ ps, const int4* __restrict__ work, Laun
     colconv_body<LOGP, MODE>(s_hp, a, w.y, w.z);
 }
 
+// The 2-D column pass with V = 16 register values per thread (radix 16, 16, 8
+// for 2048 points: two shared-memory exchanges per transform instead of the
+// radix-8 plan's three), one column of three component lines per block.
+namespace rv = mmfft::rv;
+template <int LOGP>
+struct CC16 {
+    using PL = rv::Plan<LOGP, 16>;
+    static constexpr int P = PL::P, NB = PL::NB, LS = PL::LS, NV = PL::NV;
+    static constexpr int NT = NB < 64 ? 64 : NB;
+    static constexpr int LASTF = PL::NPASS > 0 ? PL::NPASS - 1 : 0;
+};
+
+template <int LOGP>
+__global__ void __launch_bounds__(CC16<LOGP>::NT, 3) k_colconv16(HotParams p, LaunchArgs a) {
+    using S = CC16<LOGP>;
+    constexpr int NV = S::NV;
+    extern __shared__ float2 sm[];
+    if (a.mode != LM_EVAL && p.st->done) return;
+    const int j = threadIdx.x;
+    const bool act0 = j < S::NB;
+    const int kx = blockIdx.x;
+    const int HX = p.hx;
+    const bool act = act0 && kx < HX;
+    const long long base = (long long)kx * p.nyp, cstride = (long long)HX * p.nyp;
+    const int nvalid = p.ny;
+    const float2* buf = p.s1;
+    float2* lines[3] = {sm, sm + S::LS, sm + 2 * S::LS};
+    float2 v[3][16];
+    if (act) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int i = 0; i < NV; ++i) {
+                const int pos = rv::in_pos<LOGP, 16, false, 0>(j, i);
+                v[c][i] = pos < nvalid ? buf[base + c * cstride + pos] : make_float2(0.f, 0.f);
+            }
+    }
+    rv::run<LOGP, 16, false, false, 0, 3>(lines, v, j, act, p.tw, false);
+    if (act) {
+        const long long cs = (long long)HX * p.hyk * p.hzk;
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            const int pos = rv::out_pos<LOGP, 16, false, S::LASTF>(j, i);
+            const bool hi = pos > (S::P >> 1);
+            const int kq = hi ? S::P - pos : pos;
+            const float2 X = v[0][i], Y = v[1][i], Z = v[2][i];
+            const long long b = (long long)kx * p.hyk + kq;
+            const float kxx = __ldg(p.kt + b), kyy = __ldg(p.kt + cs + b), kzz = __ldg(p.kt + 2 * cs + b);
+            const float kxy = hi ? -__ldg(p.kt + 3 * cs + b) : __ldg(p.kt + 3 * cs + b);
+            v[0][i] = make_float2(kxx * X.x + kxy * Y.x, kxx * X.y + kxy * Y.y);
+            v[1][i] = make_float2(kxy * X.x + kyy * Y.x, kxy * X.y + kyy * Y.y);
+            v[2][i] = make_float2(kzz * Z.x, kzz * Z.y);
+        }
+    }
+    rv::run<LOGP, 16, true, true, 0, 3>(lines, v, j, act, p.tw, false);
+    if (act) {
+        float2* out = p.s1;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int i = 0; i < NV; ++i) {
+                const int pos = rv::out_pos<LOGP, 16, true, S::LASTF>(j, i);
+                if (pos < nvalid) out[base + c * cstride + pos] = v[c][i];
+            }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // 3-D: y forward pass.  s1 [c][kx][z][y]  ->  s2 [c][kx][ky][z]
 // (P < 64: radix-16 shared-memory lines; P >= 64: yfwd_r_body below)
@@ -1431,6 +1498,7 @@ static cudaError_t set_attr_all() {
     if ((e = cudaFuncSetAttribute(k_xfwd<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_colconv<L, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_colconv<L, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_colconv16<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_yfwd<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_yinv<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_xinv_local<L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
@@ -1478,8 +1546,18 @@ static void launch_x(const HotParams& p, const LaunchArgs& a, int pass, cudaStre
     else k_xinv_local<L, true><<<g, S::NT, sm, s>>>(p, a);
 }
 
+#ifndef MMX_CC16_MIN
+#define MMX_CC16_MIN 99
+#endif
 template <int L>
 static void launch_y(const HotParams& p, const LaunchArgs& a, int pass, cudaStream_t s) {
+    if constexpr (L >= MMX_CC16_MIN && L <= 11) {
+        if (pass == PASS_YCONV) {
+            using S = CC16<L>;
+            k_colconv16<L><<<p.hx, S::NT, (size_t)3 * S::LS * sizeof(float2), s>>>(p, a);
+            return;
+        }
+    }
     if (pass == PASS_YCONV) {
         using S = CC<L>;
         const dim3 g((p.hx + S::COLS - 1) / S::COLS);
@@ -1569,6 +1647,7 @@ cudaError_t launch_pass(const HotParams& p, const LaunchArgs& a, int pass, cudaS
 #undef MM_CALL_Y
             break;
         case PASS_ZCONV:
+            if (p.zsplit) return launch_zconv_split(p, a, s);
 #define MM_CALL_Z(L) launch_z<L>(p, a, s)
             MM_LOGP_SWITCH(p.logpz, MM_CALL_Z)
 #undef MM_CALL_Z

@@ -116,6 +116,20 @@ struct HotParams {
     float* h_out;
     float* tq_out;
     int want_energy;
+    // split-BF16 tensor-core variant of the 3-D z column pass (split_dft.cu)
+    int zsplit;              // 1: the z pass runs as DFT products on the tensor cores
+    int zs_kp;               // 2 * nzp: real width of a z line (re, im interleaved)
+    void* zs_a_hi;           // [3*hx*py][kp] bf16 lines of s2, hi and lo parts
+    void* zs_a_lo;
+    float* zs_x;             // [3*hx*py][2*pz] forward transform (fp32)
+    void* zs_y_hi;           // [3*hx*py][2*pz] bf16 product with the kernel, hi and lo parts
+    void* zs_y_lo;
+    float* zs_o;             // [3*hx*py][kp] inverse transform (fp32)
+    const void* zs_f_hi;     // [2*pz][kp] forward DFT matrix, hi and lo parts
+    const void* zs_f_lo;
+    const void* zs_g_hi;     // [kp][2*pz] inverse DFT matrix, hi and lo parts
+    const void* zs_g_lo;
+    unsigned* zs_err;        // error word of the tensor-core products
 };
 
 struct LaunchArgs {
@@ -164,6 +178,11 @@ cudaError_t launch_gather_states(const HotParams* ps, DevState* out, int n, cuda
 cudaError_t launch_set_run_batch(const HotParams* ps, const int* active, int n_active, double tol,
                                  double torque_tol, double dt0_s, int fixed_h, cudaStream_t s);
 
+// split-BF16 z pass (split_dft.cu): bytes of its buffers, its tables, its launches
+size_t zsplit_bytes(int nx, int ny, int nz, int hx, int py, int pz, int nzp, size_t* sizes /*7*/);
+cudaError_t zsplit_tables(const HotParams& p, cudaStream_t s);
+cudaError_t launch_zconv_split(const HotParams& p, const LaunchArgs& a, cudaStream_t s);
+
 // kernel setup (setup.cu)
 struct SetupParams {
     int nx, ny, nz;
@@ -193,4 +212,5 @@ namespace mm {
 cudaError_t gemm_bf16(const void* a, long long lda, long long a_batch, const void* b, long long ldb,
                       long long b_batch, float* c, long long ldc, long long c_batch, int m, int n, int k, int batch,
                       float alpha, int beta, unsigned* err, cudaStream_t s);
+cudaError_t gemm_configure();   // once per device, before any capture of a product
 }  // namespace mm

@@ -274,8 +274,7 @@ static cudaError_t make_map(CUtensorMap* map, const void* base, int k, int rows,
 }
 
 template <int BN>
-static cudaError_t launch_bn(const CUtensorMap& ma, const CUtensorMap& mb, const GemmArgs& g, int batch,
-                             cudaStream_t s) {
+static cudaError_t configure_bn() {
     static bool configured[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -285,12 +284,32 @@ static cudaError_t launch_bn(const CUtensorMap& ma, const CUtensorMap& mb, const
         if (e != cudaSuccess) return e;
         configured[dev] = true;
     }
+    return cudaSuccess;
+}
+
+template <int BN>
+static cudaError_t launch_bn(const CUtensorMap& ma, const CUtensorMap& mb, const GemmArgs& g, int batch,
+                             cudaStream_t s) {
+    cudaError_t e = configure_bn<BN>();
+    if (e != cudaSuccess) return e;
     const dim3 grid((g.m + BM - 1) / BM, (g.n + BN - 1) / BN, batch);
     k_gemm_bf16<BN><<<grid, NTHREADS, Smem<BN>::TOTAL, s>>>(ma, mb, g);
     return cudaGetLastError();
 }
 
 }  // namespace tc
+
+// kernel attributes and the tensor-map encoder, set up once outside any stream
+// capture (a step graph may contain the products)
+cudaError_t gemm_configure() {
+    using namespace tc;
+    if (!encode_fn()) return cudaErrorNotSupported;
+    cudaError_t e;
+    if ((e = configure_bn<32>())) return e;
+    if ((e = configure_bn<64>())) return e;
+    if ((e = configure_bn<128>())) return e;
+    return configure_bn<256>();
+}
 
 // C[b] = alpha A[b] B[b]^T (+ C[b] when beta); declared in mm_internal.cuh
 cudaError_t gemm_bf16(const void* a, long long lda, long long a_batch, const void* b, long long ldb,
