@@ -834,6 +834,10 @@ struct CellIn {
 
 // Issues every load a cell needs, before any arithmetic, so their latencies
 // overlap.  Which k_j are read is fixed by the tableau (a.need), not by h.
+// LITE: the film's common term set (no z neighbours, one easy axis, no cubic
+// anisotropy, no thermal field, no spin-transfer torque) compiled without the
+// other terms' registers; the host selects it only when that holds.
+template <bool LITE = false>
 __device__ __forceinline__ void load_cell(const HotParams& p, const LaunchArgs& a, int cur,
                                           const float* __restrict__ min, long long cell, int x, int y, int z,
                                           CellIn& in) {
@@ -846,7 +850,7 @@ __device__ __forceinline__ void load_cell(const HotParams& p, const LaunchArgs& 
     if (x > 0) ixm = cell - 1;
     else if (p.pbc[0]) ixm = cell + (p.nx - 1);
     const bool usey = p.ny > 1 || p.pbc[1];
-    const bool usez = p.nz > 1 || p.pbc[2];
+    const bool usez = !LITE && (p.nz > 1 || p.pbc[2]);
     long long iyp = cell, iym = cell, izp = cell, izm = cell;
     if (usey) {
         const long long sy = p.nx;
@@ -868,7 +872,7 @@ __device__ __forceinline__ void load_cell(const HotParams& p, const LaunchArgs& 
     in.myp = in.mym = in.mzp = in.mzm = in.m;
     if (usey) { in.myp = ld3(min, iyp, n); in.mym = ld3(min, iym, n); }
     if (usez) { in.mzp = ld3(min, izp, n); in.mzm = ld3(min, izm, n); }
-    in.u = p.uaxis ? ld3(p.uaxis, cell, n) : mk(p.ux, p.uy, p.uz);
+    in.u = (!LITE && p.uaxis) ? ld3(p.uaxis, cell, n) : mk(p.ux, p.uy, p.uz);
     in.q0 = mk(0.f, 0.f, 0.f);
 #pragma unroll
     for (int j = 0; j < 6; ++j) in.qk[j] = in.q0;
@@ -899,7 +903,7 @@ __device__ __forceinline__ void load_cell(const HotParams& p, const LaunchArgs& 
 // Everything that happens to one cell once its inputs and demag field are
 // known.  Returns the magnetisation the next evaluation of this step reads at
 // this cell (m_{s+1}, m_2, the predictor or m_{n+1}); zero when there is none.
-template <bool EV = true>
+template <bool EV = true, bool LITE = false>
 __device__ __forceinline__ f3 update_cell(const HotParams& p, const LaunchArgs& a, int cur, const StageCoefs& sc,
                                           long long cell, const CellIn& in, f3 hd, long long tstep, Partials& pt) {
     const long long n = p.ncell;
@@ -907,7 +911,7 @@ __device__ __forceinline__ f3 update_cell(const HotParams& p, const LaunchArgs& 
     const f3 q0 = in.q0;
     const f3* qk = in.qk;
     const bool usey = p.ny > 1 || p.pbc[1];
-    const bool usez = p.nz > 1 || p.pbc[2];
+    const bool usez = !LITE && (p.nz > 1 || p.pbc[2]);
     const int s = a.stage;
     const bool fsal = p.rk_fsal != 0;
     // exchange, 6-neighbour (4 in 2-D) Laplacian (Eq. 3)
@@ -917,7 +921,7 @@ __device__ __forceinline__ f3 update_cell(const HotParams& p, const LaunchArgs& 
     const f3 u = in.u;
     f3 han = (p.kan * dot(m, u)) * u;
     float ecub = 0.f;
-    if (p.kc1 != 0.f || p.kc2 != 0.f) {
+    if (!LITE && (p.kc1 != 0.f || p.kc2 != 0.f)) {
         // cubic anisotropy (Eq. 5): h = -sum_i a_i [kc1 (a_j^2 + a_k^2) + kc2 a_j^2 a_k^2] c_i
         const f3 c1 = mk(p.c[0][0], p.c[0][1], p.c[0][2]);
         const f3 c2 = mk(p.c[1][0], p.c[1][1], p.c[1][2]);
@@ -931,10 +935,10 @@ __device__ __forceinline__ f3 update_cell(const HotParams& p, const LaunchArgs& 
     }
     const f3 hz = mk(p.hzx, p.hzy, p.hzz);
     f3 h = hd + hex + han + hz;
-    if (p.sigma_th > 0.f) h = h + p.sigma_th * gauss3(cell, tstep, p.seed);
+    if (!LITE && p.sigma_th > 0.f) h = h + p.sigma_th * gauss3(cell, tstep, p.seed);
     const f3 mxh = cross(m, h);
     f3 k = (-p.llpref) * (mxh + p.alpha * cross(m, mxh));
-    if (p.stt) {
+    if (!LITE && p.stt) {
         // Zhang-Li spin-transfer torque (Eq. 7 / Ms): (j.grad)m from the same
         // neighbours (a missing one is the cell itself), b_j folded into stt_s
         const f3 us = (p.stt_s[0] * (mxp - mxm) + p.stt_s[1] * (myp - mym)) + p.stt_s[2] * (mzp - mzm);
@@ -1036,12 +1040,13 @@ __device__ __forceinline__ f3 update_cell(const HotParams& p, const LaunchArgs& 
     return next;
 }
 
+template <bool LITE = false>
 __device__ __forceinline__ f3 cell_update(const HotParams& p, const LaunchArgs& a, int cur, const StageCoefs& sc,
                                           const float* __restrict__ min, long long cell, int x, int y, int z,
                                           f3 hd, long long tstep, Partials& pt) {
     CellIn in;
-    load_cell(p, a, cur, min, cell, x, y, z, in);
-    return update_cell(p, a, cur, sc, cell, in, hd, tstep, pt);
+    load_cell<LITE>(p, a, cur, min, cell, x, y, z, in);
+    return update_cell<true, LITE>(p, a, cur, sc, cell, in, hd, tstep, pt);
 }
 
 // The stage weights of this pass times h, split into float pairs.  Called by
@@ -1095,7 +1100,7 @@ unsigned stage_need_mask(int rk, int mode, int stage) {
 // then transforms the next evaluation's input for its rows (forward R2C,
 // transposed store), so the next stage needs no separate x-forward pass.
 // The spectrum region a block reads is exactly the region it writes.
-template <int LOGP, bool FUSE>
+template <int LOGP, bool FUSE, bool LITE = false>
 __global__ void __launch_bounds__(XS<LOGP>::NT, XS<LOGP>::MINB) k_xinv_local(HotParams p, LaunchArgs a) {
     using S = XS<LOGP>;
     constexpr int HP = S::TY / 2;                 // row pairs per block
@@ -1155,8 +1160,9 @@ __global__ void __launch_bounds__(XS<LOGP>::NT, XS<LOGP>::MINB) k_xinv_local(Hot
         const float2 h0 = *e0, h1 = *e1, h2 = *e2;
         f3 na = mk(0.f, 0.f, 0.f), nb = mk(0.f, 0.f, 0.f);
         const long long cell = ((long long)z * NY + y) * NX + x;
-        if (y < NY) na = cell_update(p, a, cur, sc, min, cell, x, y, z, mk(h0.x, h1.x, h2.x), s_tstep, pt);
-        if (y + 1 < NY) nb = cell_update(p, a, cur, sc, min, cell + NX, x, y + 1, z, mk(h0.y, h1.y, h2.y), s_tstep, pt);
+        if (y < NY) na = cell_update<LITE>(p, a, cur, sc, min, cell, x, y, z, mk(h0.x, h1.x, h2.x), s_tstep, pt);
+        if (y + 1 < NY)
+            nb = cell_update<LITE>(p, a, cur, sc, min, cell + NX, x, y + 1, z, mk(h0.y, h1.y, h2.y), s_tstep, pt);
         if constexpr (FUSE) {
             *e0 = make_float2(na.x, nb.x);
             *e1 = make_float2(na.y, nb.y);
@@ -1483,6 +1489,15 @@ __global__ void k_copy_out(HotParams p, float* __restrict__ m_user) {
 // column pass of the 1024^2 film); other lengths keep the radix-8 kernel
 constexpr int CC16_MIN_LOGP = 10, CC16_MAX_LOGP = 11;
 
+// the LITE fused x kernels cover padded x lengths of 64 and more (measured on
+// the 1024^2 film: 73.5 against 79.1 us per fused launch, no spills against
+// 64 bytes; with three blocks per SM instead of two, 56 registers and 148
+// bytes of spills, it took 80 us)
+constexpr int LITE_MIN_LOGP = 6;
+static bool lite_terms(const HotParams& p) {
+    return p.nz == 1 && !p.pbc[2] && !p.uaxis && p.kc1 == 0.f && p.kc2 == 0.f && !(p.sigma_th > 0.f) && !p.stt;
+}
+
 // ---------------------------------------------------------------------------
 // launch helpers
 template <int L, int V>
@@ -1509,6 +1524,12 @@ static cudaError_t set_attr_all() {
     if ((e = cudaFuncSetAttribute(k_yinv<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_xinv_local<L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_xinv_local<L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if constexpr (L >= LITE_MIN_LOGP) {
+        if ((e = cudaFuncSetAttribute(k_xinv_local<L, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)))
+            return e;
+        if ((e = cudaFuncSetAttribute(k_xinv_local<L, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)))
+            return e;
+    }
     if constexpr (L >= XREG_MIN_LOGP && L <= XREG_MAX_LOGP) {
         if ((e = cudaFuncSetAttribute(k_xfwd_r<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
         if ((e = cudaFuncSetAttribute(k_xinv_h<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
@@ -1547,8 +1568,15 @@ static void launch_x(const HotParams& p, const LaunchArgs& a, int pass, cudaStre
     using S = XS<L>;
     const dim3 g((p.ny + S::TY - 1) / S::TY, p.nz);
     const size_t sm = (size_t)S::NL * S::LS * sizeof(float2);
-    if (pass == PASS_XFWD) k_xfwd<L><<<g, S::NT, sm, s>>>(p, a);
-    else if (pass == PASS_XINV_LOCAL) k_xinv_local<L, false><<<g, S::NT, sm, s>>>(p, a);
+    if (pass == PASS_XFWD) { k_xfwd<L><<<g, S::NT, sm, s>>>(p, a); return; }
+    if constexpr (L >= LITE_MIN_LOGP) {
+        if (lite_terms(p)) {
+            if (pass == PASS_XINV_LOCAL) k_xinv_local<L, false, true><<<g, S::NT, sm, s>>>(p, a);
+            else k_xinv_local<L, true, true><<<g, S::NT, sm, s>>>(p, a);
+            return;
+        }
+    }
+    if (pass == PASS_XINV_LOCAL) k_xinv_local<L, false><<<g, S::NT, sm, s>>>(p, a);
     else k_xinv_local<L, true><<<g, S::NT, sm, s>>>(p, a);
 }
 
