@@ -39,6 +39,15 @@ bool rk_info(int method, RkInfo* r) {
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 int ilog2(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
 int next_pow2(int v) { int p = 1; while (p < v) p <<= 1; return p; }
+// v = r * 2^l with r = 3, 5 or 7 and compiled x passes for that length
+bool odd_length(int v, int* r_out) {
+    int l = 0;
+    while (v > 1 && (v & 1) == 0) { v >>= 1; ++l; }
+    if (v != 3 && v != 5 && v != 7) return false;
+    if (!mm::odd_x_length_supported(v, l)) return false;
+    *r_out = v;
+    return true;
+}
 
 // Gauss-Legendre nodes/weights on [-1, 1] (Newton iteration on P_n)
 void gauss_legendre(int n, double* t, double* w) {
@@ -71,6 +80,8 @@ struct mm_ctx {
     int pbc[3] = {0, 0, 0};
     int images = 0;
     int px = 1, py = 1, pz = 1, logpx = 0, logpy = 0, logpz = 0;
+    int rx = 1, ry = 1, rz = 1;     // odd factor of each padded length (r * 2^logp)
+    size_t off_twr[8] = {0};        // exp(-2 pi i t / (r TWN)) tables of the odd factors in use
     int hx = 1, hyk = 1, hzk = 1, nyp = 16, nzp = 1, ty = 2, tz = 1, tky = 1, kxb = 1, ncomp = 4;
     int ox = 1, oy = 1, oz = 1;
     long long ncell = 0;
@@ -153,6 +164,13 @@ void layout(mm_ctx* c) {
     size_t off = 0;
     c->off_st = off; off += align256(sizeof(mm::DevState));
     c->off_tw = off; off += align256((size_t)mmfft::TWN * sizeof(float2));
+    for (int r = 3; r <= 7; r += 2) {
+        c->off_twr[r] = 0;
+        if (c->rx == r || c->ry == r || c->rz == r) {
+            c->off_twr[r] = off;
+            off += align256((size_t)r * mmfft::TWN * sizeof(float2));
+        }
+    }
     c->off_kt = off; off += align256(c->sz_kt);
     c->off_s1 = off; off += align256(c->sz_s1);
     c->off_s2 = off; off += align256(c->sz_s2);
@@ -230,6 +248,9 @@ mm::HotParams hot_params(mm_ctx* c, double dt_internal, bool thermal) {
     p.t_scale = (float)(c->gamma0 * Ms);
     p.t_unit = c->gamma0 * Ms;
     p.tw = reinterpret_cast<const float2*>(c->ws + c->off_tw);
+    p.rx = c->rx; p.ry = c->ry; p.rz = c->rz;
+    for (int r = 3; r <= 7; r += 2)
+        if (c->off_twr[r]) p.twr[r] = reinterpret_cast<const float2*>(c->ws + c->off_twr[r]);
     p.kt = reinterpret_cast<const float*>(c->ws + c->off_kt);
     p.s1 = reinterpret_cast<float2*>(c->ws + c->off_s1);
     p.s2 = reinterpret_cast<float2*>(c->ws + c->off_s2);
@@ -428,15 +449,30 @@ int mm_init_geometry(mm_ctx** out, int nx, int ny, int nz, double dx, double dy,
     *out = nullptr;
     const int n[3] = {nx, ny, nz};
     const int pb[3] = {pbc_x != 0, pbc_y != 0, pbc_z != 0};
-    int P[3];
+    int P[3], R[3];
     for (int a = 0; a < 3; ++a) {
         if (n[a] < 1) return MM_EINVAL;
+        R[a] = 1;
         if (pb[a]) {
-            if (!is_pow2(n[a]) || n[a] > 4096) return MM_EINVAL;
-            P[a] = n[a];
+            if (is_pow2(n[a]) && n[a] <= 4096) {
+                P[a] = n[a];
+            } else if (a == 0 && odd_length(n[a], &R[a])) {
+                P[a] = n[a];           // a periodic x axis of r * 2^l cells
+            } else {
+                return MM_EINVAL;
+            }
         } else {
             if (n[a] > 2048) return MM_EINVAL;
             P[a] = next_pow2(2 * n[a] - 1);
+            // x: the smallest r * 2^l >= 2n - 1 with compiled passes (Sec. 3.3's sizes)
+            if (a == 0) {
+                for (int r = 3; r <= 7; r += 2)
+                    for (int l = 0; (r << l) <= 4096; ++l)
+                        if ((r << l) >= 2 * n[a] - 1 && (r << l) < P[a] && mm::odd_x_length_supported(r, l)) {
+                            P[a] = r << l;
+                            R[a] = r;
+                        }
+            }
         }
     }
     if (!(dx > 0 && dy > 0 && dz > 0) || !std::isfinite(dx) || !std::isfinite(dy) || !std::isfinite(dz))
@@ -449,7 +485,8 @@ int mm_init_geometry(mm_ctx** out, int nx, int ny, int nz, double dx, double dy,
     for (int a = 0; a < 3; ++a) c->pbc[a] = pb[a];
     c->images = pbc_images;
     c->px = P[0]; c->py = P[1]; c->pz = P[2];
-    c->logpx = ilog2(P[0]); c->logpy = ilog2(P[1]); c->logpz = ilog2(P[2]);
+    c->rx = R[0]; c->ry = R[1]; c->rz = R[2];
+    c->logpx = ilog2(P[0] / R[0]); c->logpy = ilog2(P[1] / R[1]); c->logpz = ilog2(P[2] / R[2]);
     c->hx = c->px / 2 + 1;
     if (c->px == 1) c->hx = 1;
     c->hyk = c->py / 2 + 1;
@@ -502,6 +539,18 @@ int mm_set_workspace(mm_ctx* ctx, void* dev_ptr, size_t bytes) {
     ctx->ws_size = bytes;
     CK(cudaMemcpyAsync(ctx->ws + ctx->off_tw, ctx->tw_host.data(), mmfft::TWN * sizeof(float2),
                        cudaMemcpyHostToDevice, ctx->stream));
+    std::vector<float2> twr;
+    for (int r = 3; r <= 7; r += 2) {
+        if (!ctx->off_twr[r]) continue;
+        twr.resize((size_t)r * mmfft::TWN);
+        for (int t = 0; t < r * mmfft::TWN; ++t) {
+            const double a = -2.0 * M_PI * (double)t / ((double)r * mmfft::TWN);
+            twr[t] = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
+        CK(cudaMemcpyAsync(ctx->ws + ctx->off_twr[r], twr.data(), twr.size() * sizeof(float2),
+                           cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));      // twr is reused for the next table
+    }
     CK(cudaMemsetAsync(ctx->ws + ctx->off_st, 0, sizeof(mm::DevState), ctx->stream));
     if (ctx->dft_prec == MM_DFT_SPLIT_BF16) {
         CK(cudaMemsetAsync(ctx->ws + ctx->off_zs, 0, ctx->sz_zs, ctx->stream));

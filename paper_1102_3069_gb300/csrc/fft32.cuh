@@ -191,7 +191,158 @@ __device__ __forceinline__ void apply_twiddles(float2* v, const float2* __restri
     }
 }
 
-// Main radix of a line of length 2^LOGP and the number of radix-16 passes.
+// ---- odd radices 3, 5, 7 (line lengths R0 * 2^a, the sizes of Sec. 3.3) ----
+// cos and sin of 2 pi m / R for R = 3, 5, 7 and m = 0..R-1
+__host__ __device__ constexpr float odd_cos(int R, int m) {
+    return R == 3 ? (m == 0 ? 1.f : -0.5f)
+         : R == 5 ? (m == 0 ? 1.f : (m == 1 || m == 4) ? 0.30901699437494742410f : -0.80901699437494742410f)
+         : (m == 0 ? 1.f : (m == 1 || m == 6) ? 0.62348980185873353053f
+                          : (m == 2 || m == 5) ? -0.22252093395631440429f : -0.90096886790241912624f);
+}
+__host__ __device__ constexpr float odd_sin(int R, int m) {
+    return R == 3 ? (m == 0 ? 0.f : m == 1 ? 0.86602540378443864676f : -0.86602540378443864676f)
+         : R == 5 ? (m == 0 ? 0.f : m == 1 ? 0.95105651629515357212f : m == 2 ? 0.58778525229247312917f
+                                  : m == 3 ? -0.58778525229247312917f : -0.95105651629515357212f)
+         : (m == 0 ? 0.f : m == 1 ? 0.78183148246802980871f : m == 2 ? 0.97492791218182360702f
+                          : m == 3 ? 0.43388373911755812048f : m == 4 ? -0.43388373911755812048f
+                          : m == 5 ? -0.97492791218182360702f : -0.78183148246802980871f);
+}
+
+// DFT of odd length R in natural order: X[k] = v0 + sum_{r <= H} (v_r + v_{R-r}) cos(2 pi r k/R)
+// -/+ i sum_{r <= H} (v_r - v_{R-r}) sin(2 pi r k/R), H = (R-1)/2 (sign - forward, + inverse)
+template <int R, bool INV>
+__device__ __forceinline__ void dft_odd(float2* v) {
+    constexpr int H = (R - 1) / 2;
+    float2 sm[H], df[H];
+#pragma unroll
+    for (int r = 1; r <= H; ++r) {
+        sm[r - 1] = cadd(v[r], v[R - r]);
+        df[r - 1] = csub(v[r], v[R - r]);
+    }
+    float2 out[R];
+    out[0] = v[0];
+#pragma unroll
+    for (int r = 0; r < H; ++r) out[0] = cadd(out[0], sm[r]);
+#pragma unroll
+    for (int k = 1; k <= H; ++k) {
+        float2 re = v[0], im = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int r = 1; r <= H; ++r) {
+            const int m = (r * k) % R;
+            const float c = odd_cos(R, m), sn = odd_sin(R, m);
+            re = make_float2(fmaf(c, sm[r - 1].x, re.x), fmaf(c, sm[r - 1].y, re.y));
+            im = make_float2(fmaf(sn, df[r - 1].x, im.x), fmaf(sn, df[r - 1].y, im.y));
+        }
+        // -i*im = (im.y, -im.x), +i*im = (-im.y, im.x)
+        const float2 mi = make_float2(im.y, -im.x), pi = make_float2(-im.y, im.x);
+        out[k] = cadd(re, INV ? pi : mi);
+        out[R - k] = cadd(re, INV ? mi : pi);
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k) v[k] = out[k];
+}
+
+// In-place FFT of NL lines of length P = R0 * 2^LOGP (R0 = 3, 5 or 7,
+// LOGP >= 4) in shared memory at base + l*LS (padded indices): a first Stockham
+// pass of radix R0, then radix-16 passes and a trailing radix 2, 4 or 8, with
+// twiddles from twm[t] = exp(-2 pi i t / (R0 TWN)).  Threads [0, NL*P/16)
+// work (P/16 per line, as for the power-of-two lines); the rest only join the
+// barriers.  Called by every thread after the lines are written.  No scaling.
+template <int LOGP, int R0, int NL, bool INV>
+__device__ __forceinline__ void fft_lines_mixed(float2* base, const float2* __restrict__ twm) {
+    constexpr int Q = 1 << LOGP, P = R0 * Q, NB = P / 16, LS = padded_len(P);
+    constexpr int TWM = R0 * TWN;
+    constexpr int MB = (Q + NB - 1) / NB;          // radix-R0 butterflies per thread (at most)
+    const int tid = threadIdx.x;
+    const bool active = tid < NL * NB;
+    const int line = active ? tid / NB : 0;
+    const int j = active ? tid - line * NB : 0;
+    float2* a = base + line * LS;
+    // pass 0: radix R0, Ns = 1 (no twiddles): inputs b + r Q, outputs b R0 + r
+    {
+        float2 w[MB][R0];
+        if (active) {
+#pragma unroll
+            for (int q = 0; q < MB; ++q) {
+                const int b = j + q * NB;
+                if (b < Q) {
+#pragma unroll
+                    for (int r = 0; r < R0; ++r) w[q][r] = a[pad(b + r * Q)];
+                    dft_odd<R0, INV>(w[q]);
+                }
+            }
+        }
+        __syncthreads();
+        if (active) {
+#pragma unroll
+            for (int q = 0; q < MB; ++q) {
+                const int b = j + q * NB;
+                if (b < Q) {
+#pragma unroll
+                    for (int r = 0; r < R0; ++r) a[pad(b * R0 + r)] = w[q][r];
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // power-of-two passes with Ns = R0 16^p
+    constexpr int N16 = LOGP / 4, REM = 1 << (LOGP % 4);
+    float2 v[16];
+#pragma unroll
+    for (int p = 0; p < N16; ++p) {
+        int Ns = R0;
+        for (int q = 0; q < p; ++q) Ns *= 16;
+        if (active) {
+            const int k = j % Ns;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[r] = a[pad(j + r * NB)];
+            apply_twiddles<16, INV>(v, twm, k * (TWM / (Ns * 16)));
+            dft<16, INV>(v);
+        }
+        __syncthreads();
+        if (active) {
+            const int k = j % Ns;
+            const int o = (j - k) * 16 + k;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) a[pad(o + r * Ns)] = v[r];
+        }
+        __syncthreads();
+    }
+    if constexpr (REM > 1) {
+        constexpr int RR = REM, NBR = P / RR, PER = 16 / RR;
+        int Ns = R0;
+        for (int q = 0; q < N16; ++q) Ns *= 16;
+        if (active) {
+#pragma unroll
+            for (int b = 0; b < PER; ++b) {
+                const int jj = j + b * NB;
+#pragma unroll
+                for (int r = 0; r < RR; ++r) v[b * RR + r] = a[pad(jj + r * NBR)];
+            }
+#pragma unroll
+            for (int b = 0; b < PER; ++b) {
+                const int jj = j + b * NB;
+                const int k = jj % Ns;
+                apply_twiddles<RR, INV>(v + b * RR, twm, k * (TWM / (Ns * RR)));
+                dft<RR, INV>(v + b * RR);
+            }
+        }
+        __syncthreads();
+        if (active) {
+#pragma unroll
+            for (int b = 0; b < PER; ++b) {
+                const int jj = j + b * NB;
+                const int k = jj % Ns;
+                const int o = (jj - k) * RR + k;
+#pragma unroll
+                for (int r = 0; r < RR; ++r) a[pad(o + r * Ns)] = v[b * RR + r];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Main radix of a line of length 2^LOGP and the number of radix-16 passes.// Main radix of a line of length 2^LOGP and the number of radix-16 passes.
 template <int LOGP>
 struct Plan {
     static constexpr int P = 1 << LOGP;

@@ -62,8 +62,9 @@ enum Source : int {
 struct HotParams {
     // geometry
     int nx, ny, nz;
-    int px, py, pz;          // FFT lengths
+    int px, py, pz;          // FFT lengths: r * 2^logp
     int logpx, logpy, logpz;
+    int rx, ry, rz;          // odd factor of each FFT length (1, 3, 5 or 7)
     int hx;                  // px/2 + 1
     int hyk, hzk;            // stored kernel extents along y and z (P/2 + 1)
     int nyp;                 // y extent stored in the x-spectrum (multiple of 16)
@@ -103,6 +104,7 @@ struct HotParams {
     double t_unit;           // gamma0 Ms (1/s) in double: seconds -> internal time
     // buffers
     const float2* tw;
+    const float2* twr[8];    // twr[r]: exp(-2 pi i t / (r TWN)), t < r TWN, for the odd factors r in use
     const float* kt;
     float2* s1;
     float2* s2;
@@ -164,6 +166,10 @@ int eval_passes(const HotParams& p, const LaunchArgs& a, int* ids);     // fills
 cudaError_t launch_pass(const HotParams& p, const LaunchArgs& a, int pass, cudaStream_t s);
 cudaError_t configure_hot_kernels();
 unsigned stage_need_mask(int rk, int mode, int stage);   // host: which k_j a pass reads
+bool odd_x_length_supported(int r, int logp);          // x length r * 2^logp has compiled passes (r = 3, 5, 7)
+// the x passes of those lengths (hotpath_odd.cu)
+cudaError_t launch_x_mixed(const HotParams& p, const LaunchArgs& a, int pass, cudaStream_t s);
+cudaError_t configure_odd_kernels();
 
 // batched passes over independent samples (hotpath.cu)
 bool batch_supported(const HotParams& p);

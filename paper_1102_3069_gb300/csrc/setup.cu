@@ -206,35 +206,62 @@ __global__ void k_wrap(SetupParams p, int comp) {
     }
 }
 
-// FP64 radix-2 Stockham FFT (forward) of one line per block, in shared memory.
-// line q starts at (q % ninner) * sinner + (q / ninner) * souter; elements es apart.
-__global__ void k_fft64_axis(double2* data, int logL, long long es, int ninner, long long sinner, long long souter) {
+// FP64 Stockham FFT (forward) of one line of L = r0 * 2^logL points per block
+// in shared memory: for an odd factor r0 (3, 5, 7) a first pass of radix r0
+// (a direct r0-point DFT, out of place into the second half of the shared
+// buffer and back), then radix-2 passes.  Line q starts at
+// (q % ninner) * sinner + (q / ninner) * souter; elements es apart.
+__global__ void k_fft64_axis(double2* data, int logL, int r0, long long es, int ninner, long long sinner,
+                             long long souter) {
     extern __shared__ double2 sd[];
-    const int L = 1 << logL;
+    const int L = r0 << logL;
     const long long q = blockIdx.x;
     double2* line = data + (q % ninner) * sinner + (q / ninner) * souter;
     for (int i = threadIdx.x; i < L; i += blockDim.x) sd[i] = line[i * es];
     __syncthreads();
+    int ns0 = 1;
+    if (r0 > 1) {
+        // radix r0, Ns = 1: inputs b + r Q, outputs b r0 + k
+        const int Q = L / r0;
+        double2* sd2 = sd + L;
+        for (int b = threadIdx.x; b < Q; b += blockDim.x) {
+            for (int k = 0; k < r0; ++k) {
+                double2 acc = make_double2(0.0, 0.0);
+                for (int r = 0; r < r0; ++r) {
+                    double sn, cs;
+                    sincospi(-2.0 * (double)((r * k) % r0) / (double)r0, &sn, &cs);
+                    const double2 x = sd[b + r * Q];
+                    acc.x += x.x * cs - x.y * sn;
+                    acc.y += x.x * sn + x.y * cs;
+                }
+                sd2[b * r0 + k] = acc;
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < L; i += blockDim.x) sd[i] = sd2[i];
+        __syncthreads();
+        ns0 = r0;
+    }
     const int half = L >> 1;
-    for (int Ns = 1; Ns < L; Ns <<= 1) {
-        double2 r0[8], r1[8];
+    for (int Ns = ns0; Ns < L; Ns <<= 1) {
+        double2 r0v[8], r1v[8];
         int cnt = 0;
         for (int jb = threadIdx.x; jb < half; jb += blockDim.x, ++cnt) {
-            const int k = jb & (Ns - 1);
+            const int k = jb % Ns;
             const double2 a0 = sd[jb], a1 = sd[jb + half];
             double s, c;
             sincospi(-(double)k / (double)Ns, &s, &c);
             const double2 b = make_double2(a1.x * c - a1.y * s, a1.x * s + a1.y * c);
-            r0[cnt] = make_double2(a0.x + b.x, a0.y + b.y);
-            r1[cnt] = make_double2(a0.x - b.x, a0.y - b.y);
+            r0v[cnt] = make_double2(a0.x + b.x, a0.y + b.y);
+            r1v[cnt] = make_double2(a0.x - b.x, a0.y - b.y);
         }
         __syncthreads();
         cnt = 0;
         for (int jb = threadIdx.x; jb < half; jb += blockDim.x, ++cnt) {
-            const int k = jb & (Ns - 1);
+            const int k = jb % Ns;
             const int o = (jb - k) * 2 + k;
-            sd[o] = r0[cnt];
-            sd[o + Ns] = r1[cnt];
+            sd[o] = r0v[cnt];
+            sd[o + Ns] = r1v[cnt];
         }
         __syncthreads();
     }
@@ -267,11 +294,19 @@ cudaError_t launch_kernel_setup(const SetupParams& p, cudaStream_t s) {
     if (e) return e;
     const long long ptot = (long long)p.px * p.py * p.pz;
     const double scale = -1.0 / (double)ptot;
-    int lx = 0, ly = 0, lz = 0;
-    while ((1 << lx) < p.px) ++lx;
-    while ((1 << ly) < p.py) ++ly;
-    while ((1 << lz) < p.pz) ++lz;
-    const size_t sm_max = 4096 * sizeof(double2);
+    // each length is r * 2^l with an odd factor r (1, 3, 5 or 7)
+    auto split = [](int n, int& l, int& r) {
+        l = 0;
+        while (((n >> l) & 1) == 0 && (1 << l) < n) ++l;
+        r = n >> l;
+    };
+    int lx, ly, lz, rx, ry, rz;
+    split(p.px, lx, rx);
+    split(p.py, ly, ry);
+    split(p.pz, lz, rz);
+    // the odd-radix pass works out of place: twice the line in shared memory
+    auto smem = [](int n, int r) { return (size_t)(r > 1 ? 2 : 1) * n * sizeof(double2); };
+    const size_t sm_max = 2 * 4096 * sizeof(double2);
     if ((e = cudaFuncSetAttribute(k_fft64_axis, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_max))) return e;
     for (int comp = 0; comp < p.ncomp; ++comp) {
         int wb = (int)((ptot + 255) / 256);
@@ -280,15 +315,15 @@ cudaError_t launch_kernel_setup(const SetupParams& p, cudaStream_t s) {
         // x lines: contiguous, one per (y, z)
         if (p.px > 1)
             k_fft64_axis<<<p.py * p.pz, p.px / 2 < 512 ? (p.px / 2 < 32 ? 32 : p.px / 2) : 512,
-                           p.px * sizeof(double2), s>>>(p.work, lx, 1, 1, p.px, p.px);
+                           smem(p.px, rx), s>>>(p.work, lx, rx, 1, 1, p.px, p.px);
         // y lines: stride px, one per (x, z)
         if (p.py > 1)
             k_fft64_axis<<<p.px * p.pz, p.py / 2 < 512 ? (p.py / 2 < 32 ? 32 : p.py / 2) : 512,
-                           p.py * sizeof(double2), s>>>(p.work, ly, p.px, p.px, 1, (long long)p.px * p.py);
+                           smem(p.py, ry), s>>>(p.work, ly, ry, p.px, p.px, 1, (long long)p.px * p.py);
         // z lines: stride px*py, one per (x, y)
         if (p.pz > 1)
             k_fft64_axis<<<p.px * p.py, p.pz / 2 < 512 ? (p.pz / 2 < 32 ? 32 : p.pz / 2) : 512,
-                           p.pz * sizeof(double2), s>>>(p.work, lz, (long long)p.px * p.py, p.px * p.py, 1, 0);
+                           smem(p.pz, rz), s>>>(p.work, lz, rz, (long long)p.px * p.py, p.px * p.py, 1, 0);
         int sb = (int)(((long long)p.hx * p.hyk * p.hzk + 255) / 256);
         if (sb > 152 * 32) sb = 152 * 32;
         k_store_octant<<<sb, 256, 0, s>>>(p, comp, scale);
