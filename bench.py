@@ -405,7 +405,7 @@ def run_table1(args):
     from paper_1102_3069_gb300 import inputs
 
     rows = []
-    sizes = ([("N2", n) for n in (32, 64, 128, 256, 512, 700, 992, 1024, 2048)] +
+    sizes = ([("N2", n) for n in (32, 64, 128, 256, 512, 600, 700, 992, 1024, 2048)] +
              [("N3", n) for n in (8, 16, 32, 64, 128)])
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
     for kind, n in sizes:

@@ -79,12 +79,12 @@ typedef struct mm_stats {
  * conditions: periodic images added to the kernel, no zero padding);
  * pbc_images = number of images on each side of a periodic axis (>= 0).
  * Open axes are zero padded to the smallest FFT length >= 2n-1 of the
- * form 2^k, and for x also r * 2^l with r = 3, 5, 7 (Sec. 3.3: sizes
- * 2^n {1,3,5,7}; compiled for 3 * 2^6 .. 3 * 2^10, 5 * 2^6 .. 5 * 2^9 and
- * 7 * 2^6 .. 7 * 2^9).  A periodic axis needs n to be one of those lengths
- * (y and z: a power of two).  nx, ny, nz in [1, 2048] for open axes (padded
- * length <= 4096) and [1, 4096] for periodic ones.  Grids with an odd factor
- * in x run single contexts only (mm_batch_create refuses them).
+ * form 2^k or r * 2^l with r = 3, 5, 7 (Sec. 3.3: sizes 2^n {1,3,5,7};
+ * the odd factors are compiled for 3 * 2^6 .. 3 * 2^10, 5 * 2^6 .. 5 * 2^9
+ * and 7 * 2^6 .. 7 * 2^9).  A periodic axis needs n to be one of those
+ * lengths.  nx, ny, nz in [1, 2048] for open axes (padded length <= 4096)
+ * and [1, 4096] for periodic ones.  Grids with an odd factor in any padded
+ * length run single contexts only (mm_batch_create refuses them).
  * cuda_stream: a cudaStream_t (NULL = legacy default stream).
  * On success *out owns host memory only; free it with mm_destroy.
  */

@@ -39,12 +39,16 @@ bool rk_info(int method, RkInfo* r) {
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 int ilog2(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
 int next_pow2(int v) { int p = 1; while (p < v) p <<= 1; return p; }
-// v = r * 2^l with r = 3, 5 or 7 and compiled x passes for that length
-bool odd_length(int v, int* r_out) {
+// compiled passes for the length r * 2^l along axis a
+bool odd_supported(int axis, int r, int l) {
+    return axis == 0 ? mm::odd_x_length_supported(r, l) : mm::odd_yz_length_supported(r, l);
+}
+// v = r * 2^l with r = 3, 5 or 7 and compiled passes for that length along axis a
+bool odd_length(int v, int axis, int* r_out) {
     int l = 0;
     while (v > 1 && (v & 1) == 0) { v >>= 1; ++l; }
     if (v != 3 && v != 5 && v != 7) return false;
-    if (!mm::odd_x_length_supported(v, l)) return false;
+    if (!odd_supported(axis, v, l)) return false;
     *r_out = v;
     return true;
 }
@@ -456,23 +460,21 @@ int mm_init_geometry(mm_ctx** out, int nx, int ny, int nz, double dx, double dy,
         if (pb[a]) {
             if (is_pow2(n[a]) && n[a] <= 4096) {
                 P[a] = n[a];
-            } else if (a == 0 && odd_length(n[a], &R[a])) {
-                P[a] = n[a];           // a periodic x axis of r * 2^l cells
+            } else if (odd_length(n[a], a, &R[a])) {
+                P[a] = n[a];           // a periodic axis of r * 2^l cells
             } else {
                 return MM_EINVAL;
             }
         } else {
             if (n[a] > 2048) return MM_EINVAL;
             P[a] = next_pow2(2 * n[a] - 1);
-            // x: the smallest r * 2^l >= 2n - 1 with compiled passes (Sec. 3.3's sizes)
-            if (a == 0) {
-                for (int r = 3; r <= 7; r += 2)
-                    for (int l = 0; (r << l) <= 4096; ++l)
-                        if ((r << l) >= 2 * n[a] - 1 && (r << l) < P[a] && mm::odd_x_length_supported(r, l)) {
-                            P[a] = r << l;
-                            R[a] = r;
-                        }
-            }
+            // the smallest r * 2^l >= 2n - 1 with compiled passes (Sec. 3.3's sizes)
+            for (int r = 3; r <= 7; r += 2)
+                for (int l = 0; (r << l) <= 4096; ++l)
+                    if ((r << l) >= 2 * n[a] - 1 && (r << l) < P[a] && odd_supported(a, r, l)) {
+                        P[a] = r << l;
+                        R[a] = r;
+                    }
         }
     }
     if (!(dx > 0 && dy > 0 && dz > 0) || !std::isfinite(dx) || !std::isfinite(dy) || !std::isfinite(dz))
@@ -501,7 +503,7 @@ int mm_init_geometry(mm_ctx** out, int nx, int ny, int nz, double dx, double dy,
     c->ty = mmfft::ty_of(c->logpx);
     c->nyp = (ny + 15) / 16 * 16;                  // a multiple of every x-pass tile
     c->kxb = 1;                                    // column passes size their own blocks
-    c->tz = mmfft::tz_of(c->logpy);
+    c->tz = c->ry > 1 ? mmfft::tz_of_len(c->py) : mmfft::tz_of(c->logpy);
     c->nzp = (nz + c->tz - 1) / c->tz * c->tz;     // the 3-D y passes write whole z tiles
     c->tky = 1;
     c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);

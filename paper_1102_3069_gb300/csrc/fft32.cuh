@@ -44,6 +44,16 @@ __host__ __device__ constexpr int cols_of(int logp, int cap) {
          : (3 * 2 * nb_of(logp) <= 512 && cap >= 2) ? 2 : 1;
 }
 __host__ __device__ constexpr int tz_of(int logp) { return cols_of(logp, 8); }     // 3-D y passes
+// the same tile rules for lines of any length P = r * 2^a (P/16 threads per line)
+__host__ __device__ constexpr int cols_of_len(int P, int cap) {
+    return (3 * 64 * (P / 16) <= 512 && cap >= 64) ? 64
+         : (3 * 32 * (P / 16) <= 512 && cap >= 32) ? 32
+         : (3 * 16 * (P / 16) <= 512 && cap >= 16) ? 16
+         : (3 * 8 * (P / 16) <= 512 && cap >= 8) ? 8
+         : (3 * 4 * (P / 16) <= 512 && cap >= 4) ? 4
+         : (3 * 2 * (P / 16) <= 512 && cap >= 2) ? 2 : 1;
+}
+__host__ __device__ constexpr int tz_of_len(int P) { return cols_of_len(P, 8); }
 __host__ __device__ constexpr int threads_of(int nlines, int logp) {
     return ((nlines * nb_of(logp) + 31) / 32) * 32 < 64 ? 64 : ((nlines * nb_of(logp) + 31) / 32) * 32;
 }

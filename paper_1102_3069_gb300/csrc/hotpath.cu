@@ -136,7 +136,8 @@ static cudaError_t set_attr_all() {
 cudaError_t configure_hot_kernels() {
     cudaError_t e = set_attr_all<12>();
     if (e != cudaSuccess) return e;
-    return configure_odd_kernels();
+    if ((e = configure_odd_kernels()) != cudaSuccess) return e;
+    return configure_odd_yz_kernels();
 }
 
 template <int L>
@@ -265,12 +266,14 @@ cudaError_t launch_pass(const HotParams& p, const LaunchArgs& a, int pass, cudaS
         case PASS_YCONV:
         case PASS_YFWD:
         case PASS_YINV:
+            if (p.ry > 1) return launch_yz_mixed(p, a, pass, s);
 #define MM_CALL_Y(L) launch_y<L>(p, a, pass, s)
             MM_LOGP_SWITCH(p.logpy, MM_CALL_Y)
 #undef MM_CALL_Y
             break;
         case PASS_ZCONV:
             if (p.zsplit) return launch_zconv_split(p, a, s);
+            if (p.rz > 1) return launch_yz_mixed(p, a, pass, s);
 #define MM_CALL_Z(L) launch_z<L>(p, a, s)
             MM_LOGP_SWITCH(p.logpz, MM_CALL_Z)
 #undef MM_CALL_Z

@@ -676,6 +676,135 @@ kb_yinv(const HotParams* __restrict__ ps, const int4* __restrict__ work, LaunchA
 }
 
 // ---------------------------------------------------------------------------
+// Passes along y and z for lengths P = R0 * 2^LOGP with an odd factor R0,
+// lines in shared memory (fft_lines_mixed): the column pass (MODE 0: 2-D y
+// lines of s1; MODE 1: 3-D z lines of s2) with the kernel product between the
+// transforms, and the 3-D y passes.
+template <int LOGP, int R0>
+struct OS {
+    static constexpr int P = R0 << LOGP, NB = P / 16, LS = padded_len(P);
+    static constexpr int COLS = cols_of_len(P, 64);
+    static constexpr int NL = 3 * COLS;
+    static constexpr int NT = (NL * NB + 31) / 32 * 32 < 64 ? 64 : (NL * NB + 31) / 32 * 32;
+    static constexpr int TZ = tz_of_len(P);
+    static constexpr int NLY = 3 * TZ;
+    static constexpr int NTY = (NLY * NB + 31) / 32 * 32 < 64 ? 64 : (NLY * NB + 31) / 32 * 32;
+};
+
+template <int LOGP, int R0, int MODE>
+__global__ void __launch_bounds__(OS<LOGP, R0>::NT) k_colconv_odd(HotParams p, LaunchArgs a) {
+    using S = OS<LOGP, R0>;
+    constexpr int P = S::P;
+    extern __shared__ float2 sm[];
+    if (a.mode != LM_EVAL && p.st->done) return;
+    const int HX = p.hx, PY = p.py;
+    const long long cstride = MODE == 0 ? (long long)HX * p.nyp : (long long)HX * PY * p.nzp;
+    const int nvalid = MODE == 0 ? p.ny : p.nz;
+    float2* buf = MODE == 0 ? p.s1 : p.s2;
+    // line base of column cl of this block (valid or not)
+    auto col = [&](int cl, long long& base) {
+        if (MODE == 0) {
+            const int kx = blockIdx.x * S::COLS + cl;
+            base = (long long)kx * p.nyp;
+            return kx < HX;
+        }
+        const int ky = blockIdx.y * S::COLS + cl;
+        base = ((long long)blockIdx.x * PY + ky) * p.nzp;
+        return ky < PY;
+    };
+    for (int idx = threadIdx.x; idx < S::NL * P; idx += S::NT) {
+        const int l = idx / P, pos = idx - l * P;
+        const int c = l / S::COLS, cl = l - c * S::COLS;
+        long long base;
+        const bool ok = col(cl, base);
+        sm[l * S::LS + pad(pos)] = (ok && pos < nvalid) ? buf[base + c * cstride + pos] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    fft_lines_mixed<LOGP, R0, S::NL, false>(sm, p.twr[R0]);
+    {
+        const long long cs = (long long)HX * p.hyk * p.hzk;
+        for (int idx = threadIdx.x; idx < S::COLS * P; idx += S::NT) {
+            const int cl = idx / P, k = idx - cl * P;
+            long long base;
+            if (!col(cl, base)) continue;
+            const bool hi = k > (P >> 1);
+            const int kq = hi ? P - k : k;
+            float2* e0 = sm + (0 * S::COLS + cl) * S::LS + pad(k);
+            float2* e1 = sm + (1 * S::COLS + cl) * S::LS + pad(k);
+            float2* e2 = sm + (2 * S::COLS + cl) * S::LS + pad(k);
+            const float2 X = *e0, Y = *e1, Z = *e2;
+            if constexpr (MODE == 0) {
+                const long long b = (long long)(blockIdx.x * S::COLS + cl) * p.hyk + kq;
+                const float kxx = __ldg(p.kt + b), kyy = __ldg(p.kt + cs + b), kzz = __ldg(p.kt + 2 * cs + b);
+                const float kxy = hi ? -__ldg(p.kt + 3 * cs + b) : __ldg(p.kt + 3 * cs + b);
+                *e0 = make_float2(kxx * X.x + kxy * Y.x, kxx * X.y + kxy * Y.y);
+                *e1 = make_float2(kxy * X.x + kyy * Y.x, kxy * X.y + kyy * Y.y);
+                *e2 = make_float2(kzz * Z.x, kzz * Z.y);
+            } else {
+                const int kx = blockIdx.x, ky = blockIdx.y * S::COLS + cl;
+                const bool yh = ky > (PY >> 1);
+                const int kyq = yh ? PY - ky : ky;
+                const long long b = ((long long)kx * p.hyk + kyq) * p.hzk + kq;
+                const float kxx = __ldg(p.kt + b), kyy = __ldg(p.kt + cs + b), kzz = __ldg(p.kt + 2 * cs + b);
+                float kxy = __ldg(p.kt + 3 * cs + b), kxz = __ldg(p.kt + 4 * cs + b), kyz = __ldg(p.kt + 5 * cs + b);
+                if (yh) { kxy = -kxy; kyz = -kyz; }
+                if (hi) { kxz = -kxz; kyz = -kyz; }
+                *e0 = make_float2(kxx * X.x + kxy * Y.x + kxz * Z.x, kxx * X.y + kxy * Y.y + kxz * Z.y);
+                *e1 = make_float2(kxy * X.x + kyy * Y.x + kyz * Z.x, kxy * X.y + kyy * Y.y + kyz * Z.y);
+                *e2 = make_float2(kxz * X.x + kyz * Y.x + kzz * Z.x, kxz * X.y + kyz * Y.y + kzz * Z.y);
+            }
+        }
+    }
+    __syncthreads();
+    fft_lines_mixed<LOGP, R0, S::NL, true>(sm, p.twr[R0]);
+    for (int idx = threadIdx.x; idx < S::NL * P; idx += S::NT) {
+        const int l = idx / P, pos = idx - l * P;
+        const int c = l / S::COLS, cl = l - c * S::COLS;
+        long long base;
+        if (col(cl, base) && pos < nvalid) buf[base + c * cstride + pos] = sm[l * S::LS + pad(pos)];
+    }
+}
+
+// 3-D y forward (s1 [c][kx][z][y] -> s2 [c][kx][ky][z]) and inverse passes, TZ z lines of one kx
+template <int LOGP, int R0, bool INV>
+__global__ void __launch_bounds__(OS<LOGP, R0>::NTY) k_ypass_odd(HotParams p, LaunchArgs a) {
+    using S = OS<LOGP, R0>;
+    constexpr int P = S::P, TZ = S::TZ;
+    extern __shared__ float2 sm[];
+    const int kx = blockIdx.x, z0 = blockIdx.y * TZ;
+    if (a.mode != LM_EVAL && p.st->done) return;
+    const int HX = p.hx, NY = p.ny, NZ = p.nz;
+    if (!INV) {
+        for (int idx = threadIdx.x; idx < S::NLY * P; idx += S::NTY) {
+            const int l = idx / P, y = idx - l * P;
+            const int c = l / TZ, zt = l - c * TZ, z = z0 + zt;
+            float2 v = make_float2(0.f, 0.f);
+            if (y < NY && z < NZ) v = p.s1[((long long)(c * HX + kx) * NZ + z) * p.nyp + y];
+            sm[l * S::LS + pad(y)] = v;
+        }
+    } else {
+        for (int idx = threadIdx.x; idx < S::NLY * P; idx += S::NTY) {
+            const int zt = idx % TZ, r = idx / TZ, ky = r % P, c = r / P;
+            sm[(c * TZ + zt) * S::LS + pad(ky)] = p.s2[((long long)(c * HX + kx) * P + ky) * p.nzp + z0 + zt];
+        }
+    }
+    __syncthreads();
+    fft_lines_mixed<LOGP, R0, S::NLY, INV>(sm, p.twr[R0]);
+    if (!INV) {
+        for (int idx = threadIdx.x; idx < S::NLY * P; idx += S::NTY) {
+            const int zt = idx % TZ, r = idx / TZ, ky = r % P, c = r / P;
+            p.s2[((long long)(c * HX + kx) * P + ky) * p.nzp + z0 + zt] = sm[(c * TZ + zt) * S::LS + pad(ky)];
+        }
+    } else {
+        for (int idx = threadIdx.x; idx < S::NLY * P; idx += S::NTY) {
+            const int l = idx / P, y = idx - l * P;
+            const int c = l / TZ, zt = l - c * TZ, z = z0 + zt;
+            if (y < NY && z < NZ) p.s1[((long long)(c * HX + kx) * NZ + z) * p.nyp + y] = sm[l * S::LS + pad(y)];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // block reduction + last-block step control
 struct Partials {
     float err, torque;

@@ -170,6 +170,10 @@ bool odd_x_length_supported(int r, int logp);          // x length r * 2^logp ha
 // the x passes of those lengths (hotpath_odd.cu)
 cudaError_t launch_x_mixed(const HotParams& p, const LaunchArgs& a, int pass, cudaStream_t s);
 cudaError_t configure_odd_kernels();
+// the y and z passes of those lengths (hotpath_odd_yz.cu)
+bool odd_yz_length_supported(int r, int logp);
+cudaError_t launch_yz_mixed(const HotParams& p, const LaunchArgs& a, int pass, cudaStream_t s);
+cudaError_t configure_odd_yz_kernels();
 
 // batched passes over independent samples (hotpath.cu)
 bool batch_supported(const HotParams& p);

@@ -18,15 +18,15 @@ def _built():
         build.build()
 
 
-# x lengths r * 2^l with an odd factor r that have compiled passes
-ODD_X = {r << l for r, ls in ((3, range(6, 11)), (5, range(6, 10)), (7, range(6, 10))) for l in ls}
+# lengths r * 2^l with an odd factor r that have compiled passes (every axis)
+ODD = {r << l for r, ls in ((3, range(6, 11)), (5, range(6, 10)), (7, range(6, 10))) for l in ls}
 
 
 def _accepted(n, periodic, axis):
     if n < 1:
         return False
     if periodic:
-        return (n <= 4096 and (n & (n - 1)) == 0) or (axis == 0 and n in ODD_X)
+        return (n <= 4096 and (n & (n - 1)) == 0) or n in ODD
     return n <= 2048
 
 

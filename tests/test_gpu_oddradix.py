@@ -1,8 +1,8 @@
 """FFT lengths with an odd factor (Sec. 3.3: sizes 2^n {1,3,5,7}) against the
-oracle.  An open x axis of n cells pads to the smallest 2^k or r * 2^l
-(r = 3, 5, 7) >= 2n - 1, a periodic x axis may have r * 2^l cells; the x
-passes then take a first radix-r pass before the power-of-two passes, and
-the kernel setup's FP64 FFT does the same.  The oracle pads by its own rule
+oracle.  An open axis of n cells pads to the smallest 2^k or r * 2^l
+(r = 3, 5, 7) >= 2n - 1, a periodic axis may have r * 2^l cells; the passes
+along that axis then take a first radix-r pass before the power-of-two
+passes, and the kernel setup's FP64 FFT does the same.  The oracle pads by its own rule
 (any length >= 2n - 1 gives the same linear convolution).
 
 Bounds as everywhere: relative L2 error of H_eff <= 1e-6, element-wise
@@ -31,6 +31,10 @@ def _unit64(m):
 CASES = [((130, 9, 1), (0, 0, 0), 320), ((600, 7, 1), (0, 0, 0), 1280), ((700, 5, 1), (0, 0, 0), 1536),
          ((1700, 3, 1), (0, 0, 0), 3584), ((1500, 2, 1), (0, 0, 0), 3072), ((96, 12, 3), (0, 0, 0), 192),
          ((192, 8, 1), (1, 0, 0), 192), ((320, 4, 2), (1, 0, 0), 320), ((448, 8, 1), (1, 1, 0), 448)]
+# odd factors along y (2-D column pass, 3-D y passes) and z (3-D column pass)
+CASES_YZ = [((9, 130, 1), (0, 0, 0)), ((5, 600, 1), (0, 0, 0)), ((8, 448, 1), (0, 1, 0)), ((6, 96, 3), (0, 0, 0)),
+            ((7, 160, 2), (0, 0, 0)), ((4, 5, 96), (0, 0, 0)), ((6, 4, 130), (0, 0, 0)), ((8, 8, 192), (0, 0, 1)),
+            ((96, 130, 40), (0, 0, 0)), ((192, 64, 5), (1, 1, 0))]
 
 
 @pytest.mark.parametrize("shape,pbc,px", CASES)
@@ -52,8 +56,25 @@ def test_heff_at_odd_x_lengths(shape, pbc, px):
     assert abs(e - E) <= 2e-6 * abs(E), (e, E)
 
 
+@pytest.mark.parametrize("shape,pbc", CASES_YZ)
+def test_heff_at_odd_y_and_z_lengths(shape, pbc):
+    cell = (4e-9, 3e-9, 2e-9)
+    m = inputs.random_unit(shape, 33)
+    s = solver(shape, cell, pbc=pbc, images=2, **MAT)
+    h, tq, _ = s.heff(to_dev(m), torque=True)
+    p = oracle(shape, cell, pbc=pbc, images=2, **MAT)
+    m64 = m.astype(np.float64)
+    H = p.heff(m64)
+    Hg = to_np(h)
+    print(shape, pbc, "rel L2", rel_l2(Hg, H), "rel max", rel_max(Hg, H))
+    assert rel_l2(Hg, H) <= HEFF_REL_L2
+    assert rel_max(Hg, H) <= HEFF_REL_MAX
+    assert rel_l2(to_np(tq), llg.ll_rhs(m64, H, p.alpha)) <= 2 * HEFF_REL_L2
+
+
 @pytest.mark.parametrize("shape,pbc,method", [((600, 7, 1), (0, 0, 0), B.MM_RKDP), ((96, 12, 3), (0, 0, 0), B.MM_RKDP),
-                                              ((192, 8, 1), (1, 0, 0), B.MM_HEUN)])
+                                              ((192, 8, 1), (1, 0, 0), B.MM_HEUN), ((5, 600, 1), (0, 0, 0), B.MM_RKDP),
+                                              ((96, 130, 40), (0, 0, 0), B.MM_RKDP)])
 def test_step_at_odd_x_lengths(shape, pbc, method):
     cell = (4e-9, 3e-9, 2e-9)
     m = inputs.random_unit(shape, 32)
