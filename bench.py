@@ -518,6 +518,7 @@ def run_ensemble(args):
     t0 = time.perf_counter()
     with torch.cuda.stream(stream):
         sol = [B.Solver(s["shape"], s["cell"], pbc=s["pbc"], stream=stream.cuda_stream, tensor=False,
+                        fft_lengths=B.MM_FFT_POW2,
                         **s["material"]) for s in samples]
         ms = [torch.from_numpy(inputs.random_unit(s["shape"], s["m_seed"])).cuda() for s in samples]
         torch.cuda.synchronize()
@@ -603,6 +604,7 @@ def run_relax(args):
     tq_tol, err_tol, max_steps = 1e-4, 1e-6, args.relax_max_steps
     with torch.cuda.stream(stream):
         sol = [B.Solver(f["shape"], f["cell"], pbc=f["pbc"], stream=stream.cuda_stream, tensor=False,
+                        fft_lengths=B.MM_FFT_POW2,
                         **f["material"]) for f in films]
         m0 = [torch.from_numpy(inputs.random_unit(f["shape"], f["m_seed"])).cuda() for f in films]
         bt = B.Batch(sol, stream.cuda_stream)
@@ -656,6 +658,7 @@ def _relax_films(films, m_start, stream, tq_tol, err_tol, max_steps):
     from paper_1102_3069_gb300 import binding as B
     with torch.cuda.stream(stream):
         sol = [B.Solver(f["shape"], f["cell"], pbc=f["pbc"], stream=stream.cuda_stream, tensor=False,
+                        fft_lengths=B.MM_FFT_POW2,
                         **f["material"]) for f in films]
         bt = B.Batch(sol, stream.cuda_stream)
         ms = [m.clone() for m in m_start]
@@ -792,10 +795,16 @@ def run_relax_ensemble(args):
     ms, t, steps, tq, conv = _relax_films(samples, m0, stream, tq_tol, err_tol, max_steps)
     setup_and_relax = time.perf_counter() - t0
     cells = [int(np.prod(x["shape"])) for x in samples]
+    left = [i for i in range(len(samples)) if not tq[i] < tq_tol]
+    unconverged = [{"sample": i, "shape": list(samples[i]["shape"]), "Ms": samples[i]["material"]["Ms"],
+                    "Ku": samples[i]["material"]["Ku"], "B_T": float(np.linalg.norm(samples[i]["material"]["B"])),
+                    "steps": int(steps[i]), "torque": float(tq[i])} for i in left]
     return {"metric": "time to relax the ensemble (torque < 1e-4)", "value": t, "unit": "s",
             "higher_is_better": False, "n_gpus": 1, "samples": len(samples), "converged": conv,
             "cells_total": sum(cells), "steps_median": float(np.median(steps)), "steps_max": int(max(steps)),
             "torque_max": float(max(tq)), "setup_plus_relax_s": setup_and_relax,
+            "steps_quantiles": {q: float(np.quantile(steps, float(q))) for q in ("0.5", "0.9", "0.95")},
+            "unconverged": unconverged,
             "data": "synthetic (seeded per-sample geometry, material, field and random unit m)",
             "config": {"workload": f"ensemble_{len(samples)}_relax", "alpha": args.relax_alpha,
                        "grids": "nx, ny U{32..256}, nz U{1..4}, 4 nm cells, open boundaries",

@@ -84,12 +84,24 @@ typedef struct mm_stats {
  * and 7 * 2^6 .. 7 * 2^9).  A periodic axis needs n to be one of those
  * lengths.  nx, ny, nz in [1, 2048] for open axes (padded length <= 4096)
  * and [1, 4096] for periodic ones.  Grids with an odd factor in any padded
- * length run single contexts only (mm_batch_create refuses them).
+ * length run single contexts only: mm_batch_create refuses them (see
+ * mm_set_fft_lengths).
  * cuda_stream: a cudaStream_t (NULL = legacy default stream).
  * On success *out owns host memory only; free it with mm_destroy.
  */
 int mm_init_geometry(mm_ctx** out, int nx, int ny, int nz, double dx, double dy, double dz,
                      int pbc_x, int pbc_y, int pbc_z, int pbc_images, void* cuda_stream);
+
+/*
+ * Which FFT lengths the open axes pad to (an implementation choice within
+ * Sec. 3.3's rule): MM_FFT_2357 (default) - the smallest 2^k or r * 2^l
+ * (r = 3, 5, 7) >= 2n-1; MM_FFT_POW2 - the smallest power of two >= 2n-1,
+ * which batches (mm_batch_create) need for every sample.  Call before
+ * mm_set_workspace (the workspace size follows); MM_ESTATE after it,
+ * MM_EINVAL for MM_FFT_POW2 with a periodic axis of r * 2^l cells.
+ */
+enum { MM_FFT_2357 = 0, MM_FFT_POW2 = 1 };
+int mm_set_fft_lengths(mm_ctx* ctx, int mode);
 
 /* Device workspace size in bytes for this geometry (kernel, spectra, RK stages). */
 size_t mm_workspace_bytes(const mm_ctx* ctx);
@@ -336,8 +348,8 @@ int mm_run_host(mm_ctx* ctx, float* m_host, int method, long nsteps, double dt_s
  * local terms, stage-2 combine, local terms without demag, x inverse + local
  * terms + forward x transform of the next stage's input, x inverse alone
  * (demag field to a buffer), cell pass reading that buffer, forward x
- * transform of the next stage's input.  Time steps on grids whose padded x
- * length is at least 64 use the last three; the rest use the fused passes.
+ * transform of the next stage's input.  Time steps use the fused passes; the
+ * last three run under MM_LAYOUT_SPLIT (mm_set_pass_layout) and in batches.
  */
 enum { MM_NPASS = 12 };
 int mm_profile(mm_ctx* ctx, int enable);

@@ -22,6 +22,7 @@ MM_OK, MM_EINVAL, MM_ENOMEM, MM_ECUDA = 0, -1, -2, -3
 MM_ENOTCONVERGED, MM_ENONFINITE, MM_ETIMEOUT, MM_ESTATE = -4, -5, -6, -7
 MM_EULER, MM_HEUN, MM_RK3, MM_RK4, MM_RKDP, MM_RKCK, MM_RK12, MM_RK23 = 1, 2, 3, 4, 5, 6, 12, 23
 MM_DFT_FP32, MM_DFT_SPLIT_BF16 = 0, 1
+MM_FFT_2357, MM_FFT_POW2 = 0, 1
 
 STATUS_NAMES = {0: "MM_OK", -1: "MM_EINVAL", -2: "MM_ENOMEM", -3: "MM_ECUDA", -4: "MM_ENOTCONVERGED",
                 -5: "MM_ENONFINITE", -6: "MM_ETIMEOUT", -7: "MM_ESTATE"}
@@ -61,6 +62,7 @@ _SIGS = {
     "mm_set_max_dm": (_i, [_vp, _d]),
     "mm_set_pass_layout": (_i, [_vp, _i]),
     "mm_set_dft_precision": (_i, [_vp, _i]),
+    "mm_set_fft_lengths": (_i, [_vp, _i]),
     "mm_set_cubic_anisotropy": (_i, [_vp, _d, _d, _dp, _dp]),
     "mm_set_stt": (_i, [_vp, _d, _d, _dp]),
     "mm_demag_kernel": (_i, [_vp, _dp]),
@@ -212,6 +214,10 @@ def mm_set_pass_layout(ctx, layout):
 
 def mm_set_dft_precision(ctx, mode):
     return _check(ctx, lib().mm_set_dft_precision(ctx, int(mode)))
+
+
+def mm_set_fft_lengths(ctx, mode):
+    return _check(ctx, lib().mm_set_fft_lengths(ctx, int(mode)))
 
 
 def mm_set_max_dm(ctx, max_dm):
@@ -453,7 +459,7 @@ class Solver:
     """
 
     def __init__(self, shape, cell, pbc=(0, 0, 0), images=10, demag=True, stream=None, tensor=True,
-                 dft_precision=None, **material):
+                 dft_precision=None, fft_lengths=None, **material):
         import torch
         self.torch = torch
         self.shape = tuple(int(v) for v in shape)
@@ -462,6 +468,8 @@ class Solver:
             stream = torch.cuda.current_stream().cuda_stream
         self.stream = stream
         self.ctx = mm_init_geometry(*self.shape, *self.cell, pbc, images, stream)
+        if fft_lengths is not None:
+            mm_set_fft_lengths(self.ctx, fft_lengths)
         if dft_precision is not None:
             mm_set_dft_precision(self.ctx, dft_precision)
         nbytes = mm_workspace_bytes(self.ctx)

@@ -52,6 +52,25 @@ bool odd_length(int v, int axis, int* r_out) {
     *r_out = v;
     return true;
 }
+// FFT length of an axis of n cells: periodic - n itself (2^k or r 2^l);
+// open - the smallest 2^k, or with odd factors allowed r 2^l, >= 2n - 1
+bool pad_length(int n, bool periodic, int axis, bool odd, int* P, int* R) {
+    *R = 1;
+    if (periodic) {
+        *P = n;
+        return (is_pow2(n) && n <= 4096) || odd_length(n, axis, R);
+    }
+    if (n > 2048) return false;
+    *P = next_pow2(2 * n - 1);
+    if (odd)
+        for (int r = 3; r <= 7; r += 2)
+            for (int l = 0; (r << l) <= 4096; ++l)
+                if ((r << l) >= 2 * n - 1 && (r << l) < *P && odd_supported(axis, r, l)) {
+                    *P = r << l;
+                    *R = r;
+                }
+    return true;
+}
 
 // Gauss-Legendre nodes/weights on [-1, 1] (Newton iteration on P_n)
 void gauss_legendre(int n, double* t, double* w) {
@@ -184,6 +203,21 @@ void layout(mm_ctx* c) {
                    : 0;
     c->off_zs = off; off += align256(c->sz_zs);
     c->total = off;
+}
+
+// FFT lengths r * 2^logp of the three axes and what follows from them
+void set_lengths(mm_ctx* c, const int P[3], const int R[3]) {
+    c->px = P[0]; c->py = P[1]; c->pz = P[2];
+    c->rx = R[0]; c->ry = R[1]; c->rz = R[2];
+    c->logpx = ilog2(P[0] / R[0]); c->logpy = ilog2(P[1] / R[1]); c->logpz = ilog2(P[2] / R[2]);
+    c->hx = c->px / 2 + 1;
+    if (c->px == 1) c->hx = 1;
+    c->hyk = c->py / 2 + 1;
+    c->hzk = c->pz / 2 + 1;
+    // launch shapes: the kernels' compile-time tiles (fft32.cuh)
+    c->ty = mmfft::ty_of(c->logpx);
+    c->tz = c->ry > 1 ? mmfft::tz_of_len(c->py) : mmfft::tz_of(c->logpy);
+    c->nzp = (c->nz + c->tz - 1) / c->tz * c->tz;  // the 3-D y passes write whole z tiles
 }
 
 mm::DevState* dstate(mm_ctx* c) { return reinterpret_cast<mm::DevState*>(c->ws + c->off_st); }
@@ -456,26 +490,7 @@ int mm_init_geometry(mm_ctx** out, int nx, int ny, int nz, double dx, double dy,
     int P[3], R[3];
     for (int a = 0; a < 3; ++a) {
         if (n[a] < 1) return MM_EINVAL;
-        R[a] = 1;
-        if (pb[a]) {
-            if (is_pow2(n[a]) && n[a] <= 4096) {
-                P[a] = n[a];
-            } else if (odd_length(n[a], a, &R[a])) {
-                P[a] = n[a];           // a periodic axis of r * 2^l cells
-            } else {
-                return MM_EINVAL;
-            }
-        } else {
-            if (n[a] > 2048) return MM_EINVAL;
-            P[a] = next_pow2(2 * n[a] - 1);
-            // the smallest r * 2^l >= 2n - 1 with compiled passes (Sec. 3.3's sizes)
-            for (int r = 3; r <= 7; r += 2)
-                for (int l = 0; (r << l) <= 4096; ++l)
-                    if ((r << l) >= 2 * n[a] - 1 && (r << l) < P[a] && odd_supported(a, r, l)) {
-                        P[a] = r << l;
-                        R[a] = r;
-                    }
-        }
+        if (!pad_length(n[a], pb[a], a, true, &P[a], &R[a])) return MM_EINVAL;
     }
     if (!(dx > 0 && dy > 0 && dz > 0) || !std::isfinite(dx) || !std::isfinite(dy) || !std::isfinite(dz))
         return MM_EINVAL;
@@ -486,13 +501,7 @@ int mm_init_geometry(mm_ctx** out, int nx, int ny, int nz, double dx, double dy,
     c->dx = dx; c->dy = dy; c->dz = dz;
     for (int a = 0; a < 3; ++a) c->pbc[a] = pb[a];
     c->images = pbc_images;
-    c->px = P[0]; c->py = P[1]; c->pz = P[2];
-    c->rx = R[0]; c->ry = R[1]; c->rz = R[2];
-    c->logpx = ilog2(P[0] / R[0]); c->logpy = ilog2(P[1] / R[1]); c->logpz = ilog2(P[2] / R[2]);
-    c->hx = c->px / 2 + 1;
-    if (c->px == 1) c->hx = 1;
-    c->hyk = c->py / 2 + 1;
-    c->hzk = c->pz / 2 + 1;
+    set_lengths(c, P, R);
     c->ncomp = nz == 1 ? 4 : 6;
     c->ncell = (long long)nx * ny * nz;
     c->ox = pb[0] ? nx / 2 + 1 : nx;
@@ -500,11 +509,8 @@ int mm_init_geometry(mm_ctx** out, int nx, int ny, int nz, double dx, double dy,
     c->oz = pb[2] ? nz / 2 + 1 : nz;
     // launch shapes: the kernels' compile-time tiles (fft32.cuh), about 384
     // threads per block with one radix-16 butterfly each
-    c->ty = mmfft::ty_of(c->logpx);
     c->nyp = (ny + 15) / 16 * 16;                  // a multiple of every x-pass tile
     c->kxb = 1;                                    // column passes size their own blocks
-    c->tz = c->ry > 1 ? mmfft::tz_of_len(c->py) : mmfft::tz_of(c->logpy);
-    c->nzp = (nz + c->tz - 1) / c->tz * c->tz;     // the 3-D y passes write whole z tiles
     c->tky = 1;
     c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
     layout(c);
@@ -650,6 +656,22 @@ int mm_set_anisotropy_axes(mm_ctx* ctx, const float* u) {
     ctx->uaxis = u;
     ctx->k1_valid = false;
     ctx->param_version++;
+    return MM_OK;
+}
+
+int mm_set_fft_lengths(mm_ctx* ctx, int mode) {
+    if (!ctx) return MM_EINVAL;
+    if (mode != MM_FFT_2357 && mode != MM_FFT_POW2) return fail(ctx, MM_EINVAL, "mode must be MM_FFT_2357 or MM_FFT_POW2");
+    if (ctx->ws) return fail(ctx, MM_ESTATE, "the FFT lengths are chosen before mm_set_workspace");
+    const int n[3] = {ctx->nx, ctx->ny, ctx->nz};
+    int P[3], R[3];
+    for (int a = 0; a < 3; ++a)
+        if (!pad_length(n[a], ctx->pbc[a] != 0, a, mode == MM_FFT_2357, &P[a], &R[a]))
+            return fail(ctx, MM_EINVAL, "no FFT length for this axis");
+    if (mode == MM_FFT_POW2 && (R[0] > 1 || R[1] > 1 || R[2] > 1))
+        return fail(ctx, MM_EINVAL, "a periodic axis of r * 2^l cells needs its odd factor");
+    set_lengths(ctx, P, R);
+    layout(ctx);
     return MM_OK;
 }
 

@@ -129,3 +129,27 @@ def test_option_calls_check_their_arguments_on_host():
     assert B.lib().mm_batch_create(ctypes.byref(b), None, 0, None) == B.MM_EINVAL
     assert B.mm_batch_workspace_bytes(None) == 0
     B.lib().mm_batch_destroy(None)
+
+
+def test_fft_length_choice_on_the_host():
+    """An open axis of 600 cells pads to 1280 = 5 * 256 by default and to 2048
+    with MM_FFT_POW2 (the choice moves the workspace size); a periodic axis
+    of 192 = 3 * 64 cells keeps its odd factor and refuses MM_FFT_POW2."""
+    _ensure_built()
+    a = B.mm_init_geometry(600, 7, 1, 4e-9, 4e-9, 4e-9)
+    b = B.mm_init_geometry(600, 7, 1, 4e-9, 4e-9, 4e-9)
+    c = B.mm_init_geometry(192, 8, 1, 4e-9, 4e-9, 4e-9, pbc=(1, 0, 0))
+    try:
+        B.mm_set_fft_lengths(b, B.MM_FFT_POW2)
+        # spectrum rows: (1280/2 + 1) against (2048/2 + 1) complex values per row
+        assert B.mm_workspace_bytes(b) > B.mm_workspace_bytes(a)
+        B.mm_set_fft_lengths(b, B.MM_FFT_2357)
+        assert B.mm_workspace_bytes(b) == B.mm_workspace_bytes(a)
+        with pytest.raises(B.MMError) as e:
+            B.mm_set_fft_lengths(c, B.MM_FFT_POW2)
+        assert e.value.code == B.MM_EINVAL
+        with pytest.raises(B.MMError):
+            B.mm_set_fft_lengths(a, 7)
+    finally:
+        for x in (a, b, c):
+            B.mm_destroy(x)

@@ -24,7 +24,8 @@ pytestmark = pytest.mark.gpu
 
 
 def _solvers(samples, stream):
-    return [B.Solver(s["shape"], s["cell"], pbc=s["pbc"], stream=stream, tensor=False, **s["material"])
+    return [B.Solver(s["shape"], s["cell"], pbc=s["pbc"], stream=stream, tensor=False, fft_lengths=B.MM_FFT_POW2,
+                     **s["material"])
             for s in samples]
 
 
@@ -84,7 +85,7 @@ def test_batch_fixed_steps_match_single(method, calls):
         torch.cuda.synchronize()
         for i, s in enumerate(samples):
             one = B.Solver(s["shape"], s["cell"], pbc=s["pbc"], stream=stream.cuda_stream, tensor=False,
-                           **s["material"])
+                           fft_lengths=B.MM_FFT_POW2, **s["material"])
             m = m0[i].clone()
             B.mm_load(one.ctx, m)
             for n, dt, tol in calls:
@@ -117,7 +118,7 @@ def test_batch_relax_reaches_torque_bound():
         assert max(tq) < tq_tol and min(steps) > 0
         for i, s in enumerate(samples):
             one = B.Solver(s["shape"], s["cell"], pbc=s["pbc"], stream=stream.cuda_stream, tensor=False,
-                           **s["material"])
+                           fft_lengths=B.MM_FFT_POW2, **s["material"])
             h, _, e1 = one.heff(mb[i], energy=True)
             _, _, e0 = one.heff(m_start[i], energy=True)
             torch.cuda.synchronize()
@@ -137,7 +138,7 @@ def test_batch_rejects_unsupported_contexts():
         B.mm_batch_create([s.ctx], stream.cuda_stream)          # padded x length 32 < 64
     assert e.value.code == B.MM_EINVAL
     t = B.Solver((40, 40, 1), (4e-9, 4e-9, 4e-9), stream=stream.cuda_stream, tensor=False, Ms=8e5, Aex=1.3e-11,
-                 temperature=300.0)
+                 temperature=300.0, fft_lengths=B.MM_FFT_POW2)
     bt = B.Batch([t], stream.cuda_stream)
     B.mm_batch_load(bt.b, [torch.from_numpy(inputs.random_unit((40, 40, 1), 0)).cuda()])
     with pytest.raises(B.MMError) as e:
@@ -187,7 +188,7 @@ def test_batch_periodic_samples_match_oracle():
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         sol = [B.Solver(s["shape"], s["cell"], pbc=s["pbc"], images=images, stream=stream.cuda_stream,
-                        tensor=False, **mat) for s in samples]
+                        tensor=False, fft_lengths=B.MM_FFT_POW2, **mat) for s in samples]
         m0 = _m0(samples)
         bt = B.Batch(sol, stream.cuda_stream)
         B.mm_batch_load(bt.b, m0)
