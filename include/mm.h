@@ -160,17 +160,23 @@ int mm_set_anisotropy_axes(mm_ctx* ctx, const float* u);
 int mm_set_max_dm(mm_ctx* ctx, double max_dm);
 
 /*
- * Layout of the x passes in time steps (an implementation choice with no
- * counterpart in the paper).  For padded x lengths 64 to 2048 an evaluation
- * inside a step can either run the inverse x transform, the cell-local terms
- * with the stage update, and the forward x transform of the next stage's input
- * as one kernel (MM_LAYOUT_FUSED), or as three kernels with H_demag passing
- * through device memory (MM_LAYOUT_SPLIT).  MM_LAYOUT_AUTO (default) takes the
- * one measured faster on GB300, the fused kernel, for every method.  Results
- * agree to float32 rounding.  Other lengths and mm_eval_heff always use the
- * fused kernel; batches (mm_batch_*) always use the split passes.
+ * Layout of the passes (an implementation choice with no counterpart in the
+ * paper).  For padded x lengths 64 to 2048 an evaluation inside a step can
+ * either run the inverse x transform, the cell-local terms with the stage
+ * update, and the forward x transform of the next stage's input as one kernel
+ * (MM_LAYOUT_FUSED), or as three kernels with H_demag passing through device
+ * memory (MM_LAYOUT_SPLIT).  MM_LAYOUT_CLUSTER runs every evaluation (time
+ * steps and mm_eval_heff) as ONE launch of a thread-block cluster of 1 to 16
+ * CTAs that keeps the half spectrum in the CTAs' shared memory: 2-D grids
+ * only (nz = 1, open z), power-of-two FFT lengths along x and y, and a half
+ * spectrum that fits the cluster (up to about 256 x 256 cells); MM_EINVAL for
+ * other grids.  A run of steps (mm_advance) is one launch of that cluster
+ * for all its standard steps.  MM_LAYOUT_AUTO (default) takes the fused
+ * kernel: the cluster launch measured slower on GB300 at every size it
+ * applies to.  Results of all layouts agree to float32 rounding.  Batches
+ * (mm_batch_*) always use the split passes.
  */
-enum { MM_LAYOUT_AUTO = 0, MM_LAYOUT_FUSED = 1, MM_LAYOUT_SPLIT = 2 };
+enum { MM_LAYOUT_AUTO = 0, MM_LAYOUT_FUSED = 1, MM_LAYOUT_SPLIT = 2, MM_LAYOUT_CLUSTER = 3 };
 int mm_set_pass_layout(mm_ctx* ctx, int layout);
 
 /*
@@ -348,10 +354,12 @@ int mm_run_host(mm_ctx* ctx, float* m_host, int method, long nsteps, double dt_s
  * local terms, stage-2 combine, local terms without demag, x inverse + local
  * terms + forward x transform of the next stage's input, x inverse alone
  * (demag field to a buffer), cell pass reading that buffer, forward x
- * transform of the next stage's input.  Time steps use the fused passes; the
- * last three run under MM_LAYOUT_SPLIT (mm_set_pass_layout) and in batches.
+ * transform of the next stage's input, the one-launch cluster evaluation.
+ * Time steps use the fused passes; the split passes run under MM_LAYOUT_SPLIT
+ * (mm_set_pass_layout) and in batches; small 2-D grids run the cluster launch
+ * (MM_LAYOUT_AUTO, MM_LAYOUT_CLUSTER).
  */
-enum { MM_NPASS = 12 };
+enum { MM_NPASS = 13 };
 int mm_profile(mm_ctx* ctx, int enable);
 int mm_pass_times(mm_ctx* ctx, double* ms_out, long long* count_out);
 

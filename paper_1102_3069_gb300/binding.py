@@ -205,7 +205,7 @@ def mm_set_anisotropy_axes(ctx, u):
     return _check(ctx, lib().mm_set_anisotropy_axes(ctx, _ptr(u)))
 
 
-MM_LAYOUT_AUTO, MM_LAYOUT_FUSED, MM_LAYOUT_SPLIT = 0, 1, 2
+MM_LAYOUT_AUTO, MM_LAYOUT_FUSED, MM_LAYOUT_SPLIT, MM_LAYOUT_CLUSTER = 0, 1, 2, 3
 
 
 def mm_set_pass_layout(ctx, layout):
@@ -312,7 +312,7 @@ def mm_run_host(ctx, m_host, method, nsteps, dt_s=0.0, tol=1e-6):
 
 
 PASS_NAMES = ["k_xfwd", "k_colconv_y", "k_yfwd", "k_colconv_z", "k_yinv", "k_xinv_local", "k_combine2", "k_local",
-              "k_xinv_local_fused", "k_xinv_h", "k_local_h", "k_xfwd_next"]
+              "k_xinv_local_fused", "k_xinv_h", "k_local_h", "k_xfwd_next", "k_small"]
 NPASS = len(PASS_NAMES)
 
 

@@ -145,6 +145,8 @@ struct mm_ctx {
     std::string err;
     // one standard step captured as a CUDA graph and replayed (see mm_advance)
     cudaGraphExec_t step_graph = nullptr;
+    // while set, eval() records its launch arguments here instead of launching
+    std::vector<mm::LaunchArgs>* rec = nullptr;
     int graph_method = 0;
     double graph_dt = 0.0;
     unsigned long long graph_version = 0;
@@ -236,6 +238,19 @@ int check_ready(mm_ctx* ctx, bool need_kernel) {
     return MM_OK;
 }
 
+// Whether MM_LAYOUT_AUTO takes the one-launch cluster evaluation for a grid
+// that fits it (cl > 0 CTAs).  Not for now: on GB300 it measured slower than
+// the multi-kernel passes at every size it applies to (32^2 Euler 29.8 against
+// 22.6 us per step, 128^2 36.2 against 30.8 us, 256^2 113 against 32 us):
+// each CTA runs the phases of an evaluation one after another, and the chain
+// of barriers and dependent latencies is longer than the multi-kernel passes'
+// launch gaps.
+bool small_auto(const mm::HotParams& p, int cl) {
+    (void)p;
+    (void)cl;
+    return false;
+}
+
 mm::HotParams hot_params(mm_ctx* c, double dt_internal, bool thermal) {
     mm::HotParams p;
     std::memset(&p, 0, sizeof(p));
@@ -316,6 +331,11 @@ mm::HotParams hot_params(mm_ctx* c, double dt_internal, bool thermal) {
         p.zs_g_lo = b; b += z[4];
         p.zs_err = reinterpret_cast<unsigned*>(b);
     }
+    // small 2-D grids: one cluster launch per evaluation (automatic, or forced)
+    if (c->demag && (c->layout == MM_LAYOUT_AUTO || c->layout == MM_LAYOUT_CLUSTER)) {
+        const int cl = mm::small_cluster_size(p);
+        if (c->layout == MM_LAYOUT_CLUSTER || small_auto(p, cl)) p.small_cl = cl;
+    }
     return p;
 }
 
@@ -367,6 +387,10 @@ bool use_split_layout(const mm_ctx* ctx, int method, bool maxdm) {
 int eval(mm_ctx* ctx, const mm::HotParams& p, int src, int mode, int stage, bool fuse = false,
          bool have_spectrum = false) {
     const mm::LaunchArgs a = make_args(p, src, mode, stage, fuse, have_spectrum);
+    if (ctx->rec) {
+        ctx->rec->push_back(a);
+        return MM_OK;
+    }
     int ids[8];
     const int n = mm::eval_passes(p, a, ids);
     for (int i = 0; i < n; ++i) {
@@ -689,8 +713,22 @@ int mm_set_dft_precision(mm_ctx* ctx, int mode) {
 
 int mm_set_pass_layout(mm_ctx* ctx, int layout) {
     if (!ctx) return MM_EINVAL;
-    if (layout != MM_LAYOUT_AUTO && layout != MM_LAYOUT_FUSED && layout != MM_LAYOUT_SPLIT)
-        return fail(ctx, MM_EINVAL, "layout must be MM_LAYOUT_AUTO, MM_LAYOUT_FUSED or MM_LAYOUT_SPLIT");
+    if (layout != MM_LAYOUT_AUTO && layout != MM_LAYOUT_FUSED && layout != MM_LAYOUT_SPLIT &&
+        layout != MM_LAYOUT_CLUSTER)
+        return fail(ctx, MM_EINVAL,
+                    "layout must be MM_LAYOUT_AUTO, MM_LAYOUT_FUSED, MM_LAYOUT_SPLIT or MM_LAYOUT_CLUSTER");
+    if (layout == MM_LAYOUT_CLUSTER) {
+        mm::HotParams q;
+        std::memset(&q, 0, sizeof(q));
+        q.nx = ctx->nx; q.ny = ctx->ny; q.nz = ctx->nz;
+        q.logpx = ctx->logpx; q.logpy = ctx->logpy;
+        q.rx = ctx->rx; q.ry = ctx->ry;
+        for (int i = 0; i < 3; ++i) q.pbc[i] = ctx->pbc[i];
+        q.ncell = ctx->ncell;
+        if (mm::small_cluster_size(q) == 0)
+            return fail(ctx, MM_EINVAL, "MM_LAYOUT_CLUSTER needs a 2-D grid (open z) with power-of-two FFT lengths "
+                                        "whose half spectrum fits 16 CTAs' shared memory");
+    }
     if (layout != ctx->layout) {
         ctx->layout = layout;
         ctx->k1_valid = false;
@@ -908,6 +946,23 @@ int mm_advance(mm_ctx* ctx, int method, long nsteps, double dt_s, double tol, do
     if (nsteps > 0 && first_special) {
         if ((rc = enqueue_step(ctx, p, method, true))) return rc;
         ++s;
+    }
+    if (s < nsteps && p.small_cl > 0 && !maxdm && !ctx->profiling) {
+        // small 2-D grids: every remaining standard step in one persistent cluster launch
+        std::vector<mm::LaunchArgs> rec;
+        ctx->rec = &rec;
+        const int erc = enqueue_step(ctx, p, method, false);
+        ctx->rec = nullptr;
+        if (erc) return erc;
+        if (!rec.empty() && rec.size() <= 8) {
+            mm::SmallSteps L;
+            std::memset(&L, 0, sizeof(L));
+            L.nsteps = nsteps - s;
+            L.n = (int)rec.size();
+            for (int i = 0; i < L.n; ++i) L.a[i] = rec[i];
+            CK(mm::launch_small_steps(p, L, ctx->stream));
+            s = nsteps;
+        }
     }
     if (s < nsteps) {
         // the standard step: replayed from a CUDA graph on a capturable stream

@@ -137,7 +137,8 @@ cudaError_t configure_hot_kernels() {
     cudaError_t e = set_attr_all<12>();
     if (e != cudaSuccess) return e;
     if ((e = configure_odd_kernels()) != cudaSuccess) return e;
-    return configure_odd_yz_kernels();
+    if ((e = configure_odd_yz_kernels()) != cudaSuccess) return e;
+    return configure_small_kernels();
 }
 
 template <int L>
@@ -227,6 +228,10 @@ static void launch_z(const HotParams& p, const LaunchArgs& a, cudaStream_t s) {
 
 int eval_passes(const HotParams& p, const LaunchArgs& a, int* ids) {
     int n = 0;
+    if (p.demag && p.small_cl > 0) {
+        ids[n++] = PASS_SMALL;          // every evaluation transforms its own input
+        return n;
+    }
     if (p.demag) {
         if (!a.have_spectrum) ids[n++] = PASS_XFWD;
         if (p.nz == 1) {
@@ -281,6 +286,8 @@ cudaError_t launch_pass(const HotParams& p, const LaunchArgs& a, int pass, cudaS
         case PASS_COMBINE2:
             k_combine2<<<4 * 152, 256, 0, s>>>(p);
             break;
+        case PASS_SMALL:
+            return launch_small(p, a, s);
         case PASS_LOCAL:            // one cell per thread: every load in flight at once
             k_local<<<(unsigned)((p.ncell + 255) / 256), 256, 0, s>>>(p, a);
             break;

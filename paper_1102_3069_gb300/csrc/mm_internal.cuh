@@ -93,6 +93,7 @@ struct HotParams {
     unsigned long long seed;
     long long thermal_step;  // EVAL-mode thermal clock
     int demag;
+    int small_cl;            // > 0: each evaluation is one cluster launch of this many CTAs (hotpath_small.cu)
     // step (internal units)
     double dt_d;             // Euler/Heun fixed step
     int rk;                  // Runge-Kutta tableau index (hotpath.cu c_rka)
@@ -153,7 +154,8 @@ enum Pass : int {
     PASS_XINV_H = 9,        // inverse x transform alone: H_demag into hbuf
     PASS_LOCAL_H = 10,      // cell pass with H_demag from hbuf
     PASS_XFWD_NEXT = 11,    // forward x transform of the next evaluation's input
-    NPASS = 12
+    PASS_SMALL = 12,        // the whole evaluation in one cluster launch (small 2-D grids)
+    NPASS = 13
 };
 
 // hot path (hotpath.cu)
@@ -174,6 +176,19 @@ cudaError_t configure_odd_kernels();
 bool odd_yz_length_supported(int r, int logp);
 cudaError_t launch_yz_mixed(const HotParams& p, const LaunchArgs& a, int pass, cudaStream_t s);
 cudaError_t configure_odd_yz_kernels();
+
+// one-launch evaluation of small 2-D grids (hotpath_small.cu): CTAs per
+// cluster for this geometry (0: does not apply), the launch, the attributes
+int small_cluster_size(const HotParams& p);
+cudaError_t launch_small(const HotParams& p, const LaunchArgs& a, cudaStream_t s);
+// a run of nsteps standard steps (the n evaluations of one step, in order) in one launch
+struct SmallSteps {
+    long long nsteps;
+    int n;
+    LaunchArgs a[8];
+};
+cudaError_t launch_small_steps(const HotParams& p, const SmallSteps& steps, cudaStream_t s);
+cudaError_t configure_small_kernels();
 
 // batched passes over independent samples (hotpath.cu)
 bool batch_supported(const HotParams& p);

@@ -97,12 +97,21 @@ def test_option_calls_check_their_arguments_on_host():
     _ensure_built()
     ctx = B.mm_init_geometry(64, 16, 1, 4e-9, 4e-9, 4e-9)
     try:
-        for bad in (-1, 3, 7):
+        for bad in (-1, 4, 7):
             with pytest.raises(B.MMError) as e:
                 B.mm_set_pass_layout(ctx, bad)
             assert e.value.code == B.MM_EINVAL
-        for layout in (B.MM_LAYOUT_AUTO, B.MM_LAYOUT_FUSED, B.MM_LAYOUT_SPLIT):
+        for layout in (B.MM_LAYOUT_AUTO, B.MM_LAYOUT_FUSED, B.MM_LAYOUT_SPLIT, B.MM_LAYOUT_CLUSTER):
             B.mm_set_pass_layout(ctx, layout)
+        # the one-launch cluster evaluation: 2-D grids whose half spectrum fits 16 CTAs
+        for shape in ((8, 8, 2), (600, 7, 1), (300, 300, 1)):
+            c3 = B.mm_init_geometry(*shape, 4e-9, 4e-9, 4e-9)
+            try:
+                with pytest.raises(B.MMError) as e:
+                    B.mm_set_pass_layout(c3, B.MM_LAYOUT_CLUSTER)
+                assert e.value.code == B.MM_EINVAL
+            finally:
+                B.mm_destroy(c3)
         for bad in (-0.1, 1.5, float("nan")):
             with pytest.raises(B.MMError) as e:
                 B.mm_set_max_dm(ctx, bad)

@@ -340,7 +340,7 @@ def test_pass_times_account_for_every_evaluation():
     B.mm_advance(s.ctx, B.MM_RKDP, 3, dt_s=1e-13, tol=-1.0)
     t1 = B.mm_pass_times(s.ctx)
     st = B.mm_get_stats(s.ctx)
-    cell_passes = ("k_xinv_local", "k_xinv_local_fused", "k_local", "k_local_h")
+    cell_passes = ("k_xinv_local", "k_xinv_local_fused", "k_local", "k_local_h", "k_small")
     assert sum(v["launches"] for k, v in t1.items() if k in cell_passes) == st["evals"] == 19
     assert all(v["ms_total"] >= 0.0 for v in t1.values()) and sum(v["ms_total"] for v in t1.values()) > 0.0
     assert B.mm_pass_times(s.ctx) == t1
@@ -361,11 +361,13 @@ def test_film_term_set_kernel_agrees_with_general_kernel(method, dt, tol, shape)
     mat = dict(Ms=8e5, Aex=1.3e-11, Ku=2e4, easy_axis=tuple(ax), alpha=0.2, B=(0.0, 0.01, 0.02))
     m = inputs.smooth_tilt(shape)
     outs = []
+    # the library keeps the caller's pointer: the axes array must outlive the runs
+    axes = to_dev(np.broadcast_to(ax.astype(np.float32)[:, None, None, None], (3,) + tuple(shape[::-1])).copy())
     for per_cell in (False, True):
         s = solver(shape, cell, **mat)
+        B.mm_set_pass_layout(s.ctx, B.MM_LAYOUT_FUSED)      # the multi-kernel passes, not the cluster launch
         if per_cell:
-            axes = np.broadcast_to(ax.astype(np.float32)[:, None, None, None], (3,) + tuple(shape[::-1])).copy()
-            B.mm_set_anisotropy_axes(s.ctx, to_dev(axes))
+            B.mm_set_anisotropy_axes(s.ctx, axes)
         md = to_dev(m)
         B.mm_load(s.ctx, md)
         B.mm_advance(s.ctx, method, 1, dt_s=dt, tol=tol)
