@@ -902,7 +902,11 @@ def run_cufft_comparison(args):
 
 def algorithmic_bytes_rk_3d(shape):
     """Method bytes of one Dormand-Prince step of an open 3-D grid (Sec. 3.2
-    passes: x, y forward, z column pass, y, x inverse per evaluation)."""
+    passes: x, y forward, z column pass, y, x inverse per evaluation).  With
+    nz <= 8 the y and z stages are one pass over the x spectrum (read and
+    written once, plus the kernel); beyond, the y forward pass writes the
+    z-padded spectrum s2, the z column pass reads and writes it and the y
+    inverse pass reads it back."""
     nx, ny, nz = shape
     N = nx * ny * nz
     px, py = 2 * nx, 2 * ny
@@ -918,7 +922,7 @@ def algorithmic_bytes_rk_3d(shape):
     fused = [s1 + m + m * (reads[s] + 2) + s1 for s in range(2, 7)]
     final = s1 + m + m * 5 + m
     xf = s1 + 3 * m
-    col = 2 * (s1 + s2) + 2 * s2 + kern
+    col = 2 * s1 + kern if nz <= 8 else 2 * (s1 + s2) + 2 * s2 + kern
     return {"step": float(xf + 6 * col + sum(fused) + final)}
 
 

@@ -354,12 +354,13 @@ int mm_run_host(mm_ctx* ctx, float* m_host, int method, long nsteps, double dt_s
  * local terms, stage-2 combine, local terms without demag, x inverse + local
  * terms + forward x transform of the next stage's input, x inverse alone
  * (demag field to a buffer), cell pass reading that buffer, forward x
- * transform of the next stage's input, the one-launch cluster evaluation.
+ * transform of the next stage's input, the one-launch cluster evaluation, the
+ * y forward + z column + y inverse pass of 3-D grids with nz <= 8.
  * Time steps use the fused passes; the split passes run under MM_LAYOUT_SPLIT
  * (mm_set_pass_layout) and in batches; small 2-D grids run the cluster launch
  * (MM_LAYOUT_AUTO, MM_LAYOUT_CLUSTER).
  */
-enum { MM_NPASS = 13 };
+enum { MM_NPASS = 14 };
 int mm_profile(mm_ctx* ctx, int enable);
 int mm_pass_times(mm_ctx* ctx, double* ms_out, long long* count_out);
 

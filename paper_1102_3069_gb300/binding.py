@@ -312,7 +312,7 @@ def mm_run_host(ctx, m_host, method, nsteps, dt_s=0.0, tol=1e-6):
 
 
 PASS_NAMES = ["k_xfwd", "k_colconv_y", "k_yfwd", "k_colconv_z", "k_yinv", "k_xinv_local", "k_combine2", "k_local",
-              "k_xinv_local_fused", "k_xinv_h", "k_local_h", "k_xfwd_next", "k_small"]
+              "k_xinv_local_fused", "k_xinv_h", "k_local_h", "k_xfwd_next", "k_small", "k_yzconv"]
 NPASS = len(PASS_NAMES)
 
 

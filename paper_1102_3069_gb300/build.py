@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libmm.so")
-SOURCES = ["hotpath.cu", "hotpath_odd.cu", "hotpath_odd_yz.cu", "hotpath_small.cu", "setup.cu", "api.cu", "tc_gemm.cu", "fno.cu", "split_dft.cu"]
+SOURCES = ["hotpath.cu", "hotpath_odd.cu", "hotpath_odd_yz.cu", "hotpath_small.cu", "hotpath_yz.cu", "setup.cu", "api.cu", "tc_gemm.cu", "fno.cu", "split_dft.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

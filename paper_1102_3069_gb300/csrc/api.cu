@@ -1285,7 +1285,7 @@ struct mm_batch {
 namespace {
 
 constexpr int kBatchPasses[] = {mm::PASS_XFWD, mm::PASS_YCONV, mm::PASS_YFWD, mm::PASS_ZCONV, mm::PASS_YINV,
-                                mm::PASS_XINV_H, mm::PASS_LOCAL_H, mm::PASS_XFWD_NEXT};
+                                mm::PASS_YZCONV, mm::PASS_XINV_H, mm::PASS_LOCAL_H, mm::PASS_XFWD_NEXT};
 
 int bfail(mm_batch* b, int code, const std::string& msg) {
     if (b) b->err = msg;
@@ -1302,7 +1302,9 @@ int bfail(mm_batch* b, int code, const std::string& msg) {
 int batch_work(mm_batch* b, const std::vector<int>& which, std::vector<int4>* out,
                std::vector<mm_batch::Group>* groups) {
     for (int pass : kBatchPasses) {
-        std::vector<std::vector<int4>> by_logp(16);
+        // samples grouped by the pass's kernel (its FFT length; for the fused
+        // y-z pass the length and the z cells per block)
+        std::map<int, std::vector<int4>> by_logp;
         for (int i : which) {
             int gx = 0, gy = 0;
             BCK(mm::batch_pass_grid(b->hp[i], pass, &gx, &gy));
@@ -1312,10 +1314,9 @@ int batch_work(mm_batch* b, const std::vector<int>& which, std::vector<int4>* ou
             for (int by = 0; by < gy; ++by)
                 for (int bx = 0; bx < gx; ++bx) by_logp[lp].push_back(make_int4(i, bx, by, nblk));
         }
-        for (int lp = 0; lp < 16; ++lp) {
-            if (by_logp[lp].empty()) continue;
-            if (groups) groups->push_back({pass, lp, (int)by_logp[lp].size(), out->size(), 0});
-            out->insert(out->end(), by_logp[lp].begin(), by_logp[lp].end());
+        for (auto& kv : by_logp) {
+            if (groups) groups->push_back({pass, kv.first, (int)kv.second.size(), out->size(), 0});
+            out->insert(out->end(), kv.second.begin(), kv.second.end());
         }
     }
     return MM_OK;

@@ -138,6 +138,7 @@ cudaError_t configure_hot_kernels() {
     if (e != cudaSuccess) return e;
     if ((e = configure_odd_kernels()) != cudaSuccess) return e;
     if ((e = configure_odd_yz_kernels()) != cudaSuccess) return e;
+    if ((e = configure_yz_kernels()) != cudaSuccess) return e;
     return configure_small_kernels();
 }
 
@@ -236,6 +237,8 @@ int eval_passes(const HotParams& p, const LaunchArgs& a, int* ids) {
         if (!a.have_spectrum) ids[n++] = PASS_XFWD;
         if (p.nz == 1) {
             ids[n++] = PASS_YCONV;
+        } else if (yz_fused_nz(p)) {
+            ids[n++] = PASS_YZCONV;
         } else {
             ids[n++] = PASS_YFWD;
             ids[n++] = PASS_ZCONV;
@@ -288,6 +291,8 @@ cudaError_t launch_pass(const HotParams& p, const LaunchArgs& a, int pass, cudaS
             break;
         case PASS_SMALL:
             return launch_small(p, a, s);
+        case PASS_YZCONV:
+            return launch_yzconv(p, a, s);
         case PASS_LOCAL:            // one cell per thread: every load in flight at once
             k_local<<<(unsigned)((p.ncell + 255) / 256), 256, 0, s>>>(p, a);
             break;
@@ -311,6 +316,7 @@ int batch_pass_logp(const HotParams& p, int pass) {
         case PASS_XFWD: case PASS_XFWD_NEXT: case PASS_XINV_H: return p.logpx;
         case PASS_YCONV: case PASS_YFWD: case PASS_YINV: return p.logpy;
         case PASS_ZCONV: return p.logpz;
+        case PASS_YZCONV: return p.logpy * 100 + yz_fused_nz(p);     // length and z cells per block
         default: return 0;
     }
 }
@@ -339,13 +345,18 @@ cudaError_t batch_pass_grid(const HotParams& p, int pass, int* gx, int* gy) {
             MM_LOGP_SWITCH(p.logpy, MM_G)
 #undef MM_G
             return cudaSuccess;
+        case PASS_YZCONV:
+            if (p.nz == 1 || !yz_fused_nz(p)) return cudaSuccess;
+            *gx = p.hx;
+            *gy = 1;
+            return cudaSuccess;
         case PASS_YFWD: case PASS_YINV:
-            if (p.nz == 1) return cudaSuccess;
+            if (p.nz == 1 || yz_fused_nz(p)) return cudaSuccess;
             *gx = p.hx;
             *gy = (p.nz + tz_of(p.logpy) - 1) / tz_of(p.logpy);
             return cudaSuccess;
         case PASS_ZCONV:
-            if (p.nz == 1) return cudaSuccess;
+            if (p.nz == 1 || yz_fused_nz(p)) return cudaSuccess;
 #define MM_G(L) { *gx = p.hx; *gy = (p.py + CC<L>::COLS - 1) / CC<L>::COLS; }
             MM_LOGP_SWITCH(p.logpz, MM_G)
 #undef MM_G
@@ -406,6 +417,7 @@ cudaError_t launch_pass_batched(const HotParams* ps, const int4* work, int nb, c
         kb_local<<<nb, 256, 0, s>>>(ps, work, a);
         return cudaGetLastError();
     }
+    if (pass == PASS_YZCONV) return launch_yzconv_batched(ps, work, nb, a, logp, s);
     if (variant) {
 #define MM_CALL_B(L) e = launch_b<L, 1>(ps, work, nb, a, pass, s)
         MM_LOGP_SWITCH(logp, MM_CALL_B)

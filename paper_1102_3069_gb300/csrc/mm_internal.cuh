@@ -155,7 +155,8 @@ enum Pass : int {
     PASS_LOCAL_H = 10,      // cell pass with H_demag from hbuf
     PASS_XFWD_NEXT = 11,    // forward x transform of the next evaluation's input
     PASS_SMALL = 12,        // the whole evaluation in one cluster launch (small 2-D grids)
-    NPASS = 13
+    PASS_YZCONV = 13,       // 3-D grids with nz <= 8: y forward, z column pass and y inverse in one pass
+    NPASS = 14
 };
 
 // hot path (hotpath.cu)
@@ -189,6 +190,14 @@ struct SmallSteps {
 };
 cudaError_t launch_small_steps(const HotParams& p, const SmallSteps& steps, cudaStream_t s);
 cudaError_t configure_small_kernels();
+
+// the y and z stages of 3-D grids with few z cells in one pass (hotpath_yz.cu):
+// 4 or 8 z cells per block where it applies, else 0; its launches
+int yz_fused_nz(const HotParams& p);
+cudaError_t launch_yzconv(const HotParams& p, const LaunchArgs& a, cudaStream_t s);
+cudaError_t launch_yzconv_batched(const HotParams* ps, const int4* work, int nb, const LaunchArgs& a, int code,
+                                  cudaStream_t s);
+cudaError_t configure_yz_kernels();
 
 // batched passes over independent samples (hotpath.cu)
 bool batch_supported(const HotParams& p);

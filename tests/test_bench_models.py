@@ -50,20 +50,22 @@ def test_cube_pass_bytes_by_hand():
 
 
 def test_rk_3d_step_bytes_reduce_to_the_passes():
-    # the ensemble's 3-D samples: open in all three axes
-    nx, ny, nz = 40, 30, 3
-    N = nx * ny * nz
-    m = 12 * N
-    pz = 8                             # next power of two >= 2*3 - 1
-    hx = nx + 1
-    s1 = 3 * hx * nz * ny * 8
-    s2 = 3 * hx * 2 * ny * nz * 8
-    kern = 6 * hx * (ny + 1) * (pz // 2 + 1) * 4
-    col = 2 * (s1 + s2) + 2 * s2 + kern
-    reads = [2, 3, 4, 5, 5]
-    fused = sum(2 * s1 + m * (1 + r + 2) for r in reads)
-    final = s1 + 7 * m
-    assert bench.algorithmic_bytes_rk_3d((nx, ny, nz))["step"] == (s1 + 3 * m) + 6 * col + fused + final
+    # the ensemble's 3-D samples: open in all three axes; up to 8 z cells the
+    # y and z stages are one pass over the x spectrum, beyond they go through
+    # the z-padded spectrum s2
+    for nz, pz in ((3, 8), (12, 32)):
+        nx, ny = 40, 30
+        N = nx * ny * nz
+        m = 12 * N
+        hx = nx + 1
+        s1 = 3 * hx * nz * ny * 8
+        s2 = 3 * hx * 2 * ny * nz * 8
+        kern = 6 * hx * (ny + 1) * (pz // 2 + 1) * 4
+        col = 2 * s1 + kern if nz <= 8 else 2 * (s1 + s2) + 2 * s2 + kern
+        reads = [2, 3, 4, 5, 5]
+        fused = sum(2 * s1 + m * (1 + r + 2) for r in reads)
+        final = s1 + 7 * m
+        assert bench.algorithmic_bytes_rk_3d((nx, ny, nz))["step"] == (s1 + 3 * m) + 6 * col + fused + final
 
 
 def test_traffic_is_reported_only_for_the_profiled_sources(monkeypatch):
