@@ -125,7 +125,7 @@ def aggregate_ranks(ms, cell_evals, device):
     return ms_max, float(tot[0]) / (ms_max * 1e-3)
 
 
-HOT_SOURCES = ("fft32.cuh", "hotpath.cu", "mm_internal.cuh")   # the kernels of the timed step
+HOT_SOURCES = ("fft32.cuh", "hotpath.cu", "hotpath_kernels.cuh", "mm_internal.cuh")   # the kernels of the timed step
 
 
 def _source_hash():
