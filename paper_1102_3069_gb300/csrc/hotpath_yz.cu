@@ -19,14 +19,15 @@ namespace mm {
 
 namespace {
 
-// NZ: the z cells the block's registers hold (2, 4 or 8; nz <= NZ)
+// NZ: the z cells the block's registers hold (2, 3, 4 or 8; nz <= NZ)
 template <int LOGP, int NZ>
 struct YZ {
     static constexpr int P = 1 << LOGP;
     static constexpr int NL = 3 * NZ;                       // lines (component, z) of P points
     static constexpr int NT = mmfft::threads_of(NL, LOGP);
     static constexpr int LS = mmfft::padded_len(P);
-    static constexpr size_t SMEM = (size_t)(NL * LS + 2 * NZ) * sizeof(float2);
+    static constexpr int PZC = NZ == 3 ? 8 : 2 * NZ;        // Pz of an open z axis of NZ cells
+    static constexpr size_t SMEM = (size_t)(NL * LS + PZC) * sizeof(float2);
     // resident blocks asked of the register allocator: the blocks are many
     // (one per kx column of every sample) and each waits on its loads, so
     // residency matters more than a few spilled values (nz <= 8 keeps 48
@@ -60,9 +61,9 @@ __device__ __forceinline__ void yzconv_body(const HotParams& p, const LaunchArgs
         const bool yh = ky > (S::P >> 1);
         const int kyq = yh ? S::P - ky : ky;
         const float* kb = p.kt + ((long long)kx * p.hyk + kyq) * p.hzk;
-        if (PZ == 2 * NZ) {
-            // open z (Pz = 2 NZ): register FFTs of the Pz-point lines (zero past nz)
-            constexpr int PZC = 2 * NZ;
+        if (PZ == S::PZC) {
+            // open z: register FFTs of the Pz-point lines (zero past nz)
+            constexpr int PZC = S::PZC;
             float2 X[3][PZC];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -157,19 +158,20 @@ kb_yzconv(const HotParams* __restrict__ ps, const int4* __restrict__ work, Launc
     yzconv_body<LOGP, NZ>(s_hp, a, w.y);
 }
 
-// y lengths 2^3 .. 2^10 with nz <= 2 and nz <= 4, 2^3 .. 2^8 with nz <= 8 (the
+// y lengths 2^3 .. 2^10 with nz = 2, 3, 4, 2^3 .. 2^8 with nz = 5 .. 8 (the
 // lines fit the shared memory of a block; at 2^9 points and 8 z cells the 768
 // threads' register budget spills the z stage's 48 complex values per thread)
 #define MM_YZ_SHAPES(X) X(3, 2) X(4, 2) X(5, 2) X(6, 2) X(7, 2) X(8, 2) X(9, 2) X(10, 2) \
+    X(3, 3) X(4, 3) X(5, 3) X(6, 3) X(7, 3) X(8, 3) X(9, 3) X(10, 3) \
     X(3, 4) X(4, 4) X(5, 4) X(6, 4) X(7, 4) X(8, 4) X(9, 4) X(10, 4) \
     X(3, 8) X(4, 8) X(5, 8) X(6, 8) X(7, 8) X(8, 8)
 
 }  // namespace
 
-// 2, 4 or 8: the fused pass applies with that many z cells per block; 0: it does not
+// 2, 3, 4 or 8: the fused pass applies with that many z cells per block; 0: it does not
 int yz_fused_nz(const HotParams& p) {
     if (p.nz < 2 || p.nz > 8 || p.ry != 1 || p.rz != 1 || p.zsplit) return 0;
-    const int nzc = p.nz <= 2 ? 2 : p.nz <= 4 ? 4 : 8;
+    const int nzc = p.nz <= 4 ? p.nz : 8;
     switch (p.logpy * 100 + nzc) {
 #define MM_CASE(L, N) case L * 100 + N: return N;
         MM_YZ_SHAPES(MM_CASE)
