@@ -40,18 +40,31 @@ __device__ __forceinline__ void yzconv_body(const HotParams& p, const LaunchArgs
     using namespace mmfft;
     using S = YZ<LOGP, NZ>;
     extern __shared__ float2 sm[];
-    if (a.mode != LM_EVAL && p.st->done) return;
     float2* tz = sm + S::NL * S::LS;                        // exp(-2 pi i t / Pz), t < Pz
     const int nz = p.nz, PZ = p.pz, NY = p.ny, HX = p.hx;
     const long long nyp = p.nyp;
-    for (int t = threadIdx.x; t < PZ; t += S::NT) tz[t] = p.tw[t * (TWN / PZ)];
-    // the block's lines: l = c NZ + z, y < ny from s1, zero elsewhere
-    for (int idx = threadIdx.x; idx < S::NL * S::P; idx += S::NT) {
-        const int l = idx >> LOGP, y = idx & (S::P - 1);
-        const int c = l / NZ, z = l - c * NZ;
-        float2 v = make_float2(0.f, 0.f);
-        if (z < nz && y < NY) v = p.s1[((long long)(c * HX + kx) * nz + z) * nyp + y];
-        sm[l * S::LS + pad(y)] = v;
+    // the block's lines: l = c NZ + z, y < ny from s1, zero elsewhere; every
+    // load of the thread in flight before the first store, and before the
+    // run-state check (a finished run returns before anything is written)
+    {
+        const bool done = a.mode != LM_EVAL && p.st->done;
+        constexpr int IT = (S::NL * S::P + S::NT - 1) / S::NT;
+        float2 v[IT];
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+            const int idx = threadIdx.x + it * S::NT;
+            const int l = idx >> LOGP, y = idx & (S::P - 1);
+            const int c = l / NZ, z = l - c * NZ;
+            v[it] = make_float2(0.f, 0.f);
+            if (idx < S::NL * S::P && z < nz && y < NY) v[it] = p.s1[((long long)(c * HX + kx) * nz + z) * nyp + y];
+        }
+        if (done) return;
+        for (int t = threadIdx.x; t < PZ; t += S::NT) tz[t] = p.tw[t * (TWN / PZ)];
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+            const int idx = threadIdx.x + it * S::NT;
+            if (idx < S::NL * S::P) sm[(idx >> LOGP) * S::LS + pad(idx & (S::P - 1))] = v[it];
+        }
     }
     __syncthreads();
     fft_lines<LOGP, S::NL, false>(sm, p.tw);
