@@ -187,14 +187,16 @@ struct XS {
     static constexpr int TY = 24 * NBL <= 512 ? 16 : 12 * NBL <= 512 ? 8 : 6 * NBL <= 512 ? 4 : 2;
     static constexpr int NL = 3 * TY / 2;       // complex lines (two real rows each)
     static constexpr int NT0 = (NL * NBL + 31) / 32 * 32 < 64 ? 64 : (NL * NBL + 31) / 32 * 32;
-    // lines of <= 256 points: 512 threads, more than the transforms use (the
+    // lines of <= 128 points: 512 threads, more than the transforms use (the
     // rest join their barriers), so that the block's cell epilogue and its
     // loads run about one cell pair per thread instead of several in turn
-    // (measured: Dormand-Prince step of the 64 x 16 film 127 -> 107 us)
-    static constexpr int NT = (R0 == 1 && LOGP <= 8 && NT0 < 512) ? 512 : NT0;
+    // (measured: Dormand-Prince step of the 64 x 16 film 127 -> 107 us).
+    // Such grids have few row blocks, so the register budget is not cut for
+    // residency.
+    static constexpr int NT = (R0 == 1 && LOGP <= 7 && NT0 < 512) ? 512 : NT0;
     static constexpr int LS = padded_len(P);
     static constexpr int HX = P == 1 ? 1 : P / 2 + 1;
-    static constexpr int MINB = NT >= 768 ? 1 : 1024 / NT;
+    static constexpr int MINB = NT != NT0 || NT >= 768 ? 1 : 1024 / NT;
     static_assert(R0 != 1 || (TY == ty_of(LOGP) && NT0 == threads_of(NL, LOGP)), "power-of-two shapes");
 };
 
