@@ -453,14 +453,17 @@ int mm_batch_relax(mm_batch* b, float* const* m, double torque_tol, double err_t
 /*
  * Batch autotuner.  Every batched FFT pass is compiled with two register
  * budgets (an occupancy-first one and one of at least 80 registers per
- * thread, fewer resident blocks); where they differ, the batch times both on
- * its samples when it builds its launch lists (first advance, and after
- * finished samples leave a relaxation) and keeps the faster.  Choices are
- * cached for the process, keyed by pass, FFT length and block count (power of
- * two).  mode 1 (default) tunes, 0 always launches the default budget, 2 the
- * other budget wherever there is one (for tests; results are the same).
- * mm_batch_tuning reports the current launch groups, how many of them had two
- * budgets, and how many run the second.
+ * thread, fewer resident blocks), and the register x passes also with a
+ * second tile shape (half the row pairs per block, twice the blocks).  Where
+ * a pass has alternatives, the batch times each on its samples when it
+ * builds its launch lists (first advance, and after finished samples leave a
+ * relaxation) and keeps the fastest; a tile choice rebuilds that pass's work
+ * list.  Choices are cached for the process, keyed by pass, FFT length and
+ * block count (power of two).  mode 1 (default) tunes, 0 always launches the
+ * default kernels, 2 the other register budget wherever there is one, 3 the
+ * other tile shape wherever there is one (2 and 3 for tests; results are the
+ * same).  MM_EINVAL for other modes.  mm_batch_tuning reports the current launch
+ * groups, how many of them had alternatives, and how many run one.
  */
 int mm_batch_set_tuning(mm_batch* b, int mode);
 int mm_batch_tuning(const mm_batch* b, int* n_groups, int* n_tunable, int* n_alternative);

@@ -1266,7 +1266,10 @@ struct mm_batch {
     size_t ws_size = 0;
     size_t off_ps = 0, off_work = 0, off_states = 0, off_active = 0, total = 0;
     std::vector<mm::HotParams> hp_dev;        // what the device descriptors hold (uploaded on change)
-    size_t max_work = 0;                      // int4 entries for all samples
+    size_t max_work = 0;                      // int4 entries for all samples (both tile shapes, and a group's
+                                              // alternative list while the autotuner times it)
+    size_t work_used = 0;                     // entries of the current lists
+    std::vector<int4> work_host;              // their host copy
     std::vector<mm::HotParams> hp;            // host copies of the device descriptors
     std::vector<int> active;                  // samples in the current work lists
     struct Group { int pass, logp, nb; size_t off; int variant; };
@@ -1298,16 +1301,25 @@ int bfail(mm_batch* b, int code, const std::string& msg) {
         if (e_ != cudaSuccess) return bfail(b, MM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
+// tile variant of a group (pass, FFT length) in the work lists: 2 = the half
+// tile of the register x passes, else 0 (the register budgets share a list)
+using TileMap = std::map<std::pair<int, int>, int>;
+
 // blocks of every pass for the samples in `which` (work entries appended to out)
 int batch_work(mm_batch* b, const std::vector<int>& which, std::vector<int4>* out,
-               std::vector<mm_batch::Group>* groups) {
+               std::vector<mm_batch::Group>* groups, const TileMap* tiles = nullptr) {
     for (int pass : kBatchPasses) {
         // samples grouped by the pass's kernel (its FFT length; for the fused
         // y-z pass the length and the z cells per block)
         std::map<int, std::vector<int4>> by_logp;
         for (int i : which) {
             int gx = 0, gy = 0;
-            BCK(mm::batch_pass_grid(b->hp[i], pass, &gx, &gy));
+            int tile = 0;
+            if (tiles) {
+                auto it = tiles->find({pass, mm::batch_pass_logp(b->hp[i], pass)});
+                if (it != tiles->end()) tile = it->second;
+            }
+            BCK(mm::batch_pass_grid(b->hp[i], pass, tile, &gx, &gy));
             const int nblk = gx * gy;
             if (nblk == 0) continue;
             const int lp = mm::batch_pass_logp(b->hp[i], pass);
@@ -1315,7 +1327,12 @@ int batch_work(mm_batch* b, const std::vector<int>& which, std::vector<int4>* ou
                 for (int bx = 0; bx < gx; ++bx) by_logp[lp].push_back(make_int4(i, bx, by, nblk));
         }
         for (auto& kv : by_logp) {
-            if (groups) groups->push_back({pass, kv.first, (int)kv.second.size(), out->size(), 0});
+            int tile = 0;
+            if (tiles) {
+                auto it = tiles->find({pass, kv.first});
+                if (it != tiles->end()) tile = it->second;
+            }
+            if (groups) groups->push_back({pass, kv.first, (int)kv.second.size(), out->size(), tile});
             out->insert(out->end(), kv.second.begin(), kv.second.end());
         }
     }
@@ -1340,60 +1357,111 @@ struct EventPair {
     }
 };
 
-int batch_tune(mm_batch* b) {
+// Times every compiled variant of every group with more than one (the
+// register budgets on the group's work list, the half tile of the register x
+// passes on its own list, uploaded past the current lists) and records the
+// fastest in *pick; a choice cached for the process is taken without timing.
+int batch_tune(mm_batch* b, size_t work_used, std::map<size_t, int>* pick) {
     if (b->tune_mode == 0 || b->active.empty()) return MM_OK;
     const mm::LaunchArgs a = make_args(b->hp[b->active[0]], mm::SRC_CUR, mm::LM_EVAL, 0, false, false);
     const mm::HotParams* ps = reinterpret_cast<const mm::HotParams*>(b->ws + b->off_ps);
-    const int4* work = reinterpret_cast<const int4*>(b->ws + b->off_work);
+    int4* work = reinterpret_cast<int4*>(b->ws + b->off_work);
     EventPair ev;
     cudaEvent_t& e0 = ev.e0;
     cudaEvent_t& e1 = ev.e1;
-    for (auto& g : b->groups) {
-        if (mm::batch_variants(g.pass, g.logp) < 2) continue;
-        if (b->tune_mode == 2) { g.variant = 1; continue; }
+    for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+        const auto& g = b->groups[gi];
+        const int nv = mm::batch_variants(g.pass, g.logp);
+        if (nv < 2) continue;
+        if (b->tune_mode == 2) { (*pick)[gi] = 1; continue; }
+        if (b->tune_mode == 3) { (*pick)[gi] = nv >= 3 ? 2 : 0; continue; }
         const auto key = std::make_tuple(g.pass, g.logp, ilog2(g.nb));
         {
             std::lock_guard<std::mutex> lock(g_tune_mutex);
             auto it = g_tune_cache.find(key);
-            if (it != g_tune_cache.end()) { g.variant = it->second; continue; }
+            if (it != g_tune_cache.end()) { (*pick)[gi] = it->second; continue; }
         }
         if (!e0) { BCK(cudaEventCreate(&e0)); BCK(cudaEventCreate(&e1)); }
         float best = 0.f;
-        int pick = 0;
-        for (int v = 0; v < 2; ++v) {
-            BCK(mm::launch_pass_batched(ps, work + g.off, g.nb, a, g.pass, g.logp, v, b->stream));   // warm-up
+        int choice = 0;
+        for (int v = 0; v < nv; ++v) {
+            const int4* wv = work + g.off;
+            int nb = g.nb;
+            if (v == 2) {
+                // this group's samples with the half tile, past the current lists
+                std::vector<int> samples;
+                int last = -1;
+                for (size_t k = g.off; k < g.off + (size_t)g.nb && k < b->work_host.size(); ++k)
+                    if (b->work_host[k].x != last) { samples.push_back(b->work_host[k].x); last = b->work_host[k].x; }
+                TileMap one = {{{g.pass, g.logp}, 2}};
+                std::vector<int4> alt;
+                std::vector<mm_batch::Group> agroups;
+                int rc = batch_work(b, samples, &alt, &agroups, &one);
+                if (rc) return rc;
+                size_t off = 0, cnt = 0;
+                for (const auto& ag : agroups)
+                    if (ag.pass == g.pass && ag.logp == g.logp) { off = ag.off; cnt = ag.nb; }
+                if (cnt == 0 || work_used + cnt > b->max_work) continue;
+                BCK(cudaMemcpyAsync(work + work_used, alt.data() + off, cnt * sizeof(int4), cudaMemcpyHostToDevice,
+                                    b->stream));
+                BCK(cudaStreamSynchronize(b->stream));
+                wv = work + work_used;
+                nb = (int)cnt;
+            }
+            BCK(mm::launch_pass_batched(ps, wv, nb, a, g.pass, g.logp, v, b->stream));   // warm-up
             BCK(cudaEventRecord(e0, b->stream));
-            for (int r = 0; r < 3; ++r) BCK(mm::launch_pass_batched(ps, work + g.off, g.nb, a, g.pass, g.logp, v, b->stream));
+            for (int r = 0; r < 3; ++r) BCK(mm::launch_pass_batched(ps, wv, nb, a, g.pass, g.logp, v, b->stream));
             BCK(cudaEventRecord(e1, b->stream));
             BCK(cudaEventSynchronize(e1));
             float ms = 0.f;
             BCK(cudaEventElapsedTime(&ms, e0, e1));
-            if (v == 0 || ms < best) { best = ms; pick = v; }
+            if (v == 0 || ms < best) { best = ms; choice = v; }
         }
-        g.variant = pick;
+        (*pick)[gi] = choice;
         std::lock_guard<std::mutex> lock(g_tune_mutex);
-        g_tune_cache[key] = pick;
+        g_tune_cache[key] = choice;
     }
     return MM_OK;
 }
 
-// work lists for the active samples, uploaded to the batch workspace
-int batch_build_groups(mm_batch* b) {
+// work lists for the active samples, uploaded to the batch workspace; then
+// the autotuner's choices, and the lists again where it chose a tile shape
+int batch_upload(mm_batch* b, const TileMap* tiles) {
     std::vector<int4> work;
     std::vector<mm_batch::Group> groups;
-    int rc = batch_work(b, b->active, &work, &groups);
+    int rc = batch_work(b, b->active, &work, &groups, tiles);
     if (rc) return rc;
     if (work.size() > b->max_work) return bfail(b, MM_ENOMEM, "batch work list larger than its reservation");
     if (!work.empty())
         BCK(cudaMemcpyAsync(b->ws + b->off_work, work.data(), work.size() * sizeof(int4), cudaMemcpyHostToDevice,
                             b->stream));
+    BCK(cudaStreamSynchronize(b->stream));    // the host vector goes out of scope
+    b->groups = groups;
+    b->work_used = work.size();
+    b->work_host.swap(work);
+    return MM_OK;
+}
+
+int batch_build_groups(mm_batch* b) {
+    int rc = batch_upload(b, nullptr);
+    if (rc) return rc;
     if (!b->active.empty())
         BCK(cudaMemcpyAsync(b->ws + b->off_active, b->active.data(), b->active.size() * sizeof(int),
                             cudaMemcpyHostToDevice, b->stream));
-    BCK(cudaStreamSynchronize(b->stream));    // the host vector goes out of scope
-    b->groups = groups;
-    int rc2 = batch_tune(b);
-    if (rc2) return rc2;
+    BCK(cudaStreamSynchronize(b->stream));
+    std::map<size_t, int> pick;
+    if ((rc = batch_tune(b, b->work_used, &pick))) return rc;
+    TileMap tiles;
+    for (const auto& kv : pick)
+        if (kv.second == 2) tiles[{b->groups[kv.first].pass, b->groups[kv.first].logp}] = 2;
+    std::map<std::pair<int, int>, int> budget;      // register budget of the groups that keep their tile
+    for (const auto& kv : pick)
+        if (kv.second != 2) budget[{b->groups[kv.first].pass, b->groups[kv.first].logp}] = kv.second;
+    if (!tiles.empty() && (rc = batch_upload(b, &tiles))) return rc;
+    for (auto& g : b->groups) {
+        auto it = budget.find({g.pass, g.logp});
+        if (g.variant != 2 && it != budget.end()) g.variant = it->second;
+    }
     b->groups_ready = true;
     if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
     return MM_OK;
@@ -1567,12 +1635,19 @@ int mm_batch_create(mm_batch** out, mm_ctx* const* ctxs, int n, void* cuda_strea
     }
     std::vector<int> all(n);
     for (int i = 0; i < n; ++i) all[i] = i;
-    std::vector<int4> work;
-    if (batch_work(b, all, &work, nullptr) != MM_OK) {
+    std::vector<int4> work, half;
+    TileMap all_half;
+    for (int pass : kBatchPasses)
+        for (int i = 0; i < n; ++i) {
+            const int lp = mm::batch_pass_logp(b->hp[i], pass);
+            if (mm::batch_variants(pass, lp) >= 3) all_half[{pass, lp}] = 2;
+        }
+    if (batch_work(b, all, &work, nullptr) != MM_OK || batch_work(b, all, &half, nullptr, &all_half) != MM_OK) {
         delete b;
         return MM_EINVAL;
     }
-    b->max_work = work.size();
+    // the longer of the two lists, plus room for one group's alternative list
+    b->max_work = std::max(work.size(), half.size()) + half.size();
     for (int i = 0; i < n; ++i) ctxs[i]->stream = b->stream;    // every sample's work goes on the batch stream
     size_t off = 0;
     b->off_ps = off; off += align256((size_t)n * sizeof(mm::HotParams));
@@ -1699,7 +1774,7 @@ int mm_batch_relax(mm_batch* b, float* const* m, double torque_tol, double err_t
 
 int mm_batch_set_tuning(mm_batch* b, int mode) {
     if (!b) return MM_EINVAL;
-    if (mode < 0 || mode > 2) return bfail(b, MM_EINVAL, "tuning mode must be 0, 1 or 2");
+    if (mode < 0 || mode > 3) return bfail(b, MM_EINVAL, "tuning mode must be 0, 1, 2 or 3");
     if (mode != b->tune_mode) {
         b->tune_mode = mode;
         b->groups_ready = false;                     // chosen again at the next advance

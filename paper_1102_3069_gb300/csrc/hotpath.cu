@@ -330,11 +330,17 @@ bool batch_supported(const HotParams& p) {
     return true;
 }
 
-cudaError_t batch_pass_grid(const HotParams& p, int pass, int* gx, int* gy) {
+cudaError_t batch_pass_grid(const HotParams& p, int pass, int variant, int* gx, int* gy) {
     *gx = 0;
     *gy = 0;
     switch (pass) {
         case PASS_XFWD: case PASS_XFWD_NEXT: case PASS_XINV_H:
+            if (variant == 2) {
+#define MM_G(L) { *gx = (p.ny + XR<L, 1>::TY - 1) / XR<L, 1>::TY; *gy = p.nz; }
+                MM_LOGP_SWITCH(p.logpx, MM_G)
+#undef MM_G
+                return cudaSuccess;
+            }
 #define MM_G(L) { *gx = (p.ny + XR<L>::TY - 1) / XR<L>::TY; *gy = p.nz; }
             MM_LOGP_SWITCH(p.logpx, MM_G)
 #undef MM_G
@@ -373,6 +379,28 @@ cudaError_t batch_pass_grid(const HotParams& p, int pass, int* gx, int* gy) {
 template <int L, int V>
 static cudaError_t launch_b(const HotParams* ps, const int4* work, int nb, const LaunchArgs& a, int pass,
                             cudaStream_t s) {
+    if constexpr (V == 2) {
+        // the half tile exists for the register x passes only
+        if constexpr (L >= BATCH_MIN_LOGP && L <= BATCH_MAX_LOGP) {
+            using R = XR<L, 1>;
+            switch (pass) {
+                case PASS_XFWD:
+                    kb_xfwd_r<L, 2><<<nb, R::NT, R::SMEM, s>>>(ps, work, a);
+                    return cudaSuccess;
+                case PASS_XFWD_NEXT: {
+                    LaunchArgs b = a;
+                    b.src = a.next_src;
+                    kb_xfwd_r<L, 2><<<nb, R::NT, R::SMEM, s>>>(ps, work, b);
+                    return cudaSuccess;
+                }
+                case PASS_XINV_H:
+                    kb_xinv_h<L, 2><<<nb, R::NT, R::SMEM, s>>>(ps, work, a);
+                    return cudaSuccess;
+                default: break;
+            }
+        }
+        return cudaErrorInvalidValue;
+    }
     if constexpr (L >= BATCH_MIN_LOGP && L <= BATCH_MAX_LOGP) {
         switch (pass) {
             case PASS_XFWD:
@@ -418,7 +446,11 @@ cudaError_t launch_pass_batched(const HotParams* ps, const int4* work, int nb, c
         return cudaGetLastError();
     }
     if (pass == PASS_YZCONV) return launch_yzconv_batched(ps, work, nb, a, logp, s);
-    if (variant) {
+    if (variant == 2) {
+#define MM_CALL_B(L) e = launch_b<L, 2>(ps, work, nb, a, pass, s)
+        MM_LOGP_SWITCH(logp, MM_CALL_B)
+#undef MM_CALL_B
+    } else if (variant) {
 #define MM_CALL_B(L) e = launch_b<L, 1>(ps, work, nb, a, pass, s)
         MM_LOGP_SWITCH(logp, MM_CALL_B)
 #undef MM_CALL_B
@@ -437,7 +469,8 @@ int batch_variants(int pass, int logp) {
     int n = 1;
     switch (pass) {
         case PASS_XFWD: case PASS_XFWD_NEXT: case PASS_XINV_H:
-#define MM_V(L) n = XR<L>::MINB1 != XR<L>::MINB ? 2 : 1
+            // variants 0 and 1: register budgets; 2: half the row pairs per block
+#define MM_V(L) n = XR<L, 1>::PAIRS < XR<L>::PAIRS ? 3 : (XR<L>::MINB1 != XR<L>::MINB ? 2 : 1)
             MM_LOGP_SWITCH_INT(logp, MM_V)
 #undef MM_V
             break;

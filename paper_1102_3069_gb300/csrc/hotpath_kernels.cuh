@@ -1337,11 +1337,14 @@ constexpr int BATCH_MIN_LOGP = 6, BATCH_MAX_LOGP = 10;
 #define XR_MINB256 3
 #endif
 
-template <int LOGP>
+// HALF = 1: half the row pairs per block (a tile shape the batch autotuner
+// times against the default)
+template <int LOGP, int HALF = 0>
 struct XR {
     using PL = r8::Plan8<LOGP>;
     static constexpr int P = PL::P, NB = PL::NB, LS = PL::LS;
-    static constexpr int PAIRS = NB >= 256 ? 1 : (256 / NB > 8 ? 8 : 256 / NB);
+    static constexpr int PAIRS0 = NB >= 256 ? 1 : (256 / NB > 8 ? 8 : 256 / NB);
+    static constexpr int PAIRS = HALF && PAIRS0 > 1 ? PAIRS0 / 2 : PAIRS0;
     static constexpr int TY = 2 * PAIRS;
     static constexpr int NT = (PAIRS * NB + 31) / 32 * 32 < 64 ? 64 : (PAIRS * NB + 31) / 32 * 32;
     static constexpr int HX = P / 2 + 1;
@@ -1355,9 +1358,9 @@ struct XR {
 // Unpack of the paired rows (A = (Z_k + conj Z_-k)/2, B = (Z_k - conj Z_-k)/(2i))
 // and transposed store to s1 [c][kx][z][y] for lines laid out as
 // line (c, q) = sm + (c*PAIRS + q)*LS, q the row pair.
-template <int LOGP>
+template <int LOGP, int HALF = 0>
 __device__ __forceinline__ void store_x_spectrum_r(const HotParams& p, const float2* sm, int y0, int z) {
-    using S = XR<LOGP>;
+    using S = XR<LOGP, HALF>;
     for (int idx = threadIdx.x; idx < S::NL * S::HX; idx += S::NT) {
         const int l = idx / S::HX, k = idx - l * S::HX;
         const float2 A = sm[l * S::LS + pad(k)];
@@ -1372,10 +1375,10 @@ __device__ __forceinline__ void store_x_spectrum_r(const HotParams& p, const flo
 
 // forward transform of the lines whose pass-0 inputs are in v (REV = false
 // order) and transposed store of the half spectrum
-template <int LOGP>
+template <int LOGP, int HALF = 0>
 __device__ __forceinline__ void xr_forward_store(const HotParams& p, float2* const* lines, float2 (*v)[8], int j,
                                                  bool act, bool from_smem, int y0, int z, float2* sm) {
-    using S = XR<LOGP>;
+    using S = XR<LOGP, HALF>;
     r8::run<LOGP, false, false, 0, 3>(lines, v, j, act, p.tw, from_smem);
     __syncthreads();
     if (act) {
@@ -1385,12 +1388,12 @@ __device__ __forceinline__ void xr_forward_store(const HotParams& p, float2* con
             for (int i = 0; i < 8; ++i) lines[c][pad(r8::out_pos<LOGP, false, S::LASTF>(j, i))] = v[c][i];
     }
     __syncthreads();
-    store_x_spectrum_r<LOGP>(p, sm, y0, z);
+    store_x_spectrum_r<LOGP, HALF>(p, sm, y0, z);
 }
 
-template <int LOGP>
+template <int LOGP, int HALF = 0>
 __device__ __forceinline__ void xfwd_r_body(const HotParams& p, const LaunchArgs& a, int bx, int by) {
-    using S = XR<LOGP>;
+    using S = XR<LOGP, HALF>;
     extern __shared__ float2 sm[];
     const int y0 = bx * S::TY, z = by;
     DevState* st = p.st;
@@ -1435,28 +1438,29 @@ __device__ __forceinline__ void xfwd_r_body(const HotParams& p, const LaunchArgs
                 v[c][i] = w;
             }
     }
-    xr_forward_store<LOGP>(p, lines, v, j, act, false, y0, z, sm);
+    xr_forward_store<LOGP, HALF>(p, lines, v, j, act, false, y0, z, sm);
 }
 
 template <int LOGP>
 __global__ void __launch_bounds__(XR<LOGP>::NT, XR<LOGP>::MINB) k_xfwd_r(HotParams p, LaunchArgs a) {
     xfwd_r_body<LOGP>(p, a, blockIdx.x, blockIdx.y);
 }
+// V: 0 the default budget, 1 at least 80 registers, 2 half the row pairs per block
 template <int LOGP, int V>
-__global__ void __launch_bounds__(XR<LOGP>::NT, V ? XR<LOGP>::MINB1 : XR<LOGP>::MINB)
+__global__ void __launch_bounds__(XR<LOGP, V == 2>::NT, V == 1 ? XR<LOGP>::MINB1 : XR<LOGP, V == 2>::MINB)
 kb_xfwd_r(const HotParams* __restrict__ ps, const int4* __restrict__ work, LaunchArgs a) {
     const int4 w = work[blockIdx.x];
     __shared__ HotParams s_hp;
     load_params(ps + w.x, &s_hp);
-    xfwd_r_body<LOGP>(s_hp, a, w.y, w.z);
+    xfwd_r_body<LOGP, V == 2>(s_hp, a, w.y, w.z);
 }
 
 // Inverse x pass alone (C2R + crop): H_demag into hbuf [3][ncell], stored
 // straight from the registers of the last pass (thread j holds positions
 // j + r*P/8, so a warp stores consecutive x).
-template <int LOGP>
+template <int LOGP, int HALF = 0>
 __device__ __forceinline__ void xinv_h_body(const HotParams& p, const LaunchArgs& a, int bx, int by) {
-    using S = XR<LOGP>;
+    using S = XR<LOGP, HALF>;
     extern __shared__ float2 sm[];
     const int y0 = bx * S::TY, z = by;
     if (a.mode != LM_EVAL && p.st->done) return;
@@ -1508,12 +1512,12 @@ __global__ void __launch_bounds__(XR<LOGP>::NT, XR<LOGP>::MINB) k_xinv_h(HotPara
     xinv_h_body<LOGP>(p, a, blockIdx.x, blockIdx.y);
 }
 template <int LOGP, int V>
-__global__ void __launch_bounds__(XR<LOGP>::NT, V ? XR<LOGP>::MINB1 : XR<LOGP>::MINB)
+__global__ void __launch_bounds__(XR<LOGP, V == 2>::NT, V == 1 ? XR<LOGP>::MINB1 : XR<LOGP, V == 2>::MINB)
 kb_xinv_h(const HotParams* __restrict__ ps, const int4* __restrict__ work, LaunchArgs a) {
     const int4 w = work[blockIdx.x];
     __shared__ HotParams s_hp;
     load_params(ps + w.x, &s_hp);
-    xinv_h_body<LOGP>(s_hp, a, w.y, w.z);
+    xinv_h_body<LOGP, V == 2>(s_hp, a, w.y, w.z);
 }
 
 // Cell pass: local terms, torque and stage update for every cell, with the

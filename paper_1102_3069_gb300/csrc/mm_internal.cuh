@@ -202,10 +202,11 @@ cudaError_t configure_yz_kernels();
 // batched passes over independent samples (hotpath.cu)
 bool batch_supported(const HotParams& p);
 int batch_pass_logp(const HotParams& p, int pass);
-cudaError_t batch_pass_grid(const HotParams& p, int pass, int* gx, int* gy);
+// blocks of a pass for one sample (variant 2 of the register x passes: the half tile)
+cudaError_t batch_pass_grid(const HotParams& p, int pass, int variant, int* gx, int* gy);
 cudaError_t launch_pass_batched(const HotParams* ps, const int4* work, int nb, const LaunchArgs& a, int pass,
                                 int logp, int variant, cudaStream_t s);
-int batch_variants(int pass, int logp);     // 1 or 2 register budgets compiled for this pass
+int batch_variants(int pass, int logp);     // kernels compiled for this pass: register budgets, tile shapes
 cudaError_t launch_gather_states(const HotParams* ps, DevState* out, int n, cudaStream_t s);
 // run parameters of the active samples of a batch, one launch (as a per-context
 // mm_advance would set them; dt0_s > 0 sets the step, in seconds)

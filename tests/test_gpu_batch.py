@@ -204,3 +204,33 @@ def test_batch_periodic_samples_match_oracle():
         ref = llg.rkdp_stages(p, m, h)[0]
         d = float(np.max(np.abs(out[i].cpu().numpy() - ref)))
         assert d < 1e-6, (i, s["shape"], s["pbc"], d)
+
+
+def test_batch_autotuner_tile_shapes_agree():
+    """The register x passes are also compiled with half the row pairs per
+    block (twice the blocks, another work list): forcing that tile everywhere
+    changes no result beyond float32 rounding, the tuner reports the groups
+    that run it, and the timed choice (mode 1) agrees as well."""
+    import torch
+    samples = inputs.ensemble(6, seed=9, nmin=32, nmax=140, nzmax=3)
+    stream = torch.cuda.Stream()
+    outs, reports = {}, {}
+    with torch.cuda.stream(stream):
+        for mode in (0, 3, 1):
+            sol = _solvers(samples, stream.cuda_stream)
+            m0 = _m0(samples)
+            bt = B.Batch(sol, stream.cuda_stream)
+            B.mm_batch_set_tuning(bt.b, mode)
+            B.mm_batch_load(bt.b, m0)
+            B.mm_batch_advance(bt.b, B.MM_RKDP, 6, dt_s=5e-14, tol=-1.0)
+            out = [torch.empty_like(m) for m in m0]
+            B.mm_batch_store(bt.b, out)
+            torch.cuda.synchronize()
+            outs[mode] = out
+            reports[mode] = B.mm_batch_tuning(bt.b)
+    assert reports[3][2] > 0 and reports[0][2] == 0
+    for mode in (1, 3):
+        for a, b in zip(outs[0], outs[mode]):
+            assert float((a - b).abs().max()) <= 1e-6
+    with pytest.raises(B.MMError):
+        B.mm_batch_set_tuning(bt.b, 4)
