@@ -17,9 +17,12 @@
 // The reductions and the step control are those of the multi-kernel passes
 // (reduce_and_finish over the cluster's CTAs).
 //
-// The 1-D transforms are radix-4 Stockham passes (a final radix-2 pass for odd
-// log2 lengths) over lines in shared memory, with the line length a run-time
-// value, so one kernel serves every length.
+// The 1-D transforms are radix-8 Stockham passes (then one radix-4 or radix-2
+// pass for the rest of log2 P) over lines in shared memory, with the line
+// length a run-time value, so one kernel serves every length; the twiddles
+// are copied into shared memory once per evaluation.  A run of steps can be
+// one launch (k_small_steps): the evaluations of each standard step in turn,
+// a cluster barrier after each one's step control.
 #include "hotpath_kernels.cuh"
 
 #include <cooperative_groups.h>
